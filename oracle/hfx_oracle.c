@@ -1,0 +1,514 @@
+/*
+ * Plain FP64 CPU oracle for the screened periodic LRI exchange matrix.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the correctness reference the CUDA
+ * library is checked against; only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg load it.  It shares no code with the library.
+ *
+ * What it computes (Sec. II of the paper):
+ *   Eq. HFX_ERIs   Sigma_{Ii,Jj} = sum_{K,L} sum_{k,l} (Ii Kk | Jj Ll) D_{Kk,Ll}
+ *   Eq. LRI        phi_Ii phi_Kk ~ sum_{A in {I,K}} sum_alpha C^{A alpha}_{Ii,Kk} P_{A alpha}
+ *                  with {I,K} a SET of sites: one term when K is I.
+ *   Eq. HFX_LRI /  the four pieces, one per placement of the two ABF centres
+ *   Eq. HFX_split  (A in {I,K}, B in {J,L}), each a partial ERI (Eq. partial_
+ *                  integrals) contracted with D_{K,L}.
+ * in the loop order of Algorithm 1 (pairs <I,J> outermost, K in N[I] and
+ * L in N[J] inside, four partial-ERI terms per (K,L)), each term evaluated in
+ * the C((VC)D) multiplication order the paper adopts (Appendix A, Table 1):
+ *   Y[alpha][j][l] = sum_beta V_AB[alpha][beta] cB[beta][j][l]
+ *   T[alpha][j][k] = sum_l    Y[alpha][j][l] D_KL[k][l]
+ *   Ht[i][j]       = sum_{alpha,k} cA[alpha][i][k] T[alpha][j][k]
+ * Y for A = I does not depend on K and is computed once per (J, L, B) entry
+ * (loop-invariant, same values).
+ *
+ * Readings where the paper is silent:
+ *  - sign: Sigma carries an overall minus sign and E_X = 1/2 sum D.Sigma;
+ *  - screening: a term survives iff S > theta with
+ *      S = (maxabs(C_A-side) * maxabs(C_B-side)) * (maxabs(V_AB) * maxabs(D_KL)),
+ *    multiplied in exactly that association in round-to-nearest FP64 (block
+ *    upper limits, Sec. III.B; strict ">" as in Algorithm 4);
+ *  - a block exists iff it was supplied; missing blocks are zero.
+ *
+ * Coefficient roles: cA[alpha][i][k] = C(I,K)[alpha][i][k] when A = I and
+ * C(K,I)[alpha][k][i] when A = K (K not I); cB likewise for (J, L).
+ *
+ * Accumulation of the terms into each Sigma element is Neumaier-compensated.
+ *
+ * Keys are (i, j, n1, n2, n3): the block between site (i, 0) and site (j, n).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+typedef struct { int32_t a, n[3]; } site_t;
+
+/* ---------------- key hash (open addressing) ---------------- */
+static uint64_t pack_key(int32_t i, int32_t j, int32_t n1, int32_t n2, int32_t n3) {
+  return ((uint64_t)(uint32_t)i << 44) | ((uint64_t)(uint32_t)j << 24) |
+         ((uint64_t)((n1 + 128) & 0xFF) << 16) | ((uint64_t)((n2 + 128) & 0xFF) << 8) |
+         (uint64_t)((n3 + 128) & 0xFF);
+}
+static uint64_t mix64(uint64_t x) {
+  x ^= x >> 30; x *= 0xbf58476d1ce4e5b9ULL;
+  x ^= x >> 27; x *= 0x94d049bb133111ebULL;
+  x ^= x >> 31; return x;
+}
+typedef struct { uint64_t *keys; int64_t *vals; uint64_t mask; int64_t count; } hmap_t;
+#define EMPTY_KEY (~0ULL)
+
+static void hm_init(hmap_t *h, int64_t expected) {
+  uint64_t cap = 16;
+  while (cap < (uint64_t)(expected * 2 + 16)) cap <<= 1;
+  h->keys = (uint64_t *)malloc(cap * sizeof(uint64_t));
+  h->vals = (int64_t *)malloc(cap * sizeof(int64_t));
+  for (uint64_t s = 0; s < cap; ++s) h->keys[s] = EMPTY_KEY;
+  h->mask = cap - 1;
+  h->count = 0;
+}
+static void hm_free(hmap_t *h) { free(h->keys); free(h->vals); }
+static void hm_grow(hmap_t *h);
+/* insert if absent; returns the value stored for the key */
+static int64_t hm_put(hmap_t *h, uint64_t k, int64_t v) {
+  if ((uint64_t)(h->count + 1) * 2 > h->mask + 1) hm_grow(h);
+  uint64_t s = mix64(k) & h->mask;
+  while (h->keys[s] != EMPTY_KEY) {
+    if (h->keys[s] == k) return h->vals[s];
+    s = (s + 1) & h->mask;
+  }
+  h->keys[s] = k; h->vals[s] = v; h->count++;
+  return v;
+}
+static void hm_grow(hmap_t *h) {
+  hmap_t n;
+  hm_init(&n, (int64_t)(h->mask + 1));
+  for (uint64_t s = 0; s <= h->mask; ++s)
+    if (h->keys[s] != EMPTY_KEY) hm_put(&n, h->keys[s], h->vals[s]);
+  hm_free(h);
+  *h = n;
+}
+static int64_t hm_get(const hmap_t *h, uint64_t k) {
+  uint64_t s = mix64(k) & h->mask;
+  while (h->keys[s] != EMPTY_KEY) {
+    if (h->keys[s] == k) return h->vals[s];
+    s = (s + 1) & h->mask;
+  }
+  return -1;
+}
+
+/* ---------------- block sets ---------------- */
+typedef struct {
+  int64_t n;
+  const int32_t *keys;   /* n x 5 */
+  const double *data;
+  const int64_t *offs;   /* n + 1 */
+  double *maxabs;        /* per block upper limit (Sec. III.B) */
+  hmap_t map;
+} bset_t;
+
+typedef struct { int32_t other, n[3]; int64_t blk; } nbr_t;
+
+typedef struct orc {
+  int32_t natoms;
+  int32_t *nao, *nabf;
+  bset_t C, V, D;
+  /* per atom x: C(x, y, n) blocks ("out") and C(y, x, m) blocks ("in") */
+  int64_t *cout_start, *cin_start;
+  nbr_t *cout, *cin;
+  /* per atom a: V(a, b, n) blocks */
+  int64_t *vout_start;
+  nbr_t *vout;
+} orc;
+
+static void bset_init(bset_t *b, int64_t n, const int32_t *keys, const double *data,
+                      const int64_t *offs) {
+  b->n = n; b->keys = keys; b->data = data; b->offs = offs;
+  b->maxabs = (double *)malloc((size_t)(n > 0 ? n : 1) * sizeof(double));
+  hm_init(&b->map, n);
+  for (int64_t e = 0; e < n; ++e) {
+    const int32_t *k = keys + 5 * e;
+    hm_put(&b->map, pack_key(k[0], k[1], k[2], k[3], k[4]), e);
+    double m = 0.0;
+    for (int64_t t = offs[e]; t < offs[e + 1]; ++t) {
+      double a = fabs(data[t]);
+      if (a > m) m = a;
+    }
+    b->maxabs[e] = m;
+  }
+}
+
+static int64_t bset_find(const bset_t *b, int32_t i, int32_t j, const int32_t n[3]) {
+  return hm_get(&b->map, pack_key(i, j, n[0], n[1], n[2]));
+}
+
+orc *orc_create(int32_t natoms, const int32_t *nao, const int32_t *nabf,
+                int64_t nC, const int32_t *kC, const double *dC, const int64_t *oC,
+                int64_t nV, const int32_t *kV, const double *dV, const int64_t *oV,
+                int64_t nD, const int32_t *kD, const double *dD, const int64_t *oD) {
+  orc *o = (orc *)calloc(1, sizeof(orc));
+  o->natoms = natoms;
+  o->nao = (int32_t *)malloc(sizeof(int32_t) * natoms);
+  o->nabf = (int32_t *)malloc(sizeof(int32_t) * natoms);
+  memcpy(o->nao, nao, sizeof(int32_t) * natoms);
+  memcpy(o->nabf, nabf, sizeof(int32_t) * natoms);
+  bset_init(&o->C, nC, kC, dC, oC);
+  bset_init(&o->V, nV, kV, dV, oV);
+  bset_init(&o->D, nD, kD, dD, oD);
+  /* neighbour lists from the C key set */
+  o->cout_start = (int64_t *)calloc(natoms + 1, sizeof(int64_t));
+  o->cin_start = (int64_t *)calloc(natoms + 1, sizeof(int64_t));
+  for (int64_t e = 0; e < nC; ++e) {
+    o->cout_start[kC[5 * e] + 1]++;
+    o->cin_start[kC[5 * e + 1] + 1]++;
+  }
+  for (int32_t a = 0; a < natoms; ++a) {
+    o->cout_start[a + 1] += o->cout_start[a];
+    o->cin_start[a + 1] += o->cin_start[a];
+  }
+  o->cout = (nbr_t *)malloc(sizeof(nbr_t) * (nC > 0 ? nC : 1));
+  o->cin = (nbr_t *)malloc(sizeof(nbr_t) * (nC > 0 ? nC : 1));
+  int64_t *fo = (int64_t *)malloc(sizeof(int64_t) * (natoms + 1));
+  int64_t *fi = (int64_t *)malloc(sizeof(int64_t) * (natoms + 1));
+  memcpy(fo, o->cout_start, sizeof(int64_t) * (natoms + 1));
+  memcpy(fi, o->cin_start, sizeof(int64_t) * (natoms + 1));
+  for (int64_t e = 0; e < nC; ++e) {
+    const int32_t *k = kC + 5 * e;
+    nbr_t *p = &o->cout[fo[k[0]]++];
+    p->other = k[1]; p->n[0] = k[2]; p->n[1] = k[3]; p->n[2] = k[4]; p->blk = e;
+    /* C(y, x, m): seen from x at cell 0, y sits at cell -m */
+    nbr_t *q = &o->cin[fi[k[1]]++];
+    q->other = k[0]; q->n[0] = -k[2]; q->n[1] = -k[3]; q->n[2] = -k[4]; q->blk = e;
+  }
+  free(fo); free(fi);
+  o->vout_start = (int64_t *)calloc(natoms + 1, sizeof(int64_t));
+  for (int64_t e = 0; e < nV; ++e) o->vout_start[kV[5 * e] + 1]++;
+  for (int32_t a = 0; a < natoms; ++a) o->vout_start[a + 1] += o->vout_start[a];
+  o->vout = (nbr_t *)malloc(sizeof(nbr_t) * (nV > 0 ? nV : 1));
+  int64_t *fv = (int64_t *)malloc(sizeof(int64_t) * (natoms + 1));
+  memcpy(fv, o->vout_start, sizeof(int64_t) * (natoms + 1));
+  for (int64_t e = 0; e < nV; ++e) {
+    const int32_t *k = kV + 5 * e;
+    nbr_t *p = &o->vout[fv[k[0]]++];
+    p->other = k[1]; p->n[0] = k[2]; p->n[1] = k[3]; p->n[2] = k[4]; p->blk = e;
+  }
+  free(fv);
+  return o;
+}
+
+void orc_destroy(orc *o) {
+  if (!o) return;
+  hm_free(&o->C.map); hm_free(&o->V.map); hm_free(&o->D.map);
+  free(o->C.maxabs); free(o->V.maxabs); free(o->D.maxabs);
+  free(o->cout_start); free(o->cin_start); free(o->cout); free(o->cin);
+  free(o->vout_start); free(o->vout);
+  free(o->nao); free(o->nabf); free(o);
+}
+
+/* One way an ABF centre is placed for an AO pair (X, Y), X the Sigma-side site:
+ * the partner site Y, the ABF site (X itself or Y), the C block and whether it
+ * is read transposed (ABFs on Y: C(Y,X)[alpha][y][x]). */
+typedef struct { site_t partner, abf; int64_t cblk; int transposed; } role_t;
+
+/* All (partner, ABF centre) entries for the Sigma-side site X = (x, nx):
+ * partner Y with C(X,Y) present -> ABF on X; Y != X with C(Y,X) present -> ABF on Y. */
+static int64_t roles_of(const orc *o, int32_t x, const int32_t nx[3], role_t **out) {
+  int64_t n_out = o->cout_start[x + 1] - o->cout_start[x];
+  int64_t n_in = o->cin_start[x + 1] - o->cin_start[x];
+  role_t *r = (role_t *)malloc(sizeof(role_t) * (size_t)(n_out + n_in + 1));
+  int64_t c = 0;
+  for (int64_t t = o->cout_start[x]; t < o->cout_start[x + 1]; ++t) {
+    const nbr_t *p = &o->cout[t];
+    role_t *e = &r[c++];
+    e->partner.a = p->other;
+    for (int d = 0; d < 3; ++d) e->partner.n[d] = nx[d] + p->n[d];
+    e->abf.a = x;
+    for (int d = 0; d < 3; ++d) e->abf.n[d] = nx[d];
+    e->cblk = p->blk; e->transposed = 0;
+  }
+  for (int64_t t = o->cin_start[x]; t < o->cin_start[x + 1]; ++t) {
+    const nbr_t *p = &o->cin[t];
+    int same = (p->other == x) && p->n[0] == 0 && p->n[1] == 0 && p->n[2] == 0;
+    if (same) continue; /* {X, Y} is one site: the single term is the ABF-on-X one */
+    role_t *e = &r[c++];
+    e->partner.a = p->other;
+    for (int d = 0; d < 3; ++d) e->partner.n[d] = nx[d] + p->n[d];
+    e->abf = e->partner;
+    e->cblk = p->blk; e->transposed = 1;
+  }
+  *out = r;
+  return c;
+}
+
+static int same_site(const site_t *a, const site_t *b) {
+  return a->a == b->a && a->n[0] == b->n[0] && a->n[1] == b->n[1] && a->n[2] == b->n[2];
+}
+
+/* Block between two sites: key (x, y, ny - nx). */
+static int64_t find_between(const bset_t *b, const site_t *x, const site_t *y) {
+  int32_t n[3] = {y->n[0] - x->n[0], y->n[1] - x->n[1], y->n[2] - x->n[2]};
+  return bset_find(b, x->a, y->a, n);
+}
+
+/* Screening quantity of one term, in the fixed association. */
+static double screen_S(const orc *o, const role_t *eK, const role_t *eL, int64_t v, int64_t d) {
+  double cc = o->C.maxabs[eK->cblk] * o->C.maxabs[eL->cblk];
+  double vd = o->V.maxabs[v] * o->D.maxabs[d];
+  return cc * vd;
+}
+
+/* variant index: 0 = ABFs on (I,J), 1 = (I,L), 2 = (K,J), 3 = (K,L) */
+static int variant_of(const role_t *eK, const role_t *eL) {
+  return (eK->transposed ? 2 : 0) + (eL->transposed ? 1 : 0);
+}
+
+static int cmp_u64(const void *x, const void *y) {
+  uint64_t a = *(const uint64_t *)x, b = *(const uint64_t *)y;
+  return (a > b) - (a < b);
+}
+void orc_sort_u64(uint64_t *v, int64_t n) { qsort(v, (size_t)n, sizeof(uint64_t), cmp_u64); }
+
+/*
+ * Enumerate the Sigma key set at theta: every (i, j, n) receiving at least one
+ * surviving term, and the number of surviving terms per variant.  Returns the
+ * number of keys; writes at most cap keys (sorted) when keys_out is non-null.
+ */
+int64_t orc_keys(orc *o, double theta, int32_t *keys_out, int64_t cap, int64_t counts[4]) {
+  hmap_t keyset;
+  hm_init(&keyset, 1024);
+  int64_t cnt[4] = {0, 0, 0, 0};
+  for (int32_t i = 0; i < o->natoms; ++i) {
+    int32_t zero[3] = {0, 0, 0};
+    role_t *KI;
+    int64_t nK = roles_of(o, i, zero, &KI);
+    for (int64_t a = 0; a < nK; ++a) {
+      const role_t *eK = &KI[a];
+      const site_t *A = &eK->abf, *K = &eK->partner;
+      /* B: every site with V(A, B) */
+      for (int64_t tv = o->vout_start[A->a]; tv < o->vout_start[A->a + 1]; ++tv) {
+        const nbr_t *pv = &o->vout[tv];
+        const int64_t vb = pv->blk;
+        site_t B = {pv->other, {A->n[0] + pv->n[0], A->n[1] + pv->n[1], A->n[2] + pv->n[2]}};
+        const int64_t dKB = find_between(&o->D, K, &B);
+        /* every C(B, Y) block: either J = B with L = Y (ABFs on J), or L = B with
+         * J = Y != B (ABFs on L) */
+        for (int64_t t = o->cout_start[B.a]; t < o->cout_start[B.a + 1]; ++t) {
+          const nbr_t *p = &o->cout[t];
+          site_t Y = {p->other, {B.n[0] + p->n[0], B.n[1] + p->n[1], B.n[2] + p->n[2]}};
+          role_t eL;
+          /* J = B, L = Y */
+          int64_t d = find_between(&o->D, K, &Y);
+          if (d >= 0) {
+            eL.partner = Y; eL.abf = B; eL.cblk = p->blk; eL.transposed = 0;
+            if (screen_S(o, eK, &eL, vb, d) > theta) {
+              cnt[variant_of(eK, &eL)]++;
+              hm_put(&keyset, pack_key(i, B.a, B.n[0], B.n[1], B.n[2]), 0);
+            }
+          }
+          /* L = B, J = Y */
+          if (dKB >= 0 && !same_site(&Y, &B)) {
+            eL.partner = B; eL.abf = B; eL.cblk = p->blk; eL.transposed = 1;
+            if (screen_S(o, eK, &eL, vb, dKB) > theta) {
+              cnt[variant_of(eK, &eL)]++;
+              hm_put(&keyset, pack_key(i, Y.a, Y.n[0], Y.n[1], Y.n[2]), 0);
+            }
+          }
+        }
+      }
+    }
+    free(KI);
+  }
+  /* collect and sort keys; the +128 offsets make the packed order (i, j, n1, n2, n3) */
+  int64_t nk = keyset.count;
+  uint64_t *ks = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nk > 0 ? nk : 1));
+  int64_t c = 0;
+  for (uint64_t s = 0; s <= keyset.mask; ++s)
+    if (keyset.keys[s] != EMPTY_KEY) ks[c++] = keyset.keys[s];
+  orc_sort_u64(ks, nk);
+  if (keys_out) {
+    for (int64_t e = 0; e < nk && e < cap; ++e) {
+      uint64_t k = ks[e];
+      keys_out[5 * e + 0] = (int32_t)(k >> 44);
+      keys_out[5 * e + 1] = (int32_t)((k >> 24) & 0xFFFFF);
+      keys_out[5 * e + 2] = (int32_t)((k >> 16) & 0xFF) - 128;
+      keys_out[5 * e + 3] = (int32_t)((k >> 8) & 0xFF) - 128;
+      keys_out[5 * e + 4] = (int32_t)(k & 0xFF) - 128;
+    }
+  }
+  if (counts) for (int v = 0; v < 4; ++v) counts[v] = cnt[v];
+  free(ks);
+  hm_free(&keyset);
+  return nk;
+}
+
+
+/* Neumaier-compensated accumulation. */
+static void kahan_add(double *s, double *c, double x) {
+  double t = *s + x;
+  if (fabs(*s) >= fabs(x)) *c += (*s - t) + x;
+  else *c += (x - t) + *s;
+  *s = t;
+}
+
+/* Copy an entry's coefficients into cbuf[alpha][x][y] (x on the Sigma-side
+ * site, y on its partner): the C block straight, or transposed in its AO pair. */
+static void load_coef(const orc *o, const role_t *e, int nx, int ny, int np, double *cbuf) {
+  const double *b = o->C.data + o->C.offs[e->cblk];
+  if (!e->transposed) {
+    memcpy(cbuf, b, sizeof(double) * (size_t)np * nx * ny);
+    return;
+  }
+  for (int al = 0; al < np; ++al)
+    for (int x = 0; x < nx; ++x)
+      for (int y = 0; y < ny; ++y)
+        cbuf[((int64_t)al * nx + x) * ny + y] = b[((int64_t)al * ny + y) * nx + x];
+}
+
+enum { MAXAO = 64, MAXABF = 128, SLAB = MAXABF * MAXAO * MAXAO };
+
+/*
+ * Sigma block (I, J) for I = (i, 0), J = (j, n): Algorithm 1 for one pair.
+ * out has nao(i) * nao(j) doubles (row-major [i][j]).
+ */
+static void sigma_block(const orc *o, double theta, int32_t i, int32_t j, const int32_t nJ[3],
+                        double *out, double *work) {
+  const int ni = o->nao[i], nj = o->nao[j];
+  int32_t zero[3] = {0, 0, 0};
+  role_t *KI, *LJ;
+  int64_t nK = roles_of(o, i, zero, &KI);
+  int64_t nL = roles_of(o, j, nJ, &LJ);
+  double *acc = work;                 /* [i][j] running sum */
+  double *cmp = acc + MAXAO * MAXAO;  /* compensation */
+  double *cB = cmp + MAXAO * MAXAO;   /* [beta][j][l] */
+  double *cA = cB + SLAB;             /* [alpha][i][k] */
+  double *Y = cA + SLAB;              /* [alpha][j][l] */
+  double *YI = Y + SLAB;              /* Y for A = I */
+  double *T = YI + SLAB;              /* [alpha][j][k] */
+  for (int t = 0; t < ni * nj; ++t) { acc[t] = 0.0; cmp[t] = 0.0; }
+  site_t I = {i, {0, 0, 0}};
+  for (int64_t b = 0; b < nL; ++b) {
+    const role_t *eL = &LJ[b];
+    const site_t *L = &eL->partner, *B = &eL->abf;
+    const int nl = o->nao[L->a];
+    const int pB = o->nabf[B->a];
+    int yi_ready = 0, cb_ready = 0;
+    for (int64_t a = 0; a < nK; ++a) {
+      const role_t *eK = &KI[a];
+      const site_t *K = &eK->partner, *A = &eK->abf;
+      const int64_t d = find_between(&o->D, K, L);
+      if (d < 0) continue;
+      const int64_t v = find_between(&o->V, A, B);
+      if (v < 0) continue;
+      if (!(screen_S(o, eK, eL, v, d) > theta)) continue;
+      const int nk = o->nao[K->a];
+      const int pA = o->nabf[A->a];
+      const double *Vb = o->V.data + o->V.offs[v];
+      const double *Db = o->D.data + o->D.offs[d];
+      if (!cb_ready) { load_coef(o, eL, nj, nl, pB, cB); cb_ready = 1; }
+      /* Y[alpha][j][l] = sum_beta V_AB[alpha][beta] cB[beta][j][l] */
+      double *Yuse;
+      const int a_is_I = same_site(A, &I);
+      if (a_is_I && yi_ready) {
+        Yuse = YI;
+      } else {
+        Yuse = a_is_I ? YI : Y;
+        const int njl = nj * nl;
+        for (int al = 0; al < pA; ++al) {
+          double *y = Yuse + (int64_t)al * njl;
+          for (int t = 0; t < njl; ++t) y[t] = 0.0;
+          for (int be = 0; be < pB; ++be) {
+            const double w = Vb[(int64_t)al * pB + be];
+            const double *c = cB + (int64_t)be * njl;
+            for (int t = 0; t < njl; ++t) y[t] += w * c[t];
+          }
+        }
+        if (a_is_I) yi_ready = 1;
+      }
+      /* T[alpha][j][k] = sum_l Y[alpha][j][l] D_KL[k][l] */
+      for (int al = 0; al < pA; ++al)
+        for (int jj = 0; jj < nj; ++jj) {
+          const double *y = Yuse + ((int64_t)al * nj + jj) * nl;
+          for (int kk = 0; kk < nk; ++kk) {
+            const double *dk = Db + (int64_t)kk * nl;
+            double s = 0.0;
+            for (int ll = 0; ll < nl; ++ll) s += y[ll] * dk[ll];
+            T[((int64_t)al * nj + jj) * nk + kk] = s;
+          }
+        }
+      /* Ht[i][j] = sum_{alpha,k} cA[alpha][i][k] T[alpha][j][k];  Sigma -= Ht */
+      load_coef(o, eK, ni, nk, pA, cA);
+      for (int ii = 0; ii < ni; ++ii)
+        for (int jj = 0; jj < nj; ++jj) {
+          double s = 0.0;
+          for (int al = 0; al < pA; ++al) {
+            const double *ca = cA + ((int64_t)al * ni + ii) * nk;
+            const double *tt = T + ((int64_t)al * nj + jj) * nk;
+            for (int kk = 0; kk < nk; ++kk) s += ca[kk] * tt[kk];
+          }
+          kahan_add(&acc[ii * nj + jj], &cmp[ii * nj + jj], -s);
+        }
+    }
+  }
+  for (int t = 0; t < ni * nj; ++t) out[t] = acc[t] + cmp[t];
+  free(KI);
+  free(LJ);
+}
+
+/* Work buffer size (doubles) per thread for sigma_block. */
+static int64_t work_doubles(void) { return 2 * MAXAO * MAXAO + 5 * (int64_t)SLAB; }
+
+/*
+ * Compute the requested Sigma blocks.  req_keys: nreq x 5 (i, j, n1, n2, n3)
+ * with arbitrary (i, j, n); out_offs: nreq + 1 offsets into out (filled here).
+ * nthreads <= 0 uses the OpenMP default.  Returns 0, or -1 on a size the
+ * oracle's work buffers do not cover (nao > 64 or nabf > 128).
+ */
+int orc_blocks(orc *o, double theta, int64_t nreq, const int32_t *req_keys, double *out,
+               int64_t *out_offs, int nthreads) {
+  for (int32_t a = 0; a < o->natoms; ++a)
+    if (o->nao[a] > MAXAO || o->nabf[a] > MAXABF) return -1;
+  out_offs[0] = 0;
+  for (int64_t r = 0; r < nreq; ++r)
+    out_offs[r + 1] = out_offs[r] + (int64_t)o->nao[req_keys[5 * r]] * o->nao[req_keys[5 * r + 1]];
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel
+  {
+    double *work = (double *)malloc(sizeof(double) * (size_t)work_doubles());
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t r = 0; r < nreq; ++r) {
+      const int32_t *k = req_keys + 5 * r;
+      int32_t n[3] = {k[2], k[3], k[4]};
+      sigma_block(o, theta, k[0], k[1], n, out + out_offs[r], work);
+    }
+    free(work);
+  }
+  return 0;
+}
+
+/*
+ * E_X = 1/2 sum over Sigma keys that are also D keys of sum_ij D[i][j] Sigma[i][j]
+ * (Algorithm 5, "Calculate E^X"), summed in key order, compensated.
+ */
+double orc_ex(orc *o, int64_t nkeys, const int32_t *keys, const double *sig, const int64_t *offs) {
+  double s = 0.0, c = 0.0;
+  for (int64_t e = 0; e < nkeys; ++e) {
+    const int32_t *k = keys + 5 * e;
+    int32_t n[3] = {k[2], k[3], k[4]};
+    int64_t d = bset_find(&o->D, k[0], k[1], n);
+    if (d < 0) continue;
+    const double *Db = o->D.data + o->D.offs[d];
+    int64_t len = offs[e + 1] - offs[e];
+    for (int64_t t = 0; t < len; ++t) kahan_add(&s, &c, Db[t] * sig[offs[e] + t]);
+  }
+  return 0.5 * (s + c);
+}
+
+/* Block upper limits as computed here (exposed for tests). */
+void orc_maxabs(orc *o, char which, double *out) {
+  const bset_t *b = which == 'C' ? &o->C : which == 'V' ? &o->V : &o->D;
+  memcpy(out, b->maxabs, sizeof(double) * (size_t)b->n);
+}
