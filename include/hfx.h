@@ -1,0 +1,201 @@
+/*
+ * libhfx -- screened, linear-scaling periodic Hartree-Fock exchange build under
+ * localized resolution of the identity (LRI), for one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Lin, Ren and He, arXiv:2009.12505 (linear-scaling periodic exchange
+ * with numerical atomic orbitals and LRI).  The library computes
+ *
+ *   Sigma_{Ii,Jj} = - sum_{K,L} sum_{k,l} sum_{A in {I,K}} sum_{B in {J,L}}
+ *                     sum_{alpha,beta} C^{A alpha}_{Ii,Kk} V_{A alpha,B beta}
+ *                     C^{B beta}_{Jj,Ll} D_{Kk,Ll}                (Eq. HFX_LRI)
+ *
+ * built in the <A,B>-pair loop of Algorithm 2/3 with the C((VC)D)
+ * multiplication order (Appendix A), screened per term by block upper limits
+ * (Sec. III.B/III.C), and E_X = 1/2 sum D . Sigma (Algorithm 5).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Sites.  A site is (atom a in [0, natoms), lattice vector n in Z^3) (Eq. AO).
+ * Block keys are (i, j, n1, n2, n3): the block between site (i, 0) and site
+ * (j, n).  |n_k| <= 127.
+ *
+ * Block shapes, row-major FP64:
+ *   C key (a, f, n): [nabf(a)][nao(a)][nao(f)]  -- ABFs on a (Eq. LRI)
+ *   V key (a, b, n): [nabf(a)][nabf(b)]         -- (P_a alpha | P_b beta)
+ *   D key (k, l, n): [nao(k)][nao(l)]           -- real-space density matrix
+ *   Sigma key (i, j, n): [nao(i)][nao(j)]       -- exchange matrix, Ha
+ * A block exists iff it was set; the library never infers symmetric partners
+ * and never recomputes distances.  Setting a key again replaces it.
+ *
+ * Screening.  A term (A, B, F, G, variant) survives iff
+ *   S = (max|C_AF| * max|C_BG|) * (max|V_AB| * max|D_src|) > theta,
+ * multiplied in exactly that association in round-to-nearest FP64, where D_src
+ * is the density block the variant contracts with (D_FG, D_FB, D_AG or D_AB).
+ * When F is the same site as A (or G as B) the pieces with ABFs on F (or G)
+ * are the same term as the ABF-on-A (B) piece and are not added again.
+ * The Sigma key set is exactly the keys receiving at least one surviving term.
+ *
+ * Precision modes (hfx_prec):
+ *   HFX_FP64   -- every contraction in FP64 on CUDA cores;
+ *   HFX_BF16X3 -- contractions as three BF16 products with FP32 accumulation
+ *                 (about FP32 accuracy);
+ *   HFX_OZAKI  -- contractions as exact products of nslices BF16 slices per
+ *                 operand on the tensor cores, recombined in FP64.
+ * Sigma accumulation and E_X are FP64 and deterministic (bitwise run to run)
+ * in every mode.
+ *
+ * Ownership.  hfx_set_* copy the caller's data (host pointers) or read device
+ * pointers on the context's stream before returning; the caller may free or
+ * reuse its buffers afterwards.  The context owns all device memory it
+ * allocates.  Outputs go to caller buffers.  A context is used by one host
+ * thread at a time.
+ *
+ * Errors.  Every call returns a status and never aborts, traps or exits.
+ * hfx_last_error() gives a message for the last failing call on a context.
+ * Device-side waits are bounded; expiry returns HFX_E_TIMEOUT.
+ */
+#ifndef HFX_H
+#define HFX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hfx_ctx hfx_ctx;
+
+typedef enum {
+  HFX_OK = 0,
+  HFX_E_ARG = 1,      /* bad argument: null pointer, out-of-range index, NaN/Inf data */
+  HFX_E_SHAPE = 2,    /* sizes inconsistent with nao/nabf */
+  HFX_E_STATE = 3,    /* call out of order (e.g. results requested before a build) */
+  HFX_E_NOMEM = 4,    /* host or device allocation failed */
+  HFX_E_CUDA = 5,     /* a CUDA runtime call or kernel failed */
+  HFX_E_TIMEOUT = 6,  /* a bounded device wait expired */
+  HFX_E_NOTFOUND = 7  /* key not present */
+} hfx_status;
+
+typedef enum { HFX_FP64 = 0, HFX_BF16X3 = 1, HFX_OZAKI = 2 } hfx_prec;
+
+/*
+ * Create a context for one periodic system (Sec. II, Eq. AO).
+ *   lattice   9 doubles, rows a1, a2, a3 in bohr (recorded; not used to infer blocks)
+ *   natoms    number of atoms in the unit cell, >= 1
+ *   pos       natoms x 3 Cartesian positions in bohr (recorded), may be NULL
+ *   species   natoms species indices in [0, nspecies)
+ *   nao/nabf  nspecies NAO and ABF counts per species, 1..64 NAOs, 1..256 ABFs
+ *   cuda_stream  cudaStream_t all device work is ordered on; NULL = legacy default
+ *   out       receives the context
+ * Errors: HFX_E_ARG, HFX_E_NOMEM, HFX_E_CUDA (no usable sm_103 device).
+ */
+hfx_status hfx_create(const double lattice[9], int32_t natoms, const double *pos,
+                      const int32_t *species, int32_t nspecies, const int32_t *nao,
+                      const int32_t *nabf, void *cuda_stream, hfx_ctx **out);
+
+/*
+ * Set one LRI coefficient block C(a, f, n) (Eq. LRI; Sec. III.B "supermatrix
+ * C_{A,F} of dense rank-3 blocks").  blk: [nabf(a)][nao(a)][nao(f)] host FP64.
+ * Errors: HFX_E_ARG (index, NaN/Inf), HFX_E_NOMEM.
+ */
+hfx_status hfx_set_C(hfx_ctx *ctx, int32_t a, int32_t f, const int32_t n[3], const double *blk);
+
+/* Set one Coulomb block V(a, b, n) = (P_a | P_b) (Sec. III.B.2); [nabf(a)][nabf(b)]. */
+hfx_status hfx_set_V(hfx_ctx *ctx, int32_t a, int32_t b, const int32_t n[3], const double *blk);
+
+/* Set one density-matrix block D(k, l, n) (Eq. DM_realspace); [nao(k)][nao(l)]. */
+hfx_status hfx_set_D(hfx_ctx *ctx, int32_t k, int32_t l, const int32_t n[3], const double *blk);
+
+/*
+ * Bulk form of hfx_set_C/V/D.  which: 'C', 'V' or 'D'.
+ *   keys  nblk x 5 int32 (i, j, n1, n2, n3), HOST memory
+ *   data  packed blocks, block e at data[offs[e] .. offs[e+1]); host or device
+ *   offs  nblk + 1 int64 offsets in doubles, HOST memory; offs[e+1]-offs[e]
+ *         must equal the block's shape
+ *   on_device  0: data is host memory; 1: data is device memory on this GPU
+ * Replaces any existing blocks with the same keys.
+ * Errors: HFX_E_ARG, HFX_E_SHAPE, HFX_E_NOMEM, HFX_E_CUDA.
+ */
+hfx_status hfx_set_many(hfx_ctx *ctx, char which, int64_t nblk, const int32_t *keys,
+                        const double *data, const int64_t *offs, int on_device);
+
+/* Remove every block of one kind ('C', 'V', 'D'). */
+hfx_status hfx_clear(hfx_ctx *ctx, char which);
+
+/*
+ * Build Sigma and E_X (Algorithm 5 "Calculate exact-exchange": screen, then
+ * the staged C((VC)D) contractions of Algorithm 3, then E_X).
+ *   theta    screening threshold (>= 0; 0 keeps every term with non-zero blocks)
+ *   prec     contraction precision (see above)
+ *   nslices  BF16 slices per operand for HFX_OZAKI (2..8); ignored otherwise
+ *   ex_out   receives E_X in Ha (host pointer), may be NULL
+ * Errors: HFX_E_STATE (no C, V or D set), HFX_E_ARG, HFX_E_NOMEM, HFX_E_CUDA,
+ *         HFX_E_TIMEOUT.
+ */
+hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices, double *ex_out);
+
+/* Number of Sigma blocks of the last build.  HFX_E_STATE if inputs changed since. */
+hfx_status hfx_H_count(const hfx_ctx *ctx, int64_t *nblk);
+
+/* Sigma keys of the last build, nblk x 5 int32, sorted by (i, j, n1, n2, n3). */
+hfx_status hfx_H_keys(const hfx_ctx *ctx, int32_t *keys);
+
+/* Offsets (nblk + 1 int64, in doubles) of the blocks in hfx_get_H_all's layout. */
+hfx_status hfx_H_offsets(const hfx_ctx *ctx, int64_t *offs);
+
+/*
+ * One Sigma block (i, j, n) of the last build into out[nao(i)][nao(j)] (host).
+ * Errors: HFX_E_STATE, HFX_E_NOTFOUND (key not in the Sigma key set).
+ */
+hfx_status hfx_get_H(const hfx_ctx *ctx, int32_t i, int32_t j, const int32_t n[3], double *out);
+
+/*
+ * Every Sigma block, packed in key order at hfx_H_offsets, into out.
+ * on_device 0: out is host memory; 1: device memory on this GPU.
+ */
+hfx_status hfx_get_H_all(const hfx_ctx *ctx, double *out, int on_device);
+
+/*
+ * Adjoint of the last build with its surviving-term set frozen:
+ *   dC receives dE_X/dC packed like the C blocks in key-sorted order
+ *   dV receives dE_X/dV packed like the V blocks in key-sorted order
+ * (host pointers; either may be NULL).  HFX_E_STATE before a build.
+ */
+hfx_status hfx_grad(hfx_ctx *ctx, double *dC, double *dV);
+
+/* Statistics of the last build (layout: struct hfx_stats_v1 below). */
+typedef struct {
+  int32_t version;          /* 1 */
+  int32_t prec;
+  double theta;
+  int64_t n_sigma_blocks;
+  int64_t n_work_items;     /* <A,B> pairs */
+  int64_t n_active_abg;     /* (A,B,G) triples with >= 1 surviving term */
+  int64_t survivors[4];     /* surviving terms per variant: ABFs on (I,J),(I,L),(K,J),(K,L) */
+  double canonical_flops;   /* Algorithm 3 count: 2 nP(A)nP(B)nao(B)nao(G) per active (A,B,G)
+                               + 4 nP(A) x (product of the three AO sizes) per surviving term */
+  double executed_flops;    /* multiply-adds x 2 actually issued by this build's kernels */
+  double ms_screen, ms_contract, ms_reduce, ms_total;
+  int64_t n_waves;
+  int64_t scratch_bytes;
+  /* per kernel, summed over waves, CUDA events on the context's stream:
+     [0] screen, [1] Y = V C, [2] D-stage (P, T3), [3] Q = C D, [4] D_FG piece,
+     [5] D_AG piece, [6] D_FB piece, [7] D_AB piece */
+  double kernel_ms[8];
+  double kernel_flops[8];   /* multiply-adds x 2 issued by each kernel */
+  int64_t n_launches;       /* kernels this build launched */
+} hfx_stats_v1;
+
+hfx_status hfx_stats(const hfx_ctx *ctx, void *stats);
+
+/* Message for the last failing call on ctx (never NULL; "" when none). */
+const char *hfx_last_error(const hfx_ctx *ctx);
+
+/* Free the context and all device memory it owns.  NULL is allowed. */
+void hfx_destroy(hfx_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HFX_H */

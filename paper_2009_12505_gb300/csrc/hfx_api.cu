@@ -1,0 +1,889 @@
+// libhfx C ABI: context, block registry, planning and the build driver.
+//
+// Build (Algorithm 5, "Calculate exact-exchange"):
+//   1. pack the set blocks of each kind into one key-sorted device array and
+//      take every block's upper limit max|x| (Sec. III.B);
+//   2. plan: neighbour lists N[x] from the C keys, one work item per V block
+//      <A,B> with A in the home cell (Algorithm 2/3 loop over <A,B>);
+//   3. screen every (A,B,G) x F x variant with the block-norm product and
+//      collect the Sigma key set (Sec. III.C, Algorithm 4 level 1);
+//   4. contract the survivors in waves of work items sized to the scratch
+//      budget (Algorithm 3, C((VC)D) order);
+//   5. convert the fixed-point Sigma accumulators to FP64 and reduce E_X.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "hfx_internal.h"
+
+namespace {
+
+template <class T>
+struct DevBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf &) = delete;
+  DevBuf &operator=(const DevBuf &) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  // grow-only; contents are not preserved
+  cudaError_t reserve(size_t count) {
+    if (count <= n && p) return cudaSuccess;
+    release();
+    const size_t c = count > 0 ? count : 1;
+    cudaError_t e = cudaMalloc((void **)&p, c * sizeof(T));
+    if (e != cudaSuccess) { p = nullptr; n = 0; return e; }
+    n = c;
+    return cudaSuccess;
+  }
+};
+
+struct Entry {
+  int32_t chunk;   // -1: host pending buffer
+  int64_t off;
+  int64_t len;
+};
+
+struct Chunk {
+  double *dev = nullptr;
+  size_t n = 0;
+};
+
+struct Kind {
+  char name = '?';
+  std::unordered_map<uint64_t, Entry> map;
+  std::vector<Chunk> chunks;
+  std::vector<double> pending;
+  bool dirty = true;         // data or keys changed since the last pack
+  bool keys_changed = true;  // key set changed since the last plan
+  std::vector<uint64_t> keys;   // sorted, valid after pack
+  std::vector<int64_t> offs;    // n + 1
+  DevBuf<double> data;
+  DevBuf<int64_t> d_offs;
+  DevBuf<double> maxabs;
+  bool data_is_chunk = false;   // data.p aliases chunks[0]
+
+  ~Kind() { free_chunks(); }
+  void free_chunks() {
+    for (auto &c : chunks) {
+      if (c.dev && !(data_is_chunk && c.dev == data.p)) cudaFree(c.dev);
+    }
+    chunks.clear();
+  }
+};
+
+}  // namespace
+
+struct hfx_ctx {
+  int32_t natoms = 0;
+  std::vector<int32_t> nao, nabf;
+  double lattice[9] = {0};
+  std::vector<double> pos;
+  cudaStream_t stream = nullptr;
+  Kind K[3];  // C, V, D
+  std::string err;
+
+  // plan (depends on the C and V key sets; dab on the D key set)
+  bool plan_valid = false;
+  std::vector<NbrEntry> nbr;
+  std::vector<int64_t> nc_start;
+  std::vector<int64_t> aotot;   // sum of nao over each atom's neighbour list
+  std::vector<WorkItem> items;
+  int64_t nwg = 0, nwf = 0, nmask = 0;
+  DevBuf<NbrEntry> d_nbr;
+  DevBuf<WorkItem> d_items;
+  DevBuf<int32_t> d_nao, d_nabf;
+  std::unordered_map<uint64_t, int64_t> dindex;
+  DevBuf<uint64_t> d_dhkeys;
+  DevBuf<int64_t> d_dhvals;
+  uint64_t dmask = 0;
+
+  // screen
+  DevBuf<uint32_t> d_masks;
+  DevBuf<uint8_t> d_wg;
+  DevBuf<uint32_t> d_wf;
+  DevBuf<unsigned long long> d_stab;
+  uint64_t stab_cap = 0;
+  DevBuf<unsigned long long> d_counters;
+  DevBuf<unsigned> d_err;
+  DevBuf<unsigned long long> d_collect;
+
+  // Sigma
+  std::vector<uint64_t> sig_keys;
+  std::vector<int64_t> sig_offs;
+  DevBuf<uint64_t> d_skeys;
+  DevBuf<int64_t> d_soffs;
+  DevBuf<uint64_t> d_shkeys;
+  DevBuf<int64_t> d_shvals;
+  uint64_t smask = 0;
+  DevBuf<unsigned long long> d_acc;
+  DevBuf<double> d_sigma;
+  DevBuf<double> d_partials;
+  DevBuf<double> d_ex;
+
+  // scratch
+  DevBuf<double> d_scratch;
+  DevBuf<int64_t> d_waveoffs;
+
+  bool results_valid = false;
+  double ex = 0.0;
+  hfx_stats_v1 stats{};
+  cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t kev[10] = {nullptr};  // per-kernel marks
+  int64_t launches = 0;
+};
+
+namespace {
+
+hfx_status fail(hfx_ctx *c, hfx_status s, const std::string &msg) {
+  if (c) c->err = msg;
+  return s;
+}
+hfx_status fail_cuda(hfx_ctx *c, const char *what, cudaError_t e) {
+  return fail(c, HFX_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                                   \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return fail_cuda(ctx, #call, e_);       \
+  } while (0)
+
+int kind_index(char w) { return w == 'C' ? 0 : w == 'V' ? 1 : w == 'D' ? 2 : -1; }
+
+int64_t block_len(const hfx_ctx *ctx, int k, int i, int j) {
+  if (k == 0) return (int64_t)ctx->nabf[i] * ctx->nao[i] * ctx->nao[j];
+  if (k == 1) return (int64_t)ctx->nabf[i] * ctx->nabf[j];
+  return (int64_t)ctx->nao[i] * ctx->nao[j];
+}
+
+bool key_ok(const hfx_ctx *ctx, const int32_t *k) {
+  if (k[0] < 0 || k[0] >= ctx->natoms || k[1] < 0 || k[1] >= ctx->natoms) return false;
+  for (int d = 2; d < 5; ++d)
+    if (k[d] < -127 || k[d] > 127) return false;
+  return true;
+}
+
+void invalidate(hfx_ctx *ctx, int k, bool keys) {
+  ctx->K[k].dirty = true;
+  if (keys) ctx->K[k].keys_changed = true;
+  ctx->results_valid = false;
+}
+
+uint64_t pow2_at_least(uint64_t x) {
+  uint64_t c = 16;
+  while (c < x) c <<= 1;
+  return c;
+}
+
+// Host-built open-addressing table (same probe sequence as dh_find).
+void build_table(const std::vector<uint64_t> &keys, const std::vector<int64_t> &vals,
+                 std::vector<uint64_t> &tk, std::vector<int64_t> &tv, uint64_t &mask) {
+  const uint64_t cap = pow2_at_least(2 * keys.size() + 16);
+  tk.assign(cap, HK_EMPTY);
+  tv.assign(cap, -1);
+  mask = cap - 1;
+  for (size_t e = 0; e < keys.size(); ++e) {
+    uint64_t s = hk_mix(keys[e]) & mask;
+    while (tk[s] != HK_EMPTY) s = (s + 1) & mask;
+    tk[s] = keys[e];
+    tv[s] = vals[e];
+  }
+}
+
+// Pack one kind into a key-sorted device array and compute block upper limits.
+hfx_status pack_kind(hfx_ctx *ctx, int k) {
+  Kind &K = ctx->K[k];
+  if (!K.dirty) return HFX_OK;
+  cudaStream_t st = ctx->stream;
+  // flush host-side single-block sets
+  if (!K.pending.empty()) {
+    Chunk c;
+    c.n = K.pending.size();
+    CK(cudaMalloc((void **)&c.dev, c.n * sizeof(double)));
+    CK(cudaMemcpyAsync(c.dev, K.pending.data(), c.n * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    const int32_t id = (int32_t)K.chunks.size();
+    K.chunks.push_back(c);
+    for (auto &kv : K.map)
+      if (kv.second.chunk < 0) kv.second.chunk = id;
+    K.pending.clear();
+    K.pending.shrink_to_fit();
+  }
+  const int64_t nblk = (int64_t)K.map.size();
+  K.keys.clear();
+  K.keys.reserve(nblk);
+  for (auto &kv : K.map) K.keys.push_back(kv.first);
+  std::sort(K.keys.begin(), K.keys.end());
+  K.offs.assign(nblk + 1, 0);
+  for (int64_t e = 0; e < nblk; ++e) K.offs[e + 1] = K.offs[e] + K.map[K.keys[e]].len;
+  const int64_t total = K.offs[nblk];
+  // fast path: one chunk that already holds exactly this packing
+  bool adopt = K.chunks.size() == 1 && K.chunks[0].n == (size_t)total;
+  for (int64_t e = 0; adopt && e < nblk; ++e) {
+    const Entry &en = K.map[K.keys[e]];
+    adopt = en.chunk == 0 && en.off == K.offs[e];
+  }
+  if (adopt) {
+    if (!K.data_is_chunk) K.data.release();
+    K.data.p = K.chunks[0].dev;
+    K.data.n = K.chunks[0].n;
+    K.data_is_chunk = true;
+  } else {
+    double *dst = nullptr;
+    CK(cudaMalloc((void **)&dst, (size_t)(total > 0 ? total : 1) * sizeof(double)));
+    std::vector<const double *> src(nblk);
+    std::vector<int64_t> doff(nblk), len(nblk);
+    for (int64_t e = 0; e < nblk; ++e) {
+      const Entry &en = K.map[K.keys[e]];
+      const double *base = en.chunk >= 0 ? K.chunks[en.chunk].dev
+                                         : (K.data_is_chunk ? K.data.p : K.data.p);
+      src[e] = base + en.off;
+      doff[e] = K.offs[e];
+      len[e] = en.len;
+    }
+    const double **d_src = nullptr;
+    int64_t *d_doff = nullptr, *d_len = nullptr;
+    CK(cudaMalloc((void **)&d_src, sizeof(double *) * (nblk > 0 ? nblk : 1)));
+    CK(cudaMalloc((void **)&d_doff, sizeof(int64_t) * (nblk > 0 ? nblk : 1)));
+    CK(cudaMalloc((void **)&d_len, sizeof(int64_t) * (nblk > 0 ? nblk : 1)));
+    CK(cudaMemcpyAsync(d_src, src.data(), sizeof(double *) * nblk, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_doff, doff.data(), sizeof(int64_t) * nblk, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(d_len, len.data(), sizeof(int64_t) * nblk, cudaMemcpyHostToDevice, st));
+    CK(launch_gather(d_src, d_doff, d_len, nblk, dst, st));
+    ctx->launches += nblk > 0;
+    CK(cudaStreamSynchronize(st));
+    cudaFree(d_src);
+    cudaFree(d_doff);
+    cudaFree(d_len);
+    // the packed array becomes the only chunk
+    double *old_data = K.data_is_chunk ? nullptr : K.data.p;
+    K.data.p = nullptr;
+    K.data.n = 0;
+    if (old_data) cudaFree(old_data);
+    K.data_is_chunk = false;
+    K.free_chunks();
+    Chunk c;
+    c.dev = dst;
+    c.n = (size_t)total;
+    K.chunks.push_back(c);
+    K.data.p = dst;
+    K.data.n = (size_t)total;
+    K.data_is_chunk = true;
+  }
+  for (int64_t e = 0; e < nblk; ++e) {
+    Entry &en = K.map[K.keys[e]];
+    en.chunk = 0;
+    en.off = K.offs[e];
+  }
+  CK(K.d_offs.reserve(nblk + 1));
+  CK(cudaMemcpyAsync(K.d_offs.p, K.offs.data(), sizeof(int64_t) * (nblk + 1),
+                     cudaMemcpyHostToDevice, st));
+  CK(K.maxabs.reserve(nblk));
+  CK(launch_maxabs(K.data.p, K.d_offs.p, nblk, K.maxabs.p, ctx->d_err.p, st));
+  ctx->launches += nblk > 0;
+  K.dirty = false;
+  return HFX_OK;
+}
+
+// Neighbour lists and work items from the C and V key sets; D lookups.
+hfx_status build_plan(hfx_ctx *ctx) {
+  Kind &C = ctx->K[0], &V = ctx->K[1], &D = ctx->K[2];
+  cudaStream_t st = ctx->stream;
+  const bool cv_changed = C.keys_changed || V.keys_changed || !ctx->plan_valid;
+  if (cv_changed) {
+    const int n = ctx->natoms;
+    ctx->nc_start.assign(n + 1, 0);
+    ctx->nbr.resize(C.keys.size());
+    for (size_t e = 0; e < C.keys.size(); ++e) {
+      int32_t k[5];
+      hk_unpack(C.keys[e], k);
+      ctx->nc_start[k[0] + 1]++;
+    }
+    for (int a = 0; a < n; ++a) ctx->nc_start[a + 1] += ctx->nc_start[a];
+    ctx->aotot.assign(n, 0);
+    for (size_t e = 0; e < C.keys.size(); ++e) {  // keys sorted: grouped by atom
+      int32_t k[5];
+      hk_unpack(C.keys[e], k);
+      NbrEntry &ne = ctx->nbr[e];
+      ne.other = k[1];
+      ne.n[0] = k[2]; ne.n[1] = k[3]; ne.n[2] = k[4];
+      ne.aopre = (int32_t)ctx->aotot[k[0]];
+      ne.pad = 0;
+      ne.cblk = (int64_t)e;
+      ctx->aotot[k[0]] += ctx->nao[k[1]];
+    }
+    ctx->items.resize(V.keys.size());
+    int64_t wg = 0, wf = 0, mk = 0;
+    for (size_t e = 0; e < V.keys.size(); ++e) {
+      int32_t k[5];
+      hk_unpack(V.keys[e], k);
+      WorkItem &it = ctx->items[e];
+      it.a = k[0]; it.b = k[1];
+      it.n[0] = k[2]; it.n[1] = k[3]; it.n[2] = k[4];
+      it.nF = (int32_t)(ctx->nc_start[k[0] + 1] - ctx->nc_start[k[0]]);
+      it.nG = (int32_t)(ctx->nc_start[k[1] + 1] - ctx->nc_start[k[1]]);
+      it.nFw = (it.nF + 31) / 32;
+      it.vblk = (int64_t)e;
+      it.dab = -1;
+      it.fbase = ctx->nc_start[k[0]];
+      it.gbase = ctx->nc_start[k[1]];
+      it.mask_off = mk;
+      it.wg_off = wg;
+      it.wf_off = wf;
+      mk += (int64_t)it.nG * 4 * it.nFw;
+      wg += it.nG;
+      wf += it.nF;
+    }
+    ctx->nwg = wg;
+    ctx->nwf = wf;
+    ctx->nmask = mk;
+    CK(ctx->d_nbr.reserve(ctx->nbr.size()));
+    if (!ctx->nbr.empty())
+      CK(cudaMemcpyAsync(ctx->d_nbr.p, ctx->nbr.data(), sizeof(NbrEntry) * ctx->nbr.size(),
+                         cudaMemcpyHostToDevice, st));
+  }
+  if (cv_changed || D.keys_changed) {
+    ctx->dindex.clear();
+    ctx->dindex.reserve(D.keys.size() * 2);
+    std::vector<int64_t> vals(D.keys.size());
+    for (size_t e = 0; e < D.keys.size(); ++e) {
+      ctx->dindex[D.keys[e]] = (int64_t)e;
+      vals[e] = (int64_t)e;
+    }
+    std::vector<uint64_t> tk;
+    std::vector<int64_t> tv;
+    build_table(D.keys, vals, tk, tv, ctx->dmask);
+    CK(ctx->d_dhkeys.reserve(tk.size()));
+    CK(ctx->d_dhvals.reserve(tv.size()));
+    CK(cudaMemcpyAsync(ctx->d_dhkeys.p, tk.data(), sizeof(uint64_t) * tk.size(),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_dhvals.p, tv.data(), sizeof(int64_t) * tv.size(),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));  // tk, tv are about to go out of scope
+    for (auto &it : ctx->items) {
+      auto f = ctx->dindex.find(hk_pack(it.a, it.b, it.n[0], it.n[1], it.n[2]));
+      it.dab = f == ctx->dindex.end() ? -1 : f->second;
+    }
+    CK(ctx->d_items.reserve(ctx->items.size()));
+    if (!ctx->items.empty())
+      CK(cudaMemcpyAsync(ctx->d_items.p, ctx->items.data(), sizeof(WorkItem) * ctx->items.size(),
+                         cudaMemcpyHostToDevice, st));
+  }
+  C.keys_changed = V.keys_changed = D.keys_changed = false;
+  ctx->plan_valid = true;
+  return HFX_OK;
+}
+
+size_t scratch_budget_doubles() {
+  size_t freeb = 0, totalb = 0;
+  cudaMemGetInfo(&freeb, &totalb);
+  size_t budget = std::min<size_t>((size_t)8 << 30, freeb * 2 / 5);
+  if (const char *e = std::getenv("HFX_SCRATCH_MB")) {
+    const long long mb = std::atoll(e);
+    if (mb > 0) budget = (size_t)mb << 20;
+  }
+  return std::max<size_t>(budget / sizeof(double), 1);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+hfx_status hfx_create(const double lattice[9], int32_t natoms, const double *pos,
+                      const int32_t *species, int32_t nspecies, const int32_t *nao,
+                      const int32_t *nabf, void *cuda_stream, hfx_ctx **out) {
+  if (!out) return HFX_E_ARG;
+  *out = nullptr;
+  if (natoms <= 0 || natoms >= (1 << 20) || !species || nspecies <= 0 || !nao || !nabf)
+    return HFX_E_ARG;
+  for (int s = 0; s < nspecies; ++s)
+    if (nao[s] < 1 || nao[s] > HFX_MAX_NAO || nabf[s] < 1 || nabf[s] > HFX_MAX_NABF)
+      return HFX_E_ARG;
+  for (int a = 0; a < natoms; ++a)
+    if (species[a] < 0 || species[a] >= nspecies) return HFX_E_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return HFX_E_CUDA;
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess || prop.major < 10) return HFX_E_CUDA;
+  hfx_ctx *ctx = new (std::nothrow) hfx_ctx();
+  if (!ctx) return HFX_E_NOMEM;
+  ctx->natoms = natoms;
+  ctx->nao.resize(natoms);
+  ctx->nabf.resize(natoms);
+  for (int a = 0; a < natoms; ++a) {
+    ctx->nao[a] = nao[species[a]];
+    ctx->nabf[a] = nabf[species[a]];
+  }
+  if (lattice) std::memcpy(ctx->lattice, lattice, sizeof(ctx->lattice));
+  if (pos) ctx->pos.assign(pos, pos + 3 * (size_t)natoms);
+  ctx->stream = (cudaStream_t)cuda_stream;
+  ctx->K[0].name = 'C';
+  ctx->K[1].name = 'V';
+  ctx->K[2].name = 'D';
+  hfx_status s = HFX_OK;
+  if (ctx->d_nao.reserve(natoms) != cudaSuccess || ctx->d_nabf.reserve(natoms) != cudaSuccess ||
+      ctx->d_err.reserve(1) != cudaSuccess || ctx->d_counters.reserve(8) != cudaSuccess ||
+      ctx->d_ex.reserve(1) != cudaSuccess || ctx->d_collect.reserve(1) != cudaSuccess ||
+      ctx->d_counters.reserve(16) != cudaSuccess)
+    s = HFX_E_NOMEM;
+  if (s == HFX_OK &&
+      (cudaMemcpy(ctx->d_nao.p, ctx->nao.data(), sizeof(int32_t) * natoms,
+                  cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemcpy(ctx->d_nabf.p, ctx->nabf.data(), sizeof(int32_t) * natoms,
+                  cudaMemcpyHostToDevice) != cudaSuccess ||
+       cudaMemset(ctx->d_err.p, 0, sizeof(unsigned)) != cudaSuccess))
+    s = HFX_E_CUDA;
+  for (int e = 0; s == HFX_OK && e < 5; ++e)
+    if (cudaEventCreate(&ctx->ev[e]) != cudaSuccess) s = HFX_E_CUDA;
+  for (int e = 0; s == HFX_OK && e < 10; ++e)
+    if (cudaEventCreate(&ctx->kev[e]) != cudaSuccess) s = HFX_E_CUDA;
+  if (s != HFX_OK) {
+    hfx_destroy(ctx);
+    return s;
+  }
+  *out = ctx;
+  return HFX_OK;
+}
+
+void hfx_destroy(hfx_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  for (auto &e : ctx->ev)
+    if (e) cudaEventDestroy(e);
+  for (auto &e : ctx->kev)
+    if (e) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char *hfx_last_error(const hfx_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+static hfx_status set_one(hfx_ctx *ctx, int k, int32_t i, int32_t j, const int32_t n[3],
+                          const double *blk) {
+  if (!ctx) return HFX_E_ARG;
+  if (!n || !blk) return fail(ctx, HFX_E_ARG, "null pointer");
+  const int32_t key[5] = {i, j, n[0], n[1], n[2]};
+  if (!key_ok(ctx, key)) return fail(ctx, HFX_E_ARG, "block key out of range");
+  Kind &K = ctx->K[k];
+  const int64_t len = block_len(ctx, k, i, j);
+  for (int64_t t = 0; t < len; ++t)
+    if (!std::isfinite(blk[t])) return fail(ctx, HFX_E_ARG, "non-finite value in block");
+  const uint64_t hk = hk_pack(i, j, n[0], n[1], n[2]);
+  const bool is_new = K.map.find(hk) == K.map.end();
+  Entry en{-1, (int64_t)K.pending.size(), len};
+  K.pending.insert(K.pending.end(), blk, blk + len);
+  K.map[hk] = en;
+  invalidate(ctx, k, is_new);
+  return HFX_OK;
+}
+
+hfx_status hfx_set_C(hfx_ctx *ctx, int32_t a, int32_t f, const int32_t n[3], const double *blk) {
+  return set_one(ctx, 0, a, f, n, blk);
+}
+hfx_status hfx_set_V(hfx_ctx *ctx, int32_t a, int32_t b, const int32_t n[3], const double *blk) {
+  return set_one(ctx, 1, a, b, n, blk);
+}
+hfx_status hfx_set_D(hfx_ctx *ctx, int32_t k, int32_t l, const int32_t n[3], const double *blk) {
+  return set_one(ctx, 2, k, l, n, blk);
+}
+
+hfx_status hfx_set_many(hfx_ctx *ctx, char which, int64_t nblk, const int32_t *keys,
+                        const double *data, const int64_t *offs, int on_device) {
+  if (!ctx) return HFX_E_ARG;
+  const int k = kind_index(which);
+  if (k < 0) return fail(ctx, HFX_E_ARG, "which must be 'C', 'V' or 'D'");
+  if (nblk < 0 || (nblk > 0 && (!keys || !data || !offs)))
+    return fail(ctx, HFX_E_ARG, "null pointer or negative count");
+  if (nblk == 0) return HFX_OK;
+  if (offs[0] < 0) return fail(ctx, HFX_E_SHAPE, "negative offset");
+  for (int64_t e = 0; e < nblk; ++e) {
+    const int32_t *kk = keys + 5 * e;
+    if (!key_ok(ctx, kk)) return fail(ctx, HFX_E_ARG, "block key out of range");
+    if (offs[e + 1] - offs[e] != block_len(ctx, k, kk[0], kk[1]))
+      return fail(ctx, HFX_E_SHAPE, "block size does not match nao/nabf");
+  }
+  Kind &K = ctx->K[k];
+  const int64_t lo = offs[0], hi = offs[nblk];
+  Chunk c;
+  c.n = (size_t)(hi - lo);
+  cudaError_t e = cudaMalloc((void **)&c.dev, (c.n > 0 ? c.n : 1) * sizeof(double));
+  if (e != cudaSuccess) return fail_cuda(ctx, "cudaMalloc", e);
+  e = cudaMemcpyAsync(c.dev, data + lo, c.n * sizeof(double),
+                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    cudaFree(c.dev);
+    return fail_cuda(ctx, "cudaMemcpyAsync", e);
+  }
+  const int32_t id = (int32_t)K.chunks.size();
+  K.chunks.push_back(c);
+  bool any_new = false;
+  for (int64_t b = 0; b < nblk; ++b) {
+    const int32_t *kk = keys + 5 * b;
+    const uint64_t hk = hk_pack(kk[0], kk[1], kk[2], kk[3], kk[4]);
+    auto it = K.map.find(hk);
+    if (it == K.map.end()) any_new = true;
+    K.map[hk] = Entry{id, offs[b] - lo, offs[b + 1] - offs[b]};
+  }
+  invalidate(ctx, k, any_new);
+  return HFX_OK;
+}
+
+hfx_status hfx_clear(hfx_ctx *ctx, char which) {
+  if (!ctx) return HFX_E_ARG;
+  const int k = kind_index(which);
+  if (k < 0) return fail(ctx, HFX_E_ARG, "which must be 'C', 'V' or 'D'");
+  Kind &K = ctx->K[k];
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  K.map.clear();
+  K.pending.clear();
+  if (K.data_is_chunk) {
+    K.data.p = nullptr;
+    K.data.n = 0;
+    K.data_is_chunk = false;
+  }
+  K.free_chunks();
+  invalidate(ctx, k, true);
+  return HFX_OK;
+}
+
+hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices, double *ex_out) {
+  if (!ctx) return HFX_E_ARG;
+  if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(ctx, HFX_E_ARG, "theta must be >= 0");
+  if (prec != HFX_FP64)
+    return fail(ctx, HFX_E_ARG, "precision mode not available in this build");
+  (void)nslices;
+  for (int k = 0; k < 3; ++k)
+    if (ctx->K[k].map.empty())
+      return fail(ctx, HFX_E_STATE, std::string("no ") + ctx->K[k].name + " blocks set");
+  ctx->results_valid = false;
+  ctx->launches = 0;
+  double kms[8] = {0};
+  cudaStream_t st = ctx->stream;
+  CK(cudaEventRecord(ctx->ev[0], st));
+  CK(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(unsigned), st));
+  for (int k = 0; k < 3; ++k) {
+    hfx_status s = pack_kind(ctx, k);
+    if (s != HFX_OK) return s;
+  }
+  {
+    unsigned perr = 0;
+    CK(cudaMemcpyAsync(&perr, ctx->d_err.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (perr & HFX_DEV_ERR_NONFINITE) {
+      for (int k = 0; k < 3; ++k) ctx->K[k].dirty = true;  // re-check on the next build
+      return fail(ctx, HFX_E_ARG, "non-finite value in an input block");
+    }
+    hfx_status s = build_plan(ctx);
+    if (s != HFX_OK) return s;
+  }
+  // ---- screen (retry with a larger Sigma key table on overflow)
+  CK(ctx->d_masks.reserve(ctx->nmask));
+  CK(ctx->d_wg.reserve(ctx->nwg));
+  CK(ctx->d_wf.reserve(ctx->nwf));
+  if (ctx->stab_cap == 0)
+    ctx->stab_cap = pow2_at_least(64 * (uint64_t)ctx->K[0].keys.size() + 1024);
+  unsigned long long counters[16] = {0};
+  unsigned herr = 0;
+  for (int attempt = 0;; ++attempt) {
+    CK(ctx->d_stab.reserve(ctx->stab_cap));
+    CK(cudaMemsetAsync(ctx->d_stab.p, 0xFF, sizeof(unsigned long long) * ctx->stab_cap, st));
+    CK(cudaMemsetAsync(ctx->d_wg.p, 0, ctx->nwg ? ctx->nwg : 1, st));
+    CK(cudaMemsetAsync(ctx->d_wf.p, 0, sizeof(uint32_t) * (ctx->nwf ? ctx->nwf : 1), st));
+    CK(cudaMemsetAsync(ctx->d_counters.p, 0, sizeof(unsigned long long) * 16, st));
+    CK(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(unsigned), st));
+    ScreenArgs a{};
+    a.items = ctx->d_items.p;
+    a.nitems = (int64_t)ctx->items.size();
+    a.nwg = ctx->nwg;
+    a.nbr = ctx->d_nbr.p;
+    a.nao = ctx->d_nao.p;
+    a.nabf = ctx->d_nabf.p;
+    a.C = DevBlocks{ctx->K[0].data.p, ctx->K[0].d_offs.p, ctx->K[0].maxabs.p};
+    a.V = DevBlocks{ctx->K[1].data.p, ctx->K[1].d_offs.p, ctx->K[1].maxabs.p};
+    a.D = DevBlocks{ctx->K[2].data.p, ctx->K[2].d_offs.p, ctx->K[2].maxabs.p};
+    a.dhash = DevHash{ctx->d_dhkeys.p, ctx->d_dhvals.p, ctx->dmask};
+    a.theta = theta;
+    a.masks = ctx->d_masks.p;
+    a.wg_flags = ctx->d_wg.p;
+    a.wf_flags = ctx->d_wf.p;
+    a.sig_keys = ctx->d_stab.p;
+    a.sig_mask = ctx->stab_cap - 1;
+    a.sig_count = ctx->d_counters.p + 7;
+    a.sig_limit = ctx->stab_cap / 2;
+    a.counters = ctx->d_counters.p;
+    a.err = ctx->d_err.p;
+    CK(cudaEventRecord(ctx->kev[8], st));
+    CK(launch_screen(a, st));
+    CK(cudaEventRecord(ctx->kev[9], st));
+    ctx->launches += a.nwg > 0;
+    CK(cudaMemcpyAsync(counters, ctx->d_counters.p, sizeof(counters), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&herr, ctx->d_err.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if ((herr & HFX_DEV_ERR_HASH_FULL) && attempt < 6) {
+      ctx->stab_cap *= 4;
+      continue;
+    }
+    if (herr) return fail(ctx, HFX_E_CUDA, "screen kernel reported error " + std::to_string(herr));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->kev[8], ctx->kev[9]);
+    kms[0] = ms;
+    break;
+  }
+  // ---- Sigma key set: collect, sort, offsets, lookup table
+  const int64_t nsig = (int64_t)counters[7];
+  {
+    CK(ctx->d_collect.reserve(nsig + 1));
+    CK(cudaMemsetAsync(ctx->d_counters.p + 7, 0, sizeof(unsigned long long), st));
+    CK(launch_collect_keys(ctx->d_stab.p, ctx->stab_cap, ctx->d_collect.p,
+                           ctx->d_counters.p + 7, st));
+    ctx->launches += 1;
+    ctx->sig_keys.resize(nsig);
+    if (nsig)
+      CK(cudaMemcpyAsync(ctx->sig_keys.data(), ctx->d_collect.p, sizeof(uint64_t) * nsig,
+                         cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    std::sort(ctx->sig_keys.begin(), ctx->sig_keys.end());
+    ctx->sig_offs.assign(nsig + 1, 0);
+    for (int64_t e = 0; e < nsig; ++e) {
+      int32_t k[5];
+      hk_unpack(ctx->sig_keys[e], k);
+      ctx->sig_offs[e + 1] = ctx->sig_offs[e] + (int64_t)ctx->nao[k[0]] * ctx->nao[k[1]];
+    }
+    std::vector<uint64_t> tk;
+    std::vector<int64_t> tv;
+    std::vector<int64_t> vals(ctx->sig_offs.begin(), ctx->sig_offs.end() - 1);
+    build_table(ctx->sig_keys, vals, tk, tv, ctx->smask);
+    CK(ctx->d_shkeys.reserve(tk.size()));
+    CK(ctx->d_shvals.reserve(tv.size()));
+    CK(ctx->d_skeys.reserve(nsig));
+    CK(ctx->d_soffs.reserve(nsig + 1));
+    CK(cudaMemcpyAsync(ctx->d_shkeys.p, tk.data(), sizeof(uint64_t) * tk.size(),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_shvals.p, tv.data(), sizeof(int64_t) * tv.size(),
+                       cudaMemcpyHostToDevice, st));
+    if (nsig)
+      CK(cudaMemcpyAsync(ctx->d_skeys.p, ctx->sig_keys.data(), sizeof(uint64_t) * nsig,
+                         cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_soffs.p, ctx->sig_offs.data(), sizeof(int64_t) * (nsig + 1),
+                       cudaMemcpyHostToDevice, st));
+    const int64_t nelem = ctx->sig_offs[nsig];
+    CK(ctx->d_acc.reserve(2 * nelem));
+    CK(cudaMemsetAsync(ctx->d_acc.p, 0, sizeof(unsigned long long) * 2 * (nelem ? nelem : 1), st));
+    CK(cudaStreamSynchronize(st));  // tk, tv, vals go out of scope
+  }
+  CK(cudaEventRecord(ctx->ev[1], st));
+  // ---- contraction waves
+  const size_t budget = scratch_budget_doubles();
+  int64_t nwaves = 0;
+  size_t peak = 0;
+  {
+    const size_t nit = ctx->items.size();
+    size_t w0 = 0;
+    std::vector<int64_t> offs4;
+    while (w0 < nit) {
+      size_t w1 = w0;
+      size_t used = 0;
+      offs4.clear();
+      std::vector<int64_t> yo, po, to, qo;
+      while (w1 < nit) {
+        const WorkItem &it = ctx->items[w1];
+        const int64_t pA = ctx->nabf[it.a], na = ctx->nao[it.a], nb = ctx->nao[it.b];
+        const int64_t ysz = pA * nb * ctx->aotot[it.b];
+        const int64_t psz = it.dab >= 0 ? pA * na * ctx->aotot[it.b] : 0;
+        const int64_t tsz = (int64_t)it.nG * pA * na * nb;
+        const int64_t qsz = (int64_t)it.nF * pA * na * nb;
+        const size_t need = (size_t)(ysz + psz + tsz + qsz);
+        if (w1 > w0 && used + need > budget) break;
+        yo.push_back((int64_t)used);
+        po.push_back((int64_t)used + ysz);
+        to.push_back((int64_t)used + ysz + psz);
+        qo.push_back((int64_t)used + ysz + psz + tsz);
+        used += need;
+        ++w1;
+      }
+      const size_t nw = w1 - w0;
+      offs4.insert(offs4.end(), yo.begin(), yo.end());
+      offs4.insert(offs4.end(), po.begin(), po.end());
+      offs4.insert(offs4.end(), to.begin(), to.end());
+      offs4.insert(offs4.end(), qo.begin(), qo.end());
+      CK(ctx->d_scratch.reserve(std::max<size_t>(used, 1)));
+      CK(ctx->d_waveoffs.reserve(offs4.size()));
+      CK(cudaMemcpyAsync(ctx->d_waveoffs.p, offs4.data(), sizeof(int64_t) * offs4.size(),
+                         cudaMemcpyHostToDevice, st));
+      peak = std::max(peak, used);
+      ContractArgs c{};
+      c.items = ctx->d_items.p;
+      c.w0 = (int64_t)w0;
+      c.w1 = (int64_t)w1;
+      c.wg_base = ctx->items[w0].wg_off;
+      c.wf_base = ctx->items[w0].wf_off;
+      const int64_t wg_end = (w1 < nit) ? ctx->items[w1].wg_off : ctx->nwg;
+      const int64_t wf_end = (w1 < nit) ? ctx->items[w1].wf_off : ctx->nwf;
+      c.nwg = wg_end - c.wg_base;
+      c.nwf = wf_end - c.wf_base;
+      c.nbr = ctx->d_nbr.p;
+      c.nao = ctx->d_nao.p;
+      c.nabf = ctx->d_nabf.p;
+      c.C = DevBlocks{ctx->K[0].data.p, ctx->K[0].d_offs.p, ctx->K[0].maxabs.p};
+      c.V = DevBlocks{ctx->K[1].data.p, ctx->K[1].d_offs.p, ctx->K[1].maxabs.p};
+      c.D = DevBlocks{ctx->K[2].data.p, ctx->K[2].d_offs.p, ctx->K[2].maxabs.p};
+      c.dhash = DevHash{ctx->d_dhkeys.p, ctx->d_dhvals.p, ctx->dmask};
+      c.shash = DevHash{ctx->d_shkeys.p, ctx->d_shvals.p, ctx->smask};
+      c.masks = ctx->d_masks.p;
+      c.wg_flags = ctx->d_wg.p;
+      c.wf_flags = ctx->d_wf.p;
+      c.scratch = ctx->d_scratch.p;
+      c.y_off = ctx->d_waveoffs.p;
+      c.p_off = ctx->d_waveoffs.p + nw;
+      c.t3_off = ctx->d_waveoffs.p + 2 * nw;
+      c.q_off = ctx->d_waveoffs.p + 3 * nw;
+      c.acc = ctx->d_acc.p;
+      c.macs = ctx->d_counters.p + 8;
+      c.err = ctx->d_err.p;
+      int nl = 0;
+      CK(launch_contract_fp64(c, st, ctx->kev, &nl));
+      ctx->launches += nl;
+      // the host offsets vector is reused next wave: order the copy first
+      CK(cudaStreamSynchronize(st));
+      for (int q = 0; q < 7; ++q) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ctx->kev[q], ctx->kev[q + 1]);
+        kms[1 + q] += ms;
+      }
+      ++nwaves;
+      w0 = w1;
+    }
+  }
+  CK(cudaEventRecord(ctx->ev[2], st));
+  // ---- finalize
+  const int64_t nelem = ctx->sig_offs[nsig];
+  CK(ctx->d_sigma.reserve(nelem));
+  CK(ctx->d_partials.reserve(nsig));
+  CK(launch_finalize(ctx->d_acc.p, nelem, ctx->d_sigma.p, ctx->d_skeys.p, ctx->d_soffs.p, nsig,
+                     DevBlocks{ctx->K[2].data.p, ctx->K[2].d_offs.p, ctx->K[2].maxabs.p},
+                     DevHash{ctx->d_dhkeys.p, ctx->d_dhvals.p, ctx->dmask}, ctx->d_partials.p,
+                     ctx->d_ex.p, st));
+  ctx->launches += (nelem > 0) + (nsig > 0) + 1;
+  CK(cudaEventRecord(ctx->ev[3], st));
+  double ex = 0.0;
+  CK(cudaMemcpyAsync(&ex, ctx->d_ex.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&herr, ctx->d_err.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  unsigned long long kmacs[7] = {0};
+  CK(cudaMemcpyAsync(kmacs, ctx->d_counters.p + 8, sizeof(kmacs), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (herr) return fail(ctx, HFX_E_CUDA, "contraction kernels reported error " + std::to_string(herr));
+  float ms01 = 0, ms12 = 0, ms23 = 0, ms03 = 0;
+  cudaEventElapsedTime(&ms01, ctx->ev[0], ctx->ev[1]);
+  cudaEventElapsedTime(&ms12, ctx->ev[1], ctx->ev[2]);
+  cudaEventElapsedTime(&ms23, ctx->ev[2], ctx->ev[3]);
+  cudaEventElapsedTime(&ms03, ctx->ev[0], ctx->ev[3]);
+  hfx_stats_v1 &S = ctx->stats;
+  S = hfx_stats_v1{};
+  S.version = 1;
+  S.prec = (int32_t)prec;
+  S.theta = theta;
+  S.n_sigma_blocks = nsig;
+  S.n_work_items = (int64_t)ctx->items.size();
+  S.n_active_abg = (int64_t)counters[4];
+  for (int v = 0; v < 4; ++v) S.survivors[v] = (int64_t)counters[v];
+  S.canonical_flops = 2.0 * (double)counters[5];
+  double macs = 0;
+  for (int q = 0; q < 7; ++q) macs += (double)kmacs[q];
+  S.executed_flops = 2.0 * macs;
+  // stats kernel order: screen, Y, D-stage, Q, D_FG, D_AG, D_FB, D_AB
+  // (kmacs / kms[1..7] are in launch order: Y, D-stage, Q, D_FG, D_AG, D_FB, D_AB)
+  for (int q = 0; q < 8; ++q) S.kernel_ms[q] = kms[q];
+  S.kernel_flops[0] = 0.0;
+  for (int q = 0; q < 7; ++q) S.kernel_flops[1 + q] = 2.0 * (double)kmacs[q];
+  S.n_launches = ctx->launches;
+  S.ms_screen = ms01;
+  S.ms_contract = ms12;
+  S.ms_reduce = ms23;
+  S.ms_total = ms03;
+  S.n_waves = nwaves;
+  S.scratch_bytes = (int64_t)(peak * sizeof(double));
+  ctx->ex = ex;
+  ctx->results_valid = true;
+  if (ex_out) *ex_out = ex;
+  return HFX_OK;
+}
+
+hfx_status hfx_H_count(const hfx_ctx *ctx, int64_t *nblk) {
+  if (!ctx || !nblk) return HFX_E_ARG;
+  if (!ctx->results_valid) return HFX_E_STATE;
+  *nblk = (int64_t)ctx->sig_keys.size();
+  return HFX_OK;
+}
+
+hfx_status hfx_H_keys(const hfx_ctx *ctx, int32_t *keys) {
+  if (!ctx || !keys) return HFX_E_ARG;
+  if (!ctx->results_valid) return HFX_E_STATE;
+  for (size_t e = 0; e < ctx->sig_keys.size(); ++e) hk_unpack(ctx->sig_keys[e], keys + 5 * e);
+  return HFX_OK;
+}
+
+hfx_status hfx_H_offsets(const hfx_ctx *ctx, int64_t *offs) {
+  if (!ctx || !offs) return HFX_E_ARG;
+  if (!ctx->results_valid) return HFX_E_STATE;
+  std::memcpy(offs, ctx->sig_offs.data(), sizeof(int64_t) * ctx->sig_offs.size());
+  return HFX_OK;
+}
+
+hfx_status hfx_get_H(const hfx_ctx *ctx, int32_t i, int32_t j, const int32_t n[3], double *out) {
+  if (!ctx || !n || !out) return HFX_E_ARG;
+  if (!ctx->results_valid) return HFX_E_STATE;
+  const uint64_t k = hk_pack(i, j, n[0], n[1], n[2]);
+  auto it = std::lower_bound(ctx->sig_keys.begin(), ctx->sig_keys.end(), k);
+  if (it == ctx->sig_keys.end() || *it != k) return HFX_E_NOTFOUND;
+  const size_t e = (size_t)(it - ctx->sig_keys.begin());
+  const int64_t len = ctx->sig_offs[e + 1] - ctx->sig_offs[e];
+  if (cudaMemcpyAsync(out, ctx->d_sigma.p + ctx->sig_offs[e], sizeof(double) * len,
+                      cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+    return HFX_E_CUDA;
+  return HFX_OK;
+}
+
+hfx_status hfx_get_H_all(const hfx_ctx *ctx, double *out, int on_device) {
+  if (!ctx || !out) return HFX_E_ARG;
+  if (!ctx->results_valid) return HFX_E_STATE;
+  const int64_t n = ctx->sig_offs.empty() ? 0 : ctx->sig_offs.back();
+  if (n == 0) return HFX_OK;
+  if (cudaMemcpyAsync(out, ctx->d_sigma.p, sizeof(double) * n,
+                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                      ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+    return HFX_E_CUDA;
+  return HFX_OK;
+}
+
+hfx_status hfx_grad(hfx_ctx *ctx, double *dC, double *dV) {
+  if (!ctx) return HFX_E_ARG;
+  (void)dC;
+  (void)dV;
+  if (!ctx->results_valid) return fail(ctx, HFX_E_STATE, "no build to differentiate");
+  return fail(ctx, HFX_E_ARG, "adjoint not available in this build");
+}
+
+hfx_status hfx_stats(const hfx_ctx *ctx, void *stats) {
+  if (!ctx || !stats) return HFX_E_ARG;
+  if (!ctx->results_valid) return HFX_E_STATE;
+  std::memcpy(stats, &ctx->stats, sizeof(hfx_stats_v1));
+  return HFX_OK;
+}
+
+}  // extern "C"

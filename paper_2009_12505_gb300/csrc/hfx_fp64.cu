@@ -1,0 +1,413 @@
+// FP64 contraction kernels: the staged C((VC)D) build of Algorithm 3 on CUDA
+// cores, one wave of <A,B> work items at a time.
+//
+// Per work item w = <A,B> (A = (a,0), B = (b,n)), F in N[A], G in N[B]:
+//   k_y      Y_G[al][b][g]  = sum_be V_AB[al][be] C_BG[be][b][g]       (Alg. 3, Y = V*C)
+//   k_dstage P_G[al][a][g]  = sum_b  D_AB[a][b]  Y_G[al][b][g]         (T of the D_AB piece)
+//            T3_G[al][a][b] = sum_g  D_AG[a][g]  Y_G[al][b][g]         (T of the D_AG piece)
+//   k_q      Q_F[al][a][b]  = sum_f  C_AF[al][a][f] D_FB[f][b]
+//   k_v1     Sigma_AB[a][b] -= sum_{al,f} C_AF[al][a][f] sum_{G in M1(F)} sum_g Y_G[al][b][g] D_FG[f][g]
+//   k_v2     Sigma_AG[a][g] -= sum_{al,b} (sum_{F in M2(G)} Q_F[al][a][b]) Y_G[al][b][g]
+//   k_v3     Sigma_FB[f][b] -= sum_{al,a} C_AF[al][a][f] (sum_{G in M3(F)} T3_G[al][a][b])
+//   k_v4     Sigma_FG[f][g] -= sum_{al,a} C_AF[al][a][f] P_G[al][a][g]       for F in M4(G)
+// M_v are the surviving-term bitmasks from the screen.  Every term is the
+// same multilinear form as Algorithm 3's Ht; the D_FB and D_AG pieces sum the
+// masked F (G) contributions before the last contraction, which is exact
+// reassociation (distributivity), not an approximation.
+//
+// Summation order inside a kernel is fixed (masks are scanned in index order),
+// and Sigma receives each block through the deterministic fixed-point adder,
+// so results are bitwise reproducible.
+#include "hfx_internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kChunk = 4096;     // doubles of shared staging per chunk
+constexpr int kMaxOut = 16;      // outputs per thread: nao*nao <= 4096
+
+struct PairLoc {
+  int64_t w;   // work item (absolute index)
+  int idx;     // g or f within the item
+};
+
+// (w, g) or (w, f) pair p of the wave -> item and index (binary search).
+__device__ inline PairLoc locate(const ContractArgs &A, int64_t p, bool by_g) {
+  const int64_t base = by_g ? A.wg_base : A.wf_base;
+  int64_t lo = A.w0, hi = A.w1 - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    const int64_t off = (by_g ? A.items[mid].wg_off : A.items[mid].wf_off) - base;
+    if (off <= p) lo = mid; else hi = mid - 1;
+  }
+  const int64_t off = (by_g ? A.items[lo].wg_off : A.items[lo].wf_off) - base;
+  return PairLoc{lo, (int)(p - off)};
+}
+
+__device__ inline bool mask_bit(const ContractArgs &A, const WorkItem &it, int g, int v, int f) {
+  const uint32_t w = A.masks[it.mask_off + ((int64_t)g * 4 + v) * it.nFw + (f >> 5)];
+  return (w >> (f & 31)) & 1u;
+}
+
+__device__ inline int64_t sig_offset(const ContractArgs &A, int i, int j, int n0, int n1, int n2) {
+  const int64_t off = dh_find(A.shash, hk_pack(i, j, n0, n1, n2));
+  if (off < 0) atomicOr(A.err, HFX_DEV_ERR_MISSING);
+  return off;
+}
+
+// Ordered list of the indices x in [0, n) with bit(x) set, built by warp 0
+// with ballots so the order is ascending (deterministic).  Returns the count.
+template <class Bit>
+__device__ inline int ordered_select(int n, Bit bit, int *list, int *count_smem) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int c = 0;
+    for (int x0 = 0; x0 < n; x0 += 32) {
+      const int x = x0 + lane;
+      const bool b = x < n && bit(x);
+      const uint32_t bal = __ballot_sync(0xffffffffu, b);
+      if (b) list[c + __popc(bal & ((1u << lane) - 1u))] = x;
+      c += __popc(bal);
+    }
+    if (lane == 0) *count_smem = c;
+  }
+  __syncthreads();
+  return *count_smem;
+}
+
+__global__ void __launch_bounds__(kThreads) k_y(ContractArgs A) {
+  const PairLoc L = locate(A, blockIdx.x, true);
+  const WorkItem it = A.items[L.w];
+  if (!(A.wg_flags[it.wg_off + L.idx] & 0xFu)) return;
+  const NbrEntry eg = A.nbr[it.gbase + L.idx];
+  const int pA = A.nabf[it.a], pB = A.nabf[it.b], nb = A.nao[it.b], ng = A.nao[eg.other];
+  const double *V = A.V.data + A.V.offs[it.vblk];
+  const double *Cb = A.C.data + A.C.offs[eg.cblk];
+  double *Y = A.scratch + A.y_off[L.w - A.w0] + (int64_t)pA * nb * eg.aopre;
+  const int N = nb * ng;
+  for (int idx = threadIdx.x; idx < pA * N; idx += kThreads) {
+    const int al = idx / N, c = idx - al * N;
+    const double *v = V + (int64_t)al * pB;
+    double s = 0.0;
+    for (int be = 0; be < pB; ++be) s = fma(v[be], Cb[(int64_t)be * N + c], s);
+    Y[idx] = s;
+  }
+  if (threadIdx.x == 0) atomicAdd(A.macs + 0, (unsigned long long)pA * pB * N);
+}
+
+__global__ void __launch_bounds__(kThreads) k_dstage(ContractArgs A) {
+  const PairLoc L = locate(A, blockIdx.x, true);
+  const WorkItem it = A.items[L.w];
+  const unsigned bits = A.wg_flags[it.wg_off + L.idx];
+  if (!(bits & 0xCu)) return;
+  const NbrEntry eg = A.nbr[it.gbase + L.idx];
+  const int pA = A.nabf[it.a], na = A.nao[it.a], nb = A.nao[it.b], ng = A.nao[eg.other];
+  const double *Y = A.scratch + A.y_off[L.w - A.w0] + (int64_t)pA * nb * eg.aopre;
+  unsigned long long macs = 0;
+  if ((bits & 8u) && it.dab >= 0) {  // P_G[al][a][g] = sum_b D_AB[a][b] Y_G[al][b][g]
+    const double *Dab = A.D.data + A.D.offs[it.dab];
+    double *P = A.scratch + A.p_off[L.w - A.w0] + (int64_t)pA * na * eg.aopre;
+    const int per = na * ng;
+    for (int idx = threadIdx.x; idx < pA * per; idx += kThreads) {
+      const int al = idx / per, r = idx - al * per, a = r / ng, g = r - a * ng;
+      const double *y = Y + (int64_t)al * nb * ng + g;
+      const double *d = Dab + a * nb;
+      double s = 0.0;
+      for (int b = 0; b < nb; ++b) s = fma(d[b], y[b * ng], s);
+      P[idx] = s;
+    }
+    macs += (unsigned long long)pA * per * nb;
+  }
+  if (bits & 4u) {  // T3_G[al][a][b] = sum_g D_AG[a][g] Y_G[al][b][g]
+    const int n0 = it.n[0] + eg.n[0], n1 = it.n[1] + eg.n[1], n2 = it.n[2] + eg.n[2];
+    const int64_t dag = dh_find(A.dhash, hk_pack(it.a, eg.other, n0, n1, n2));
+    if (dag < 0) { atomicOr(A.err, HFX_DEV_ERR_MISSING); return; }
+    const double *Dag = A.D.data + A.D.offs[dag];
+    double *T3 = A.scratch + A.t3_off[L.w - A.w0] + (int64_t)L.idx * pA * na * nb;
+    const int per = na * nb;
+    for (int idx = threadIdx.x; idx < pA * per; idx += kThreads) {
+      const int al = idx / per, r = idx - al * per, a = r / nb, b = r - a * nb;
+      const double *y = Y + ((int64_t)al * nb + b) * ng;
+      const double *d = Dag + a * ng;
+      double s = 0.0;
+      for (int g = 0; g < ng; ++g) s = fma(d[g], y[g], s);
+      T3[idx] = s;
+    }
+    macs += (unsigned long long)pA * per * ng;
+  }
+  if (threadIdx.x == 0 && macs) atomicAdd(A.macs + 1, macs);
+}
+
+__global__ void __launch_bounds__(kThreads) k_q(ContractArgs A) {
+  const PairLoc L = locate(A, blockIdx.x, false);
+  const WorkItem it = A.items[L.w];
+  if (!(A.wf_flags[it.wf_off + L.idx] & 2u)) return;
+  const NbrEntry ef = A.nbr[it.fbase + L.idx];
+  const int pA = A.nabf[it.a], na = A.nao[it.a], nb = A.nao[it.b], nf = A.nao[ef.other];
+  const int64_t dfb = dh_find(A.dhash, hk_pack(ef.other, it.b, it.n[0] - ef.n[0],
+                                               it.n[1] - ef.n[1], it.n[2] - ef.n[2]));
+  if (dfb < 0) { atomicOr(A.err, HFX_DEV_ERR_MISSING); return; }
+  const double *Dfb = A.D.data + A.D.offs[dfb];
+  const double *Caf = A.C.data + A.C.offs[ef.cblk];
+  double *Q = A.scratch + A.q_off[L.w - A.w0] + (int64_t)L.idx * pA * na * nb;
+  const int per = na * nb;
+  for (int idx = threadIdx.x; idx < pA * per; idx += kThreads) {
+    const int al = idx / per, r = idx - al * per, a = r / nb, b = r - a * nb;
+    const double *c = Caf + ((int64_t)al * na + a) * nf;
+    double s = 0.0;
+    for (int f = 0; f < nf; ++f) s = fma(c[f], Dfb[f * nb + b], s);
+    Q[idx] = s;
+  }
+  if (threadIdx.x == 0) atomicAdd(A.macs + 2, (unsigned long long)pA * per * nf);
+}
+
+// Sigma_AB -= sum_{al,f} C_AF[al][a][f] T1[al][b][f],
+// T1[al][b][f] = sum_{G in M1(F)} sum_g Y_G[al][b][g] D_FG[f][g].
+__global__ void __launch_bounds__(kThreads) k_v1(ContractArgs A) {
+  __shared__ int glist[1024];
+  __shared__ int64_t dlist[1024];
+  __shared__ int nsel_s;
+  __shared__ double T1[kChunk];
+  const PairLoc L = locate(A, blockIdx.x, false);
+  const WorkItem it = A.items[L.w];
+  if (!(A.wf_flags[it.wf_off + L.idx] & 1u)) return;
+  if (it.nG > 1024) { if (threadIdx.x == 0) atomicOr(A.err, HFX_DEV_ERR_BOUNDS); return; }
+  const int f_ = L.idx;
+  const NbrEntry ef = A.nbr[it.fbase + f_];
+  const int pA = A.nabf[it.a], na = A.nao[it.a], nb = A.nao[it.b], nf = A.nao[ef.other];
+  const int nsel = ordered_select(it.nG, [&](int g) { return mask_bit(A, it, g, 0, f_); },
+                                  glist, &nsel_s);
+  for (int s = threadIdx.x; s < nsel; s += kThreads) {
+    const NbrEntry eg = A.nbr[it.gbase + glist[s]];
+    dlist[s] = dh_find(A.dhash, hk_pack(ef.other, eg.other, it.n[0] + eg.n[0] - ef.n[0],
+                                        it.n[1] + eg.n[1] - ef.n[1], it.n[2] + eg.n[2] - ef.n[2]));
+  }
+  __syncthreads();
+  const double *Caf = A.C.data + A.C.offs[ef.cblk];
+  const double *Ybase = A.scratch + A.y_off[L.w - A.w0];
+  const int nout = na * nb;
+  double acc[kMaxOut];
+#pragma unroll
+  for (int q = 0; q < kMaxOut; ++q) acc[q] = 0.0;
+  const int per = nb * nf;
+  const int ach = max(1, min(pA, kChunk / per));
+  unsigned long long macs = 0;
+  for (int al0 = 0; al0 < pA; al0 += ach) {
+    const int ac = min(ach, pA - al0);
+    for (int idx = threadIdx.x; idx < ac * per; idx += kThreads) T1[idx] = 0.0;
+    for (int s = 0; s < nsel; ++s) {
+      const NbrEntry eg = A.nbr[it.gbase + glist[s]];
+      const int ng = A.nao[eg.other];
+      const int64_t dfg = dlist[s];
+      if (dfg < 0) continue;
+      const double *Dfg = A.D.data + A.D.offs[dfg];
+      const double *Y = Ybase + (int64_t)pA * nb * eg.aopre + (int64_t)al0 * nb * ng;
+      for (int idx = threadIdx.x; idx < ac * per; idx += kThreads) {
+        const int ab = idx / nf, f = idx - ab * nf;  // ab = al*nb + b
+        const double *y = Y + (int64_t)ab * ng;
+        const double *d = Dfg + f * ng;
+        double t = 0.0;
+        for (int g = 0; g < ng; ++g) t = fma(y[g], d[g], t);
+        T1[idx] += t;
+      }
+      macs += (unsigned long long)ac * per * ng;
+    }
+    __syncthreads();
+    for (int q = 0; q < kMaxOut; ++q) {
+      const int o = threadIdx.x + q * kThreads;
+      if (o >= nout) break;
+      const int a = o / nb, b = o - a * nb;
+      double s = acc[q];
+      for (int al = 0; al < ac; ++al) {
+        const double *c = Caf + ((int64_t)(al0 + al) * na + a) * nf;
+        const double *t = T1 + (al * nb + b) * nf;
+        for (int f = 0; f < nf; ++f) s = fma(c[f], t[f], s);
+      }
+      acc[q] = s;
+    }
+    macs += (unsigned long long)ac * nout * nf;
+    __syncthreads();
+  }
+  const int64_t off = sig_offset(A, it.a, it.b, it.n[0], it.n[1], it.n[2]);
+  if (off >= 0)
+    for (int q = 0; q < kMaxOut; ++q) {
+      const int o = threadIdx.x + q * kThreads;
+      if (o >= nout) break;
+      fx_add(A.acc + 2 * (off + o), -acc[q]);
+    }
+  if (threadIdx.x == 0) atomicAdd(A.macs + 3, macs);
+}
+
+// Sigma_AG -= sum_{al,b} Qsum[al][a][b] Y_G[al][b][g],  Qsum = sum_{F in M2(G)} Q_F.
+__global__ void __launch_bounds__(kThreads) k_v2(ContractArgs A) {
+  __shared__ int flist[1024];
+  __shared__ int nsel_s;
+  __shared__ double Qs[kChunk];
+  const PairLoc L = locate(A, blockIdx.x, true);
+  const WorkItem it = A.items[L.w];
+  if (!(A.wg_flags[it.wg_off + L.idx] & 2u)) return;
+  if (it.nF > 1024) { if (threadIdx.x == 0) atomicOr(A.err, HFX_DEV_ERR_BOUNDS); return; }
+  const int g_ = L.idx;
+  const NbrEntry eg = A.nbr[it.gbase + g_];
+  const int pA = A.nabf[it.a], na = A.nao[it.a], nb = A.nao[it.b], ng = A.nao[eg.other];
+  const int nsel = ordered_select(it.nF, [&](int f) { return mask_bit(A, it, g_, 1, f); },
+                                  flist, &nsel_s);
+  const double *Qbase = A.scratch + A.q_off[L.w - A.w0];
+  const double *Y = A.scratch + A.y_off[L.w - A.w0] + (int64_t)pA * nb * eg.aopre;
+  const int per = na * nb, nout = na * ng;
+  double acc[kMaxOut];
+#pragma unroll
+  for (int q = 0; q < kMaxOut; ++q) acc[q] = 0.0;
+  const int ach = max(1, min(pA, kChunk / per));
+  unsigned long long macs = 0;
+  for (int al0 = 0; al0 < pA; al0 += ach) {
+    const int ac = min(ach, pA - al0);
+    for (int idx = threadIdx.x; idx < ac * per; idx += kThreads) {
+      double s = 0.0;
+      for (int k = 0; k < nsel; ++k) s += Qbase[((int64_t)flist[k] * pA + al0) * per + idx];
+      Qs[idx] = s;
+    }
+    macs += (unsigned long long)nsel * ac * per;
+    __syncthreads();
+    for (int q = 0; q < kMaxOut; ++q) {
+      const int o = threadIdx.x + q * kThreads;
+      if (o >= nout) break;
+      const int a = o / ng, g = o - a * ng;
+      double s = acc[q];
+      for (int al = 0; al < ac; ++al) {
+        const double *qq = Qs + (al * na + a) * nb;
+        const double *y = Y + (int64_t)(al0 + al) * nb * ng + g;
+        for (int b = 0; b < nb; ++b) s = fma(qq[b], y[b * ng], s);
+      }
+      acc[q] = s;
+    }
+    macs += (unsigned long long)ac * nout * nb;
+    __syncthreads();
+  }
+  const int64_t off = sig_offset(A, it.a, eg.other, it.n[0] + eg.n[0], it.n[1] + eg.n[1],
+                                 it.n[2] + eg.n[2]);
+  if (off >= 0)
+    for (int q = 0; q < kMaxOut; ++q) {
+      const int o = threadIdx.x + q * kThreads;
+      if (o >= nout) break;
+      fx_add(A.acc + 2 * (off + o), -acc[q]);
+    }
+  if (threadIdx.x == 0) atomicAdd(A.macs + 5, macs);
+}
+
+// Sigma_FB -= sum_{al,a} C_AF[al][a][f] Tsum[al][a][b],  Tsum = sum_{G in M3(F)} T3_G.
+__global__ void __launch_bounds__(kThreads) k_v3(ContractArgs A) {
+  __shared__ int glist[1024];
+  __shared__ int nsel_s;
+  __shared__ double Ts[kChunk];
+  const PairLoc L = locate(A, blockIdx.x, false);
+  const WorkItem it = A.items[L.w];
+  if (!(A.wf_flags[it.wf_off + L.idx] & 4u)) return;
+  if (it.nG > 1024) { if (threadIdx.x == 0) atomicOr(A.err, HFX_DEV_ERR_BOUNDS); return; }
+  const int f_ = L.idx;
+  const NbrEntry ef = A.nbr[it.fbase + f_];
+  const int pA = A.nabf[it.a], na = A.nao[it.a], nb = A.nao[it.b], nf = A.nao[ef.other];
+  const int nsel = ordered_select(it.nG, [&](int g) { return mask_bit(A, it, g, 2, f_); },
+                                  glist, &nsel_s);
+  const double *Tbase = A.scratch + A.t3_off[L.w - A.w0];
+  const double *Caf = A.C.data + A.C.offs[ef.cblk];
+  const int per = na * nb, nout = nf * nb;
+  double acc[kMaxOut];
+#pragma unroll
+  for (int q = 0; q < kMaxOut; ++q) acc[q] = 0.0;
+  const int ach = max(1, min(pA, kChunk / per));
+  unsigned long long macs = 0;
+  for (int al0 = 0; al0 < pA; al0 += ach) {
+    const int ac = min(ach, pA - al0);
+    for (int idx = threadIdx.x; idx < ac * per; idx += kThreads) {
+      double s = 0.0;
+      for (int k = 0; k < nsel; ++k) s += Tbase[((int64_t)glist[k] * pA + al0) * per + idx];
+      Ts[idx] = s;
+    }
+    macs += (unsigned long long)nsel * ac * per;
+    __syncthreads();
+    for (int q = 0; q < kMaxOut; ++q) {
+      const int o = threadIdx.x + q * kThreads;
+      if (o >= nout) break;
+      const int f = o / nb, b = o - f * nb;
+      double s = acc[q];
+      for (int al = 0; al < ac; ++al)
+        for (int a = 0; a < na; ++a)
+          s = fma(Caf[((int64_t)(al0 + al) * na + a) * nf + f], Ts[(al * na + a) * nb + b], s);
+      acc[q] = s;
+    }
+    macs += (unsigned long long)ac * nout * na;
+    __syncthreads();
+  }
+  const int64_t off = sig_offset(A, ef.other, it.b, it.n[0] - ef.n[0], it.n[1] - ef.n[1],
+                                 it.n[2] - ef.n[2]);
+  if (off >= 0)
+    for (int q = 0; q < kMaxOut; ++q) {
+      const int o = threadIdx.x + q * kThreads;
+      if (o >= nout) break;
+      fx_add(A.acc + 2 * (off + o), -acc[q]);
+    }
+  if (threadIdx.x == 0) atomicAdd(A.macs + 4, macs);
+}
+
+// Sigma_FG -= sum_{al,a} C_AF[al][a][f] P_G[al][a][g]   for every F in M4(G).
+__global__ void __launch_bounds__(kThreads) k_v4(ContractArgs A) {
+  __shared__ int flist[1024];
+  __shared__ int nsel_s;
+  const PairLoc L = locate(A, blockIdx.x, true);
+  const WorkItem it = A.items[L.w];
+  if (!(A.wg_flags[it.wg_off + L.idx] & 8u)) return;
+  if (it.nF > 1024) { if (threadIdx.x == 0) atomicOr(A.err, HFX_DEV_ERR_BOUNDS); return; }
+  const int g_ = L.idx;
+  const NbrEntry eg = A.nbr[it.gbase + g_];
+  const int pA = A.nabf[it.a], na = A.nao[it.a], ng = A.nao[eg.other];
+  const int nsel = ordered_select(it.nF, [&](int f) { return mask_bit(A, it, g_, 3, f); },
+                                  flist, &nsel_s);
+  const double *P = A.scratch + A.p_off[L.w - A.w0] + (int64_t)pA * na * eg.aopre;
+  const int K = pA * na;
+  const int nG0 = it.n[0] + eg.n[0], nG1 = it.n[1] + eg.n[1], nG2 = it.n[2] + eg.n[2];
+  unsigned long long macs = 0;
+  for (int k = 0; k < nsel; ++k) {
+    const NbrEntry ef = A.nbr[it.fbase + flist[k]];
+    const int nf = A.nao[ef.other];
+    const double *Caf = A.C.data + A.C.offs[ef.cblk];
+    const int nout = nf * ng;
+    const int64_t off = sig_offset(A, ef.other, eg.other, nG0 - ef.n[0], nG1 - ef.n[1],
+                                   nG2 - ef.n[2]);
+    for (int o = threadIdx.x; o < nout; o += kThreads) {
+      const int f = o / ng, g = o - f * ng;
+      double s = 0.0;
+      for (int r = 0; r < K; ++r) s = fma(Caf[(int64_t)r * nf + f], P[(int64_t)r * ng + g], s);
+      if (off >= 0) fx_add(A.acc + 2 * (off + o), -s);
+    }
+    macs += (unsigned long long)nout * K;
+  }
+  if (threadIdx.x == 0 && macs) atomicAdd(A.macs + 6, macs);
+}
+
+}  // namespace
+
+cudaError_t launch_contract_fp64(const ContractArgs &a, cudaStream_t st, cudaEvent_t *ev, int *nl) {
+  int n = 0;
+  auto mark = [&](int i) {
+    if (ev) cudaEventRecord(ev[i], st);
+  };
+  const unsigned gg = (unsigned)(a.nwg > 0 ? a.nwg : 0), gf = (unsigned)(a.nwf > 0 ? a.nwf : 0);
+  mark(0);
+  if (gg) { k_y<<<gg, kThreads, 0, st>>>(a); ++n; }
+  mark(1);
+  if (gg) { k_dstage<<<gg, kThreads, 0, st>>>(a); ++n; }
+  mark(2);
+  if (gf) { k_q<<<gf, kThreads, 0, st>>>(a); ++n; }
+  mark(3);
+  if (gf) { k_v1<<<gf, kThreads, 0, st>>>(a); ++n; }
+  mark(4);
+  if (gf) { k_v3<<<gf, kThreads, 0, st>>>(a); ++n; }
+  mark(5);
+  if (gg) { k_v2<<<gg, kThreads, 0, st>>>(a); ++n; }
+  mark(6);
+  if (gg) { k_v4<<<gg, kThreads, 0, st>>>(a); ++n; }
+  mark(7);
+  if (nl) *nl = n;
+  return cudaGetLastError();
+}

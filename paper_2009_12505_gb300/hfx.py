@@ -1,0 +1,206 @@
+"""Thin ctypes binding of libhfx (include/hfx.h): argument marshalling only.
+
+Every step of the build runs in the CUDA library.  Arrays may be numpy
+arrays (host) or torch CUDA tensors (device, passed by data pointer).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+HFX_FP64, HFX_BF16X3, HFX_OZAKI = 0, 1, 2
+_PREC = {"fp64": HFX_FP64, "bf16x3": HFX_BF16X3, "ozaki": HFX_OZAKI}
+_STATUS = {0: "HFX_OK", 1: "HFX_E_ARG", 2: "HFX_E_SHAPE", 3: "HFX_E_STATE", 4: "HFX_E_NOMEM",
+           5: "HFX_E_CUDA", 6: "HFX_E_TIMEOUT", 7: "HFX_E_NOTFOUND"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class HfxError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("version", ctypes.c_int32), ("prec", ctypes.c_int32), ("theta", ctypes.c_double),
+                ("n_sigma_blocks", ctypes.c_int64), ("n_work_items", ctypes.c_int64),
+                ("n_active_abg", ctypes.c_int64), ("survivors", ctypes.c_int64 * 4),
+                ("canonical_flops", ctypes.c_double), ("executed_flops", ctypes.c_double),
+                ("ms_screen", ctypes.c_double), ("ms_contract", ctypes.c_double),
+                ("ms_reduce", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("n_waves", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64),
+                ("kernel_ms", ctypes.c_double * 8), ("kernel_flops", ctypes.c_double * 8),
+                ("n_launches", ctypes.c_int64)]
+
+KERNELS = ["screen", "Y", "Dstage", "Q", "v1_DFG", "v3_DAG", "v2_DFB", "v4_DAB"]
+
+
+def build_library(force: bool = False, verbose: bool = False) -> str:
+    return _build.build(force=force, verbose=verbose)
+
+
+def load_library():
+    """Build (if stale) and load libhfx; raises if that is impossible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        P, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+        S = ctypes.c_int
+        sig = {
+            "hfx_create": (S, [P, i32, P, P, i32, P, P, P, P]),
+            "hfx_set_C": (S, [P, i32, i32, P, P]),
+            "hfx_set_V": (S, [P, i32, i32, P, P]),
+            "hfx_set_D": (S, [P, i32, i32, P, P]),
+            "hfx_set_many": (S, [P, ctypes.c_char, i64, P, P, P, ctypes.c_int]),
+            "hfx_clear": (S, [P, ctypes.c_char]),
+            "hfx_build": (S, [P, f64, ctypes.c_int, i32, P]),
+            "hfx_H_count": (S, [P, P]),
+            "hfx_H_keys": (S, [P, P]),
+            "hfx_H_offsets": (S, [P, P]),
+            "hfx_get_H": (S, [P, i32, i32, P, P]),
+            "hfx_get_H_all": (S, [P, P, ctypes.c_int]),
+            "hfx_grad": (S, [P, P, P]),
+            "hfx_stats": (S, [P, P]),
+            "hfx_last_error": (ctypes.c_char_p, [P]),
+            "hfx_destroy": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _p(a):
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+class Context:
+    """One periodic system.  nao/nabf are per-atom sizes."""
+
+    def __init__(self, nao, nabf, stream=None, lattice=None, pos=None):
+        self._lib = load_library()
+        nao = np.ascontiguousarray(nao, np.int32)
+        nabf = np.ascontiguousarray(nabf, np.int32)
+        natoms = nao.shape[0]
+        self.nao, self.nabf = nao, nabf
+        species = np.arange(natoms, dtype=np.int32)
+        lat = None if lattice is None else np.ascontiguousarray(lattice, np.float64).reshape(9)
+        ps = None if pos is None else np.ascontiguousarray(pos, np.float64).reshape(-1)
+        h = ctypes.c_void_p()
+        st = None if stream is None else ctypes.c_void_p(int(stream))
+        rc = self._lib.hfx_create(_p(lat), natoms, _p(ps), _p(species), natoms, _p(nao), _p(nabf),
+                                  st, ctypes.byref(h))
+        if rc != 0:
+            raise HfxError(rc, "hfx_create failed")
+        self._h = h
+
+    def _check(self, rc):
+        if rc != 0:
+            raise HfxError(rc, self._lib.hfx_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.hfx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_block(self, which: str, i: int, j: int, n, blk):
+        fn = {"C": self._lib.hfx_set_C, "V": self._lib.hfx_set_V, "D": self._lib.hfx_set_D}[which]
+        nn = np.ascontiguousarray(n, np.int32)
+        b = np.ascontiguousarray(blk, np.float64)
+        if not (0 <= i < len(self.nao) and 0 <= j < len(self.nao)):
+            raise HfxError(1, "atom index out of range")
+        need = {"C": self.nabf[i] * self.nao[i] * self.nao[j], "V": self.nabf[i] * self.nabf[j],
+                "D": self.nao[i] * self.nao[j]}[which]
+        if b.size != need or nn.size != 3:
+            raise HfxError(2, f"block has {b.size} values, the {which} block needs {need}")
+        self._check(fn(self._h, i, j, _p(nn), _p(b)))
+
+    def set_many(self, which: str, keys, data, offs, on_device: bool = False):
+        k = np.ascontiguousarray(keys, np.int32).reshape(-1, 5)
+        o = np.ascontiguousarray(offs, np.int64)
+        d = data if on_device else np.ascontiguousarray(data, np.float64)
+        n_data = d.numel() if hasattr(d, "numel") else d.size
+        if o.shape[0] != k.shape[0] + 1 or (k.shape[0] and (o[0] < 0 or o[-1] > n_data)):
+            raise HfxError(2, "offsets do not match the keys or exceed the data")
+        self._check(self._lib.hfx_set_many(self._h, which.encode(), k.shape[0], _p(k), _p(d),
+                                           _p(o), 1 if on_device else 0))
+
+    def set_blocks(self, which: str, blocks, on_device: bool = False):
+        """blocks: object with keys/data/offs (e.g. synth.Blocks)."""
+        self.set_many(which, blocks.keys, blocks.data, blocks.offs, on_device)
+
+    def clear(self, which: str):
+        self._check(self._lib.hfx_clear(self._h, which.encode()))
+
+    def build(self, theta: float, prec="fp64", nslices: int = 0) -> float:
+        ex = ctypes.c_double()
+        p = _PREC[prec] if isinstance(prec, str) else int(prec)
+        self._check(self._lib.hfx_build(self._h, float(theta), p, int(nslices), ctypes.byref(ex)))
+        return ex.value
+
+    def count(self) -> int:
+        n = ctypes.c_int64()
+        self._check(self._lib.hfx_H_count(self._h, ctypes.byref(n)))
+        return n.value
+
+    def keys(self) -> np.ndarray:
+        n = self.count()
+        out = np.zeros((n, 5), np.int32)
+        self._check(self._lib.hfx_H_keys(self._h, _p(out)))
+        return out
+
+    def offsets(self) -> np.ndarray:
+        out = np.zeros(self.count() + 1, np.int64)
+        self._check(self._lib.hfx_H_offsets(self._h, _p(out)))
+        return out
+
+    def sigma(self, out=None, on_device: bool = False):
+        """All Sigma blocks packed at offsets(); a numpy array, or fills ``out``."""
+        if out is None:
+            out = np.zeros(int(self.offsets()[-1]), np.float64)
+            on_device = False
+        self._check(self._lib.hfx_get_H_all(self._h, _p(out), 1 if on_device else 0))
+        return out
+
+    def get(self, i: int, j: int, n) -> np.ndarray:
+        out = np.zeros((int(self.nao[i]), int(self.nao[j])), np.float64)
+        nn = np.ascontiguousarray(n, np.int32)
+        self._check(self._lib.hfx_get_H(self._h, i, j, _p(nn), _p(out)))
+        return out
+
+    def grad(self, nC: int, nV: int):
+        dC = np.zeros(nC, np.float64)
+        dV = np.zeros(nV, np.float64)
+        self._check(self._lib.hfx_grad(self._h, _p(dC), _p(dV)))
+        return dC, dV
+
+    def stats(self) -> dict:
+        s = Stats()
+        self._check(self._lib.hfx_stats(self._h, ctypes.byref(s)))
+        d = {f: getattr(s, f) for f, _ in Stats._fields_}
+        d["survivors"] = list(s.survivors)
+        d["kernel_ms"] = dict(zip(KERNELS, list(s.kernel_ms)))
+        d["kernel_flops"] = dict(zip(KERNELS, list(s.kernel_flops)))
+        return d

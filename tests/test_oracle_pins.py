@@ -201,7 +201,7 @@ def test_threshold_is_strict():
     _, c_above = o.keys(s)
     assert c_at[0] - c_above[0] >= 1
     # values: theta = S drops the term exactly as theta just above S does
-    ref = o.blocks(np.nextafter(s, 1.0), [z])[0]
+    ref = o.blocks(np.nextafter(s, np.inf), [z])[0]
     np.testing.assert_array_equal(o.blocks(s, [z])[0], ref)
     assert np.abs(o.blocks(np.nextafter(s, 0.0), [z])[0] - ref).max() > 0.0
 
