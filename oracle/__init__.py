@@ -46,9 +46,9 @@ def _load():
             lib.orc_create.argtypes = [i32, P, P] + [i64, P, P, P] * 3
             lib.orc_destroy.argtypes = [P]
             lib.orc_keys.restype = i64
-            lib.orc_keys.argtypes = [P, f64, P, i64, P]
+            lib.orc_keys.argtypes = [P, f64, i32, i32, P, i64, P, P]
             lib.orc_blocks.restype = ctypes.c_int
-            lib.orc_blocks.argtypes = [P, f64, i64, P, P, P, ctypes.c_int]
+            lib.orc_blocks.argtypes = [P, f64, i64, P, P, P, ctypes.c_int, P]
             lib.orc_ex.restype = f64
             lib.orc_ex.argtypes = [P, i64, P, P, P]
             lib.orc_maxabs.argtypes = [P, ctypes.c_char, P]
@@ -95,27 +95,35 @@ class Oracle:
         except Exception:
             pass
 
-    def keys(self, theta: float):
+    def keys(self, theta: float, atoms=None, extra: bool = False):
         """Sigma key set at theta (sorted) and surviving terms per variant
-        (ABFs on (I,J), (I,L), (K,J), (K,L))."""
+        (ABFs on (I,J), (I,L), (K,J), (K,L)); ``atoms`` = (first, end) limits
+        the central atoms.  With ``extra`` also returns {"active_abg",
+        "canonical_flops"} (Algorithm 3 count, 2 flops per multiply-add)."""
+        a0, a1 = (0, 0) if atoms is None else atoms
         counts = np.zeros(4, np.int64)
-        n = self._lib.orc_keys(self._h, float(theta), None, 0, _ptr(counts))
+        ex = np.zeros(2, np.int64)
+        n = self._lib.orc_keys(self._h, float(theta), a0, a1, None, 0, _ptr(counts), _ptr(ex))
         keys = np.zeros((n, 5), np.int32)
-        self._lib.orc_keys(self._h, float(theta), _ptr(keys), n, _ptr(counts))
+        self._lib.orc_keys(self._h, float(theta), a0, a1, _ptr(keys), n, _ptr(counts), _ptr(ex))
+        if extra:
+            return keys, counts, {"active_abg": int(ex[0]), "canonical_flops": 2.0 * float(ex[1])}
         return keys, counts
 
-    def blocks(self, theta: float, keys, nthreads: int = 0):
-        """Sigma blocks for the given keys: (data, offs) packed in key order."""
+    def blocks(self, theta: float, keys, nthreads: int = 0, terms: bool = False):
+        """Sigma blocks for the given keys: (data, offs) packed in key order,
+        plus the surviving terms per block when ``terms``."""
         keys = np.ascontiguousarray(np.asarray(keys, np.int32).reshape(-1, 5))
         n = keys.shape[0]
         sizes = self.nao[keys[:, 0]].astype(np.int64) * self.nao[keys[:, 1]]
         out = np.zeros(int(sizes.sum()), np.float64)
         offs = np.zeros(n + 1, np.int64)
+        nterms = np.zeros(n, np.int64)
         rc = self._lib.orc_blocks(self._h, float(theta), n, _ptr(keys), _ptr(out), _ptr(offs),
-                                  int(nthreads))
+                                  int(nthreads), _ptr(nterms))
         if rc != 0:
             raise ValueError("oracle work buffers cover nao <= 64 and nabf <= 128")
-        return out, offs
+        return (out, offs, nterms) if terms else (out, offs)
 
     def ex(self, keys, data, offs) -> float:
         keys = np.ascontiguousarray(keys, np.int32)

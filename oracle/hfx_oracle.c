@@ -271,65 +271,113 @@ static int cmp_u64(const void *x, const void *y) {
 void orc_sort_u64(uint64_t *v, int64_t n) { qsort(v, (size_t)n, sizeof(uint64_t), cmp_u64); }
 
 /*
- * Enumerate the Sigma key set at theta: every (i, j, n) receiving at least one
- * surviving term, and the number of surviving terms per variant.  Returns the
- * number of keys; writes at most cap keys (sorted) when keys_out is non-null.
+ * Enumerate the Sigma key set at theta for central atoms i in [a0, a1): every
+ * (i, j, n) receiving at least one surviving term, and the number of
+ * surviving terms per variant.  Returns the number of keys; writes at most
+ * cap keys (sorted) when keys_out is non-null.  extra (nullable) receives
+ * [0] the number of distinct (A, B, G) triples with a surviving term and
+ * [1] the Algorithm 3 multiply-add count of the build: per surviving term the
+ * T and Ht contractions, per active (A, B, G) the product Y = V C_BG.
  */
-int64_t orc_keys(orc *o, double theta, int32_t *keys_out, int64_t cap, int64_t counts[4]) {
-  hmap_t keyset;
-  hm_init(&keyset, 1024);
-  int64_t cnt[4] = {0, 0, 0, 0};
-  for (int32_t i = 0; i < o->natoms; ++i) {
-    int32_t zero[3] = {0, 0, 0};
-    role_t *KI;
-    int64_t nK = roles_of(o, i, zero, &KI);
-    for (int64_t a = 0; a < nK; ++a) {
-      const role_t *eK = &KI[a];
-      const site_t *A = &eK->abf, *K = &eK->partner;
-      /* B: every site with V(A, B) */
-      for (int64_t tv = o->vout_start[A->a]; tv < o->vout_start[A->a + 1]; ++tv) {
-        const nbr_t *pv = &o->vout[tv];
-        const int64_t vb = pv->blk;
-        site_t B = {pv->other, {A->n[0] + pv->n[0], A->n[1] + pv->n[1], A->n[2] + pv->n[2]}};
-        const int64_t dKB = find_between(&o->D, K, &B);
-        /* every C(B, Y) block: either J = B with L = Y (ABFs on J), or L = B with
-         * J = Y != B (ABFs on L) */
-        for (int64_t t = o->cout_start[B.a]; t < o->cout_start[B.a + 1]; ++t) {
-          const nbr_t *p = &o->cout[t];
-          site_t Y = {p->other, {B.n[0] + p->n[0], B.n[1] + p->n[1], B.n[2] + p->n[2]}};
-          role_t eL;
-          /* J = B, L = Y */
-          int64_t d = find_between(&o->D, K, &Y);
-          if (d >= 0) {
-            eL.partner = Y; eL.abf = B; eL.cblk = p->blk; eL.transposed = 0;
-            if (screen_S(o, eK, &eL, vb, d) > theta) {
-              cnt[variant_of(eK, &eL)]++;
-              hm_put(&keyset, pack_key(i, B.a, B.n[0], B.n[1], B.n[2]), 0);
+int64_t orc_keys(orc *o, double theta, int32_t a0, int32_t a1, int32_t *keys_out, int64_t cap,
+                 int64_t counts[4], int64_t extra[2]) {
+  if (a0 < 0) a0 = 0;
+  if (a1 > o->natoms || a1 <= 0) a1 = o->natoms;
+  int nth = 1;
+#ifdef _OPENMP
+  nth = omp_get_max_threads();
+#endif
+  hmap_t *keysets = (hmap_t *)malloc(sizeof(hmap_t) * nth);
+  hmap_t *triples = (hmap_t *)malloc(sizeof(hmap_t) * nth);
+  int64_t *cnt = (int64_t *)calloc((size_t)nth * 5, sizeof(int64_t));
+  for (int t = 0; t < nth; ++t) { hm_init(&keysets[t], 1024); hm_init(&triples[t], 1024); }
+#pragma omp parallel num_threads(nth)
+  {
+    int tid = 0;
+#ifdef _OPENMP
+    tid = omp_get_thread_num();
+#endif
+    hmap_t *ks = &keysets[tid], *tr = &triples[tid];
+    int64_t *c = cnt + 5 * tid;
+#pragma omp for schedule(dynamic, 1)
+    for (int32_t i = a0; i < a1; ++i) {
+      int32_t zero[3] = {0, 0, 0};
+      site_t I = {i, {0, 0, 0}};
+      role_t *KI;
+      int64_t nK = roles_of(o, i, zero, &KI);
+      for (int64_t a = 0; a < nK; ++a) {
+        const role_t *eK = &KI[a];
+        const site_t *A = &eK->abf, *K = &eK->partner;
+        const site_t *F = same_site(A, &I) ? K : &I;   /* the AO site without the ABFs */
+        const int64_t pA = o->nabf[A->a], na = o->nao[A->a], nf = o->nao[F->a];
+        /* B: every site with V(A, B) */
+        for (int64_t tv = o->vout_start[A->a]; tv < o->vout_start[A->a + 1]; ++tv) {
+          const nbr_t *pv = &o->vout[tv];
+          const int64_t vb = pv->blk;
+          site_t B = {pv->other, {A->n[0] + pv->n[0], A->n[1] + pv->n[1], A->n[2] + pv->n[2]}};
+          const int64_t pB = o->nabf[B.a], nb = o->nao[B.a];
+          const int64_t dKB = find_between(&o->D, K, &B);
+          /* every C(B, Y) block: either J = B with L = Y (ABFs on J), or L = B with
+           * J = Y != B (ABFs on L); in both cases Y is the site G without ABFs */
+          for (int64_t t = o->cout_start[B.a]; t < o->cout_start[B.a + 1]; ++t) {
+            const nbr_t *p = &o->cout[t];
+            site_t Y = {p->other, {B.n[0] + p->n[0], B.n[1] + p->n[1], B.n[2] + p->n[2]}};
+            const int64_t ng = o->nao[Y.a];
+            int alive = 0;
+            role_t eL;
+            /* J = B, L = Y */
+            int64_t d = find_between(&o->D, K, &Y);
+            if (d >= 0) {
+              eL.partner = Y; eL.abf = B; eL.cblk = p->blk; eL.transposed = 0;
+              if (screen_S(o, eK, &eL, vb, d) > theta) {
+                const int v = variant_of(eK, &eL);
+                c[v]++;
+                alive = 1;
+                /* v1: T[al,b,f] over g, Ht over (al,f);  v3: T[al,a,b] over g, Ht over (al,a) */
+                c[4] += v == 0 ? pA * nb * nf * (ng + na) : pA * na * nb * (ng + nf);
+                hm_put(ks, pack_key(i, B.a, B.n[0], B.n[1], B.n[2]), 0);
+              }
             }
-          }
-          /* L = B, J = Y */
-          if (dKB >= 0 && !same_site(&Y, &B)) {
-            eL.partner = B; eL.abf = B; eL.cblk = p->blk; eL.transposed = 1;
-            if (screen_S(o, eK, &eL, vb, dKB) > theta) {
-              cnt[variant_of(eK, &eL)]++;
-              hm_put(&keyset, pack_key(i, Y.a, Y.n[0], Y.n[1], Y.n[2]), 0);
+            /* L = B, J = Y */
+            if (dKB >= 0 && !same_site(&Y, &B)) {
+              eL.partner = B; eL.abf = B; eL.cblk = p->blk; eL.transposed = 1;
+              if (screen_S(o, eK, &eL, vb, dKB) > theta) {
+                const int v = variant_of(eK, &eL);
+                c[v]++;
+                alive = 1;
+                /* v2: T[al,f,g] over b, Ht over (al,f);  v4: T[al,a,g] over b, Ht over (al,a) */
+                c[4] += v == 1 ? pA * nf * ng * (nb + na) : pA * na * ng * (nb + nf);
+                hm_put(ks, pack_key(i, Y.a, Y.n[0], Y.n[1], Y.n[2]), 0);
+              }
             }
+            /* (A, B, G) with A moved to the home cell: (V block, C(B,G) block) */
+            if (alive) hm_put(tr, ((uint64_t)vb << 32) | (uint64_t)p->blk, pA * pB * nb * ng);
           }
         }
       }
+      free(KI);
     }
-    free(KI);
   }
-  /* collect and sort keys; the +128 offsets make the packed order (i, j, n1, n2, n3) */
-  int64_t nk = keyset.count;
-  uint64_t *ks = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nk > 0 ? nk : 1));
+  /* merge: keys are disjoint per central atom, triples are not */
+  int64_t nk = 0;
+  for (int t = 0; t < nth; ++t) nk += keysets[t].count;
+  uint64_t *kall = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)(nk > 0 ? nk : 1));
   int64_t c = 0;
-  for (uint64_t s = 0; s <= keyset.mask; ++s)
-    if (keyset.keys[s] != EMPTY_KEY) ks[c++] = keyset.keys[s];
-  orc_sort_u64(ks, nk);
+  for (int t = 0; t < nth; ++t)
+    for (uint64_t sl = 0; sl <= keysets[t].mask; ++sl)
+      if (keysets[t].keys[sl] != EMPTY_KEY) kall[c++] = keysets[t].keys[sl];
+  orc_sort_u64(kall, nk);
+  hmap_t tall;
+  hm_init(&tall, 1024);
+  for (int t = 0; t < nth; ++t)
+    for (uint64_t sl = 0; sl <= triples[t].mask; ++sl)
+      if (triples[t].keys[sl] != EMPTY_KEY) hm_put(&tall, triples[t].keys[sl], triples[t].vals[sl]);
+  int64_t ymacs = 0;
+  for (uint64_t sl = 0; sl <= tall.mask; ++sl)
+    if (tall.keys[sl] != EMPTY_KEY) ymacs += tall.vals[sl];
   if (keys_out) {
     for (int64_t e = 0; e < nk && e < cap; ++e) {
-      uint64_t k = ks[e];
+      uint64_t k = kall[e];
       keys_out[5 * e + 0] = (int32_t)(k >> 44);
       keys_out[5 * e + 1] = (int32_t)((k >> 24) & 0xFFFFF);
       keys_out[5 * e + 2] = (int32_t)((k >> 16) & 0xFF) - 128;
@@ -337,12 +385,16 @@ int64_t orc_keys(orc *o, double theta, int32_t *keys_out, int64_t cap, int64_t c
       keys_out[5 * e + 4] = (int32_t)(k & 0xFF) - 128;
     }
   }
-  if (counts) for (int v = 0; v < 4; ++v) counts[v] = cnt[v];
-  free(ks);
-  hm_free(&keyset);
+  int64_t tot[5] = {0, 0, 0, 0, 0};
+  for (int t = 0; t < nth; ++t)
+    for (int v = 0; v < 5; ++v) tot[v] += cnt[5 * t + v];
+  if (counts) for (int v = 0; v < 4; ++v) counts[v] = tot[v];
+  if (extra) { extra[0] = tall.count; extra[1] = tot[4] + ymacs; }
+  for (int t = 0; t < nth; ++t) { hm_free(&keysets[t]); hm_free(&triples[t]); }
+  free(keysets); free(triples); free(cnt); free(kall);
+  hm_free(&tall);
   return nk;
 }
-
 
 /* Neumaier-compensated accumulation. */
 static void kahan_add(double *s, double *c, double x) {
@@ -372,8 +424,9 @@ enum { MAXAO = 64, MAXABF = 128, SLAB = MAXABF * MAXAO * MAXAO };
  * Sigma block (I, J) for I = (i, 0), J = (j, n): Algorithm 1 for one pair.
  * out has nao(i) * nao(j) doubles (row-major [i][j]).
  */
-static void sigma_block(const orc *o, double theta, int32_t i, int32_t j, const int32_t nJ[3],
-                        double *out, double *work) {
+static int64_t sigma_block(const orc *o, double theta, int32_t i, int32_t j, const int32_t nJ[3],
+                           double *out, double *work) {
+  int64_t nterms = 0;
   const int ni = o->nao[i], nj = o->nao[j];
   int32_t zero[3] = {0, 0, 0};
   role_t *KI, *LJ;
@@ -402,6 +455,7 @@ static void sigma_block(const orc *o, double theta, int32_t i, int32_t j, const 
       const int64_t v = find_between(&o->V, A, B);
       if (v < 0) continue;
       if (!(screen_S(o, eK, eL, v, d) > theta)) continue;
+      ++nterms;
       const int nk = o->nao[K->a];
       const int pA = o->nabf[A->a];
       const double *Vb = o->V.data + o->V.offs[v];
@@ -454,6 +508,7 @@ static void sigma_block(const orc *o, double theta, int32_t i, int32_t j, const 
   for (int t = 0; t < ni * nj; ++t) out[t] = acc[t] + cmp[t];
   free(KI);
   free(LJ);
+  return nterms;
 }
 
 /* Work buffer size (doubles) per thread for sigma_block. */
@@ -462,11 +517,13 @@ static int64_t work_doubles(void) { return 2 * MAXAO * MAXAO + 5 * (int64_t)SLAB
 /*
  * Compute the requested Sigma blocks.  req_keys: nreq x 5 (i, j, n1, n2, n3)
  * with arbitrary (i, j, n); out_offs: nreq + 1 offsets into out (filled here).
- * nthreads <= 0 uses the OpenMP default.  Returns 0, or -1 on a size the
- * oracle's work buffers do not cover (nao > 64 or nabf > 128).
+ * nthreads <= 0 uses the OpenMP default.  terms_out (nullable, nreq entries)
+ * receives the number of surviving terms summed into each block.  Returns 0,
+ * or -1 on a size the oracle's work buffers do not cover (nao > 64 or
+ * nabf > 128).
  */
 int orc_blocks(orc *o, double theta, int64_t nreq, const int32_t *req_keys, double *out,
-               int64_t *out_offs, int nthreads) {
+               int64_t *out_offs, int nthreads, int64_t *terms_out) {
   for (int32_t a = 0; a < o->natoms; ++a)
     if (o->nao[a] > MAXAO || o->nabf[a] > MAXABF) return -1;
   out_offs[0] = 0;
@@ -482,7 +539,8 @@ int orc_blocks(orc *o, double theta, int64_t nreq, const int32_t *req_keys, doub
     for (int64_t r = 0; r < nreq; ++r) {
       const int32_t *k = req_keys + 5 * r;
       int32_t n[3] = {k[2], k[3], k[4]};
-      sigma_block(o, theta, k[0], k[1], n, out + out_offs[r], work);
+      const int64_t nt = sigma_block(o, theta, k[0], k[1], n, out + out_offs[r], work);
+      if (terms_out) terms_out[r] = nt;
     }
     free(work);
   }

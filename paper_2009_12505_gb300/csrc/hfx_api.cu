@@ -388,7 +388,7 @@ hfx_status build_plan(hfx_ctx *ctx) {
 size_t scratch_budget_doubles() {
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
-  size_t budget = std::min<size_t>((size_t)8 << 30, freeb * 2 / 5);
+  size_t budget = std::min<size_t>((size_t)32 << 30, freeb * 2 / 5);
   if (const char *e = std::getenv("HFX_SCRATCH_MB")) {
     const long long mb = std::atoll(e);
     if (mb > 0) budget = (size_t)mb << 20;

@@ -184,3 +184,14 @@ def test_error_paths():
     # a threshold above every S: no surviving term, empty key set, E_X = 0
     assert c.build(1e30) == 0.0
     assert c.count() == 0
+
+
+@pytest.mark.parametrize("make,theta", [(synth.si_shrunk, 1e-2), (synth.si8, 1e-6)])
+def test_flop_accounting_matches_oracle(make, theta):
+    """The library's canonical flop count and active (A,B,G) count equal the
+    oracle's, which equals Table 1 per quadruple (test_flop_accounting)."""
+    wl = make()
+    _, _, extra = oracle.Oracle.of(wl).keys(theta, extra=True)
+    _, g = gpu_build(wl, theta)
+    assert g["stats"]["canonical_flops"] == extra["canonical_flops"]
+    assert g["stats"]["n_active_abg"] == extra["active_abg"]
