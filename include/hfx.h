@@ -188,6 +188,44 @@ typedef struct {
 
 hfx_status hfx_stats(const hfx_ctx *ctx, void *stats);
 
+/*
+ * One exchange term, contracted on the GPU without allocating any device
+ * memory.  The paper has no counterpart to this entry point; it exists for
+ * callers that cannot allocate device memory at call time -- a host framework
+ * that owns the GPU's memory through its own pool and forbids direct
+ * cudaMalloc, a latency-critical loop where cudaMalloc/cudaFree (which may
+ * synchronize the device) are not allowed, or a process whose device memory is
+ * already fully reserved by another allocator.
+ *
+ * Computes, on cuda_stream (NULL = legacy default stream),
+ *   out[i][j] = sum_{alpha,beta,k,l} cA[alpha][i][k] V[alpha][beta] cB[beta][j][l] D[k][l]
+ * in the C((VC)D) order the build uses (Y = V cB, T = Y D, out = cA T).  The
+ * exchange matrix receives minus this term.
+ *   cA  [nabf_a][nao_i][nao_k]   V [nabf_a][nabf_b]
+ *   cB  [nabf_b][nao_j][nao_l]   D [nao_k][nao_l]    out [nao_i][nao_j]
+ * All pointers are device memory on the current device, row-major FP64, owned
+ * by the caller; out is overwritten.
+ *
+ * Working memory: the two intermediates Y and T live in one fixed 2 MiB static
+ * device array (each at most 131072 doubles: nabf_a*nao_j*nao_l and
+ * nabf_a*nao_j*nao_k must both be <= 131072, else HFX_E_SHAPE).  Every GPU
+ * that loads the library holds that array until the process exits.  The first
+ * call on each device looks the array's address up (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  No
+ * call allocates or frees device memory.  All calls share the one array:
+ * calls whose kernels overlap on the GPU (different streams, or different host
+ * threads on one device) race on it and give wrong results -- order them on
+ * one stream.  Each call writes every intermediate element it reads, so
+ * nothing from an earlier call leaks into the result.
+ *
+ * The call is asynchronous: results are in out once the stream reaches them.
+ * Errors: HFX_E_ARG (null pointer, size < 1), HFX_E_SHAPE (intermediates
+ * larger than the static array), HFX_E_CUDA (device lookup or launch failed).
+ */
+hfx_status hfx_term_noalloc(int32_t nabf_a, int32_t nabf_b, int32_t nao_i, int32_t nao_k,
+                            int32_t nao_j, int32_t nao_l, const double *cA, const double *V,
+                            const double *cB, const double *D, double *out, void *cuda_stream);
+
 /* Message for the last failing call on ctx (never NULL; "" when none). */
 const char *hfx_last_error(const hfx_ctx *ctx);
 

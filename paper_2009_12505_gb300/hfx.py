@@ -72,6 +72,7 @@ def load_library():
             "hfx_grad": (S, [P, P, P]),
             "hfx_stats": (S, [P, P]),
             "hfx_last_error": (ctypes.c_char_p, [P]),
+            "hfx_term_noalloc": (S, [i32, i32, i32, i32, i32, i32, P, P, P, P, P, P]),
             "hfx_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
@@ -88,6 +89,21 @@ def _p(a):
     if hasattr(a, "data_ptr"):
         return ctypes.c_void_p(a.data_ptr())
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def term_noalloc(cA, V, cB, D, out, stream=None):
+    """hfx_term_noalloc on device tensors: out[i][j] = sum cA[a][i][k] V[a][b] cB[b][j][l] D[k][l].
+
+    cA (nabf_a, nao_i, nao_k), V (nabf_a, nabf_b), cB (nabf_b, nao_j, nao_l),
+    D (nao_k, nao_l), out (nao_i, nao_j): contiguous float64 CUDA tensors."""
+    lib = load_library()
+    pa, ni, nk = cA.shape
+    pb, nj, nl = cB.shape
+    st = None if stream is None else ctypes.c_void_p(int(stream))
+    rc = lib.hfx_term_noalloc(pa, pb, ni, nk, nj, nl, _p(cA), _p(V), _p(cB), _p(D), _p(out), st)
+    if rc != 0:
+        raise HfxError(rc, "hfx_term_noalloc failed")
+    return out
 
 
 class Context:
