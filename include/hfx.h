@@ -226,6 +226,18 @@ hfx_status hfx_term_noalloc(int32_t nabf_a, int32_t nabf_b, int32_t nao_i, int32
                             int32_t nao_j, int32_t nao_l, const double *cA, const double *V,
                             const double *cB, const double *D, double *out, void *cuda_stream);
 
+/*
+ * Self-check of the split-precision tensor-core product used by HFX_OZAKI
+ * (the matrix products of Appendix A's C((VC)D) chain):
+ *   C[M][N] = A[M][K] B[K][N]  (host, row-major FP64), 1 <= K <= 640,
+ * computed from nslices (1..6) balanced base-128 digits per operand row with
+ * exact tensor-core group sums (see the header of the library's Ozaki
+ * kernels).  Allocates its own temporary device memory.  Errors: HFX_E_ARG,
+ * HFX_E_NOMEM, HFX_E_CUDA, HFX_E_TIMEOUT.
+ */
+hfx_status hfx_selftest_ozaki(int32_t M, int32_t N, int32_t K, const double *A, const double *B,
+                              double *C, int32_t nslices);
+
 /* Message for the last failing call on ctx (never NULL; "" when none). */
 const char *hfx_last_error(const hfx_ctx *ctx);
 

@@ -107,6 +107,7 @@ enum : unsigned {
   HFX_DEV_ERR_NONFINITE = 2u,   // NaN/Inf in an input block
   HFX_DEV_ERR_MISSING = 4u,     // a Sigma key looked up by a contraction is absent
   HFX_DEV_ERR_BOUNDS = 8u,      // a size exceeded a kernel's compiled limit
+  HFX_DEV_ERR_TIMEOUT = 16u,    // a bounded device wait expired
 };
 
 // Limits of the FP64 kernels' shared-memory staging.

@@ -73,6 +73,7 @@ def load_library():
             "hfx_stats": (S, [P, P]),
             "hfx_last_error": (ctypes.c_char_p, [P]),
             "hfx_term_noalloc": (S, [i32, i32, i32, i32, i32, i32, P, P, P, P, P, P]),
+            "hfx_selftest_ozaki": (S, [i32, i32, i32, P, P, P, i32]),
             "hfx_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
@@ -89,6 +90,21 @@ def _p(a):
     if hasattr(a, "data_ptr"):
         return ctypes.c_void_p(a.data_ptr())
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def selftest_ozaki(A, B, nslices: int):
+    """C = A @ B (host FP64) through the split-precision tensor-core product."""
+    lib = load_library()
+    A = np.ascontiguousarray(A, np.float64)
+    B = np.ascontiguousarray(B, np.float64)
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    C = np.zeros((M, N), np.float64)
+    rc = lib.hfx_selftest_ozaki(M, N, K, _p(A), _p(B), _p(C), int(nslices))
+    if rc != 0:
+        raise HfxError(rc, "hfx_selftest_ozaki failed")
+    return C
 
 
 def term_noalloc(cA, V, cB, D, out, stream=None):
