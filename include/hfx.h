@@ -184,6 +184,9 @@ typedef struct {
   double kernel_ms[8];
   double kernel_flops[8];   /* multiply-adds x 2 issued by each kernel */
   int64_t n_launches;       /* kernels this build launched */
+  int32_t mirror;           /* 1: V and D were exactly Hermitian and the mirror pieces were used */
+  int32_t nslices;          /* digits per operand in HFX_OZAKI mode, else 0 */
+  double kernel_tensor_flops[8]; /* bf16 tensor-core flops issued per kernel (HFX_OZAKI) */
 } hfx_stats_v1;
 
 hfx_status hfx_stats(const hfx_ctx *ctx, void *stats);

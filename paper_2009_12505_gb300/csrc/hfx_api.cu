@@ -16,10 +16,12 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
 #include "hfx_internal.h"
+#include "hfx_split.h"
 
 namespace {
 
@@ -102,7 +104,7 @@ struct hfx_ctx {
   int64_t nwg = 0, nwf = 0, nmask = 0;
   DevBuf<NbrEntry> d_nbr;
   DevBuf<WorkItem> d_items;
-  DevBuf<int32_t> d_nao, d_nabf;
+  DevBuf<int32_t> d_nao, d_nabf, d_ncol;
   std::unordered_map<uint64_t, int64_t> dindex;
   DevBuf<uint64_t> d_dhkeys;
   DevBuf<int64_t> d_dhvals;
@@ -135,6 +137,21 @@ struct hfx_ctx {
   DevBuf<double> d_scratch;
   DevBuf<int64_t> d_waveoffs;
 
+  // split-precision (HFX_OZAKI) operands
+  int split_ks = 0;
+  DevBuf<__nv_bfloat16> d_cy, d_c4, d_vs, d_ps;
+  DevBuf<int16_t> d_cy_e, d_c4_e, d_vs_e, d_ps_e;
+  DevBuf<int64_t> d_split_meta;   // cy_base, cy_rowpre, c4_base, c4_rowpre, vs_base, v_rowpre, nc_start
+  DevBuf<int32_t> d_kt;           // ktY, kt4
+  std::vector<int32_t> ktY, kt4;
+  int64_t h_cy_rows = 0, h_c4_rows = 0, h_v_rows = 0;
+  DevBuf<int64_t> d_wave_split;   // p_rowpre, ps_base, y_candpre, v4_candpre
+  DevBuf<Job> d_jobs, d_jobs4;
+  DevBuf<int> d_njobs;
+  DevBuf<unsigned long long> d_tmacs;
+  cudaEvent_t sev[4] = {nullptr, nullptr, nullptr, nullptr};
+
+  bool sym = false;             // V and D blocks all have transposed mirrors
   bool results_valid = false;
   double ex = 0.0;
   hfx_stats_v1 stats{};
@@ -341,6 +358,12 @@ hfx_status build_plan(hfx_ctx *ctx) {
       it.mask_off = mk;
       it.wg_off = wg;
       it.wf_off = wf;
+      // role of the pair under the mirror map <A,B> -> <B,A>
+      const bool self = k[0] == k[1] && k[2] == 0 && k[3] == 0 && k[4] == 0;
+      const bool canon = k[0] < k[1] || (k[0] == k[1] && std::make_tuple(k[2], k[3], k[4]) >
+                                                             std::make_tuple(0, 0, 0));
+      it.role = self ? 0 : canon ? 1 : 2;
+      it.pad = 0;
       mk += (int64_t)it.nG * 4 * it.nFw;
       wg += it.nG;
       wf += it.nF;
@@ -348,6 +371,10 @@ hfx_status build_plan(hfx_ctx *ctx) {
     ctx->nwg = wg;
     ctx->nwf = wf;
     ctx->nmask = mk;
+    std::vector<int32_t> ncol(ctx->aotot.begin(), ctx->aotot.end());
+    CK(ctx->d_ncol.reserve(n));
+    CK(cudaMemcpyAsync(ctx->d_ncol.p, ncol.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
     CK(ctx->d_nbr.reserve(ctx->nbr.size()));
     if (!ctx->nbr.empty())
       CK(cudaMemcpyAsync(ctx->d_nbr.p, ctx->nbr.data(), sizeof(NbrEntry) * ctx->nbr.size(),
@@ -383,6 +410,142 @@ hfx_status build_plan(hfx_ctx *ctx) {
   C.keys_changed = V.keys_changed = D.keys_changed = false;
   ctx->plan_valid = true;
   return HFX_OK;
+}
+
+// Bitwise check that every block of kind k has its mirror key (j, i, -n) and
+// that the mirror equals its transpose.
+hfx_status check_mirror(hfx_ctx *ctx, int k, bool *ok) {
+  Kind &K = ctx->K[k];
+  cudaStream_t st = ctx->stream;
+  const int64_t n = (int64_t)K.keys.size();
+  std::vector<int64_t> mir(n);
+  std::vector<int32_t> rows(n);
+  for (int64_t e = 0; e < n; ++e) {
+    int32_t q[5];
+    hk_unpack(K.keys[e], q);
+    const uint64_t mk = hk_pack(q[1], q[0], -q[2], -q[3], -q[4]);
+    auto it = std::lower_bound(K.keys.begin(), K.keys.end(), mk);
+    mir[e] = (it != K.keys.end() && *it == mk) ? (int64_t)(it - K.keys.begin()) : -1;
+    rows[e] = k == 1 ? ctx->nabf[q[0]] : ctx->nao[q[0]];
+  }
+  int64_t *d_mir = nullptr;
+  int32_t *d_rows = nullptr;
+  unsigned *d_bad = nullptr;
+  CK(cudaMalloc((void **)&d_mir, sizeof(int64_t) * (n ? n : 1)));
+  CK(cudaMalloc((void **)&d_rows, sizeof(int32_t) * (n ? n : 1)));
+  CK(cudaMalloc((void **)&d_bad, sizeof(unsigned)));
+  CK(cudaMemsetAsync(d_bad, 0, sizeof(unsigned), st));
+  CK(cudaMemcpyAsync(d_mir, mir.data(), sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(d_rows, rows.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+  CK(launch_check_mirror(K.data.p, K.d_offs.p, d_mir, d_rows, n, d_bad, st));
+  ctx->launches += n > 0;
+  unsigned bad = 0;
+  CK(cudaMemcpyAsync(&bad, d_bad, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  cudaFree(d_mir);
+  cudaFree(d_rows);
+  cudaFree(d_bad);
+  *ok = bad == 0;
+  return HFX_OK;
+}
+
+// Digit-sliced C (two layouts) and V for the split-precision products.
+hfx_status split_prepare(hfx_ctx *ctx, int ks) {
+  cudaStream_t st = ctx->stream;
+  const int n = ctx->natoms;
+  const int64_t nv = (int64_t)ctx->items.size();
+  const int TM = 128, NT = 64, TK = 32;
+  ctx->ktY.assign(n, 0);
+  ctx->kt4.assign(n, 0);
+  std::vector<int64_t> cy_base(n + 1, 0), cy_row(n + 1, 0), c4_base(n + 1, 0), c4_row(n + 1, 0);
+  for (int x = 0; x < n; ++x) {
+    const int64_t nx = ctx->nao[x], px = ctx->nabf[x], ncol = ctx->aotot[x];
+    ctx->ktY[x] = (int32_t)((px + TK - 1) / TK);
+    ctx->kt4[x] = (int32_t)((px * nx + TK - 1) / TK);
+    const int64_t mty = (nx * ncol + TM - 1) / TM, mt4 = (ncol + TM - 1) / TM;
+    cy_row[x + 1] = cy_row[x] + mty * TM;
+    c4_row[x + 1] = c4_row[x] + mt4 * TM;
+    cy_base[x + 1] = cy_base[x] + mty * ctx->ktY[x] * ks * TM * TK;
+    c4_base[x + 1] = c4_base[x] + mt4 * ctx->kt4[x] * ks * TM * TK;
+  }
+  std::vector<int64_t> vs_base(nv + 1, 0), v_row(nv + 1, 0);
+  for (int64_t e = 0; e < nv; ++e) {
+    const WorkItem &it = ctx->items[e];
+    const int64_t ntv = (ctx->nabf[it.a] + NT - 1) / NT;
+    v_row[e + 1] = v_row[e] + ntv * NT;
+    vs_base[e + 1] = vs_base[e] + ntv * ctx->ktY[it.b] * ks * NT * TK;
+  }
+  ctx->h_cy_rows = cy_row[n];
+  ctx->h_c4_rows = c4_row[n];
+  ctx->h_v_rows = v_row[nv];
+  CK(ctx->d_cy.reserve(cy_base[n]));
+  CK(ctx->d_c4.reserve(c4_base[n]));
+  CK(ctx->d_vs.reserve(vs_base[nv]));
+  CK(ctx->d_cy_e.reserve(cy_row[n]));
+  CK(ctx->d_c4_e.reserve(c4_row[n]));
+  CK(ctx->d_vs_e.reserve(v_row[nv]));
+  std::vector<int64_t> meta;
+  meta.insert(meta.end(), cy_base.begin(), cy_base.end());
+  meta.insert(meta.end(), cy_row.begin(), cy_row.end());
+  meta.insert(meta.end(), c4_base.begin(), c4_base.end());
+  meta.insert(meta.end(), c4_row.begin(), c4_row.end());
+  meta.insert(meta.end(), vs_base.begin(), vs_base.end());
+  meta.insert(meta.end(), v_row.begin(), v_row.end());
+  meta.insert(meta.end(), ctx->nc_start.begin(), ctx->nc_start.end());
+  CK(ctx->d_split_meta.reserve(meta.size()));
+  CK(cudaMemcpyAsync(ctx->d_split_meta.p, meta.data(), sizeof(int64_t) * meta.size(),
+                     cudaMemcpyHostToDevice, st));
+  std::vector<int32_t> kt(ctx->ktY);
+  kt.insert(kt.end(), ctx->kt4.begin(), ctx->kt4.end());
+  CK(ctx->d_kt.reserve(kt.size()));
+  CK(cudaMemcpyAsync(ctx->d_kt.p, kt.data(), sizeof(int32_t) * kt.size(), cudaMemcpyHostToDevice,
+                     st));
+  CK(cudaStreamSynchronize(st));
+  ctx->split_ks = ks;
+  return HFX_OK;
+}
+
+SplitShared split_shared(hfx_ctx *ctx) {
+  SplitShared S{};
+  const int n = ctx->natoms;
+  const int64_t nv = (int64_t)ctx->items.size();
+  const int64_t *m = ctx->d_split_meta.p;
+  S.natoms = n;
+  S.nv = nv;
+  S.nao = ctx->d_nao.p;
+  S.nabf = ctx->d_nabf.p;
+  S.ncol = ctx->d_ncol.p;
+  S.ktY = ctx->d_kt.p;
+  S.kt4 = ctx->d_kt.p + n;
+  S.cy_base = m;
+  S.cy_rowpre = m + (n + 1);
+  S.c4_base = m + 2 * (n + 1);
+  S.c4_rowpre = m + 3 * (n + 1);
+  S.vs_base = m + 4 * (n + 1);
+  S.v_rowpre = m + 4 * (n + 1) + (nv + 1);
+  S.nc_start = m + 4 * (n + 1) + 2 * (nv + 1);
+  S.nbr = ctx->d_nbr.p;
+  S.items = ctx->d_items.p;
+  S.Cd = ctx->K[0].data.p;
+  S.Co = ctx->K[0].d_offs.p;
+  S.Vd = ctx->K[1].data.p;
+  S.Vo = ctx->K[1].d_offs.p;
+  S.masks = ctx->d_masks.p;
+  S.wg = ctx->d_wg.p;
+  S.shash = DevHash{ctx->d_shkeys.p, ctx->d_shvals.p, ctx->smask};
+  S.acc = ctx->d_acc.p;
+  S.err = ctx->d_err.p;
+  S.sym = ctx->sym ? 1 : 0;
+  S.cy = ctx->d_cy.p;
+  S.cy_e = ctx->d_cy_e.p;
+  S.c4 = ctx->d_c4.p;
+  S.c4_e = ctx->d_c4_e.p;
+  S.vs = ctx->d_vs.p;
+  S.vs_e = ctx->d_vs_e.p;
+  S.h_cy_rows = ctx->h_cy_rows;
+  S.h_c4_rows = ctx->h_c4_rows;
+  S.h_v_rows = ctx->h_v_rows;
+  return S;
 }
 
 size_t scratch_budget_doubles() {
@@ -451,6 +614,8 @@ hfx_status hfx_create(const double lattice[9], int32_t natoms, const double *pos
     if (cudaEventCreate(&ctx->ev[e]) != cudaSuccess) s = HFX_E_CUDA;
   for (int e = 0; s == HFX_OK && e < 10; ++e)
     if (cudaEventCreate(&ctx->kev[e]) != cudaSuccess) s = HFX_E_CUDA;
+  for (int e = 0; s == HFX_OK && e < 4; ++e)
+    if (cudaEventCreate(&ctx->sev[e]) != cudaSuccess) s = HFX_E_CUDA;
   if (s != HFX_OK) {
     hfx_destroy(ctx);
     return s;
@@ -465,6 +630,8 @@ void hfx_destroy(hfx_ctx *ctx) {
   for (auto &e : ctx->ev)
     if (e) cudaEventDestroy(e);
   for (auto &e : ctx->kev)
+    if (e) cudaEventDestroy(e);
+  for (auto &e : ctx->sev)
     if (e) cudaEventDestroy(e);
   delete ctx;
 }
@@ -563,9 +730,12 @@ hfx_status hfx_clear(hfx_ctx *ctx, char which) {
 hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices, double *ex_out) {
   if (!ctx) return HFX_E_ARG;
   if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(ctx, HFX_E_ARG, "theta must be >= 0");
-  if (prec != HFX_FP64)
+  const bool split = prec == HFX_OZAKI;
+  if (prec != HFX_FP64 && !split)
     return fail(ctx, HFX_E_ARG, "precision mode not available in this build");
-  (void)nslices;
+  if (split && nslices == 0) nslices = 6;
+  if (split && (nslices < 4 || nslices > 6))
+    return fail(ctx, HFX_E_ARG, "HFX_OZAKI takes 4 to 6 digit slices");
   for (int k = 0; k < 3; ++k)
     if (ctx->K[k].map.empty())
       return fail(ctx, HFX_E_STATE, std::string("no ") + ctx->K[k].name + " blocks set");
@@ -575,9 +745,19 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
   cudaStream_t st = ctx->stream;
   CK(cudaEventRecord(ctx->ev[0], st));
   CK(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(unsigned), st));
+  const bool vd_dirty = ctx->K[1].dirty || ctx->K[2].dirty;
+  const bool cv_dirty = ctx->K[0].dirty || ctx->K[1].dirty || !ctx->plan_valid;
   for (int k = 0; k < 3; ++k) {
     hfx_status s = pack_kind(ctx, k);
     if (s != HFX_OK) return s;
+  }
+  if (vd_dirty) {
+    bool okV = false, okD = false;
+    hfx_status s = check_mirror(ctx, 1, &okV);
+    if (s == HFX_OK) s = check_mirror(ctx, 2, &okD);
+    if (s != HFX_OK) return s;
+    const char *no = std::getenv("HFX_NO_MIRROR");
+    ctx->sym = okV && okD && !(no && no[0] && no[0] != '0');
   }
   {
     unsigned perr = 0;
@@ -685,6 +865,20 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
     CK(cudaMemsetAsync(ctx->d_acc.p, 0, sizeof(unsigned long long) * 2 * (nelem ? nelem : 1), st));
     CK(cudaStreamSynchronize(st));  // tk, tv, vals go out of scope
   }
+  SplitShared SS{};
+  if (split) {
+    if (cv_dirty || ctx->split_ks != nslices) {
+      hfx_status s = split_prepare(ctx, nslices);
+      if (s != HFX_OK) return s;
+      SS = split_shared(ctx);
+      CK(split_slice_inputs(SS, nslices, st));
+      ctx->launches += (SS.h_cy_rows > 0) + (SS.h_c4_rows > 0) + (SS.h_v_rows > 0);
+    }
+    SS = split_shared(ctx);
+    CK(ctx->d_njobs.reserve(2));
+    CK(ctx->d_tmacs.reserve(2));
+  }
+  double tmac_y = 0, tmac_v4 = 0;
   CK(cudaEventRecord(ctx->ev[1], st));
   // ---- contraction waves
   const size_t budget = scratch_budget_doubles();
@@ -706,7 +900,10 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         const int64_t psz = it.dab >= 0 ? pA * na * ctx->aotot[it.b] : 0;
         const int64_t tsz = (int64_t)it.nG * pA * na * nb;
         const int64_t qsz = (int64_t)it.nF * pA * na * nb;
-        const size_t need = (size_t)(ysz + psz + tsz + qsz);
+        int64_t pssz = 0;  // bf16 P digits, in doubles
+        if (split && it.dab >= 0 && !(ctx->sym && it.role == 2))
+          pssz = ((ctx->aotot[it.b] + 63) / 64) * ctx->kt4[it.a] * nslices * 64 * 32 / 4 + 64;
+        const size_t need = (size_t)(ysz + psz + tsz + qsz + pssz);
         if (w1 > w0 && used + need > budget) break;
         yo.push_back((int64_t)used);
         po.push_back((int64_t)used + ysz);
@@ -738,6 +935,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
       c.nbr = ctx->d_nbr.p;
       c.nao = ctx->d_nao.p;
       c.nabf = ctx->d_nabf.p;
+      c.ncol = ctx->d_ncol.p;
       c.C = DevBlocks{ctx->K[0].data.p, ctx->K[0].d_offs.p, ctx->K[0].maxabs.p};
       c.V = DevBlocks{ctx->K[1].data.p, ctx->K[1].d_offs.p, ctx->K[1].maxabs.p};
       c.D = DevBlocks{ctx->K[2].data.p, ctx->K[2].d_offs.p, ctx->K[2].maxabs.p};
@@ -754,15 +952,92 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
       c.acc = ctx->d_acc.p;
       c.macs = ctx->d_counters.p + 8;
       c.err = ctx->d_err.p;
+      c.sym = ctx->sym ? 1 : 0;
       int nl = 0;
+      SplitWave SW{};
+      if (split) {
+        // per-wave split metadata
+        std::vector<int64_t> prow(nw + 1, 0), psb(nw, -1), ycand(nw + 1, 0), v4cand(nw + 1, 0);
+        int64_t ps_elems = 0, v4max = 0;
+        for (size_t q = 0; q < nw; ++q) {
+          const WorkItem &it = ctx->items[w0 + q];
+          const int64_t ntv = (ctx->nabf[it.a] + 63) / 64;
+          const int64_t mty = ((int64_t)ctx->nao[it.b] * ctx->aotot[it.b] + 127) / 128;
+          ycand[q + 1] = ycand[q] + mty * ntv;
+          const bool has = it.dab >= 0 && !(ctx->sym && it.role == 2);
+          const int64_t ntp = (ctx->aotot[it.b] + 63) / 64, mt4 = (ctx->aotot[it.a] + 127) / 128;
+          prow[q + 1] = prow[q] + (has ? ntp * 64 : 0);
+          v4cand[q + 1] = v4cand[q] + (has ? mt4 * ntp : 0);
+          if (has) {
+            psb[q] = ps_elems;
+            ps_elems += ntp * ctx->kt4[it.a] * nslices * 64 * 32;
+            v4max += mt4 * ntp * ((ctx->kt4[it.a] + 19) / 20);
+          }
+        }
+        std::vector<int64_t> wm;
+        wm.insert(wm.end(), prow.begin(), prow.end());
+        wm.insert(wm.end(), psb.begin(), psb.end());
+        wm.insert(wm.end(), ycand.begin(), ycand.end());
+        wm.insert(wm.end(), v4cand.begin(), v4cand.end());
+        CK(ctx->d_wave_split.reserve(wm.size()));
+        CK(cudaMemcpyAsync(ctx->d_wave_split.p, wm.data(), sizeof(int64_t) * wm.size(),
+                           cudaMemcpyHostToDevice, st));
+        CK(ctx->d_ps.reserve(std::max<int64_t>(ps_elems, 1)));
+        CK(ctx->d_ps_e.reserve(std::max<int64_t>(prow[nw], 1)));
+        CK(ctx->d_jobs.reserve(std::max<int64_t>(ycand[nw], 1)));
+        CK(ctx->d_jobs4.reserve(std::max<int64_t>(v4max, 1)));
+        CK(cudaMemsetAsync(ctx->d_njobs.p, 0, 2 * sizeof(int), st));
+        CK(cudaMemsetAsync(ctx->d_tmacs.p, 0, 2 * sizeof(unsigned long long), st));
+        SW.w0 = (int64_t)w0;
+        SW.nw = (int32_t)nw;
+        SW.scratch = ctx->d_scratch.p;
+        SW.y_off = c.y_off;
+        SW.p_off = c.p_off;
+        SW.p_rowpre = ctx->d_wave_split.p;
+        SW.ps_base = ctx->d_wave_split.p + (nw + 1);
+        SW.y_candpre = ctx->d_wave_split.p + (nw + 1) + nw;
+        SW.v4_candpre = ctx->d_wave_split.p + 2 * (nw + 1) + nw;
+        SW.ps = ctx->d_ps.p;
+        SW.ps_e = ctx->d_ps_e.p;
+        SW.jobs = ctx->d_jobs.p;
+        SW.jobs4 = ctx->d_jobs4.p;
+        SW.njobs = ctx->d_njobs.p;
+        SW.tmacs = ctx->d_tmacs.p;
+        SW.h_ycand = ycand[nw];
+        SW.h_v4cand = v4cand[nw];
+        SW.h_prows = prow[nw];
+        SW.h_v4jobs_max = v4max;
+        CK(cudaEventRecord(ctx->sev[0], st));
+        CK(split_wave(SS, SW, nslices, 0, st));
+        CK(cudaEventRecord(ctx->sev[1], st));
+        ctx->launches += 2;
+        c.skip = 1u | 64u;  // Y and the D_AB piece run on the tensor cores
+      }
       CK(launch_contract_fp64(c, st, ctx->kev, &nl));
       ctx->launches += nl;
+      if (split) {
+        CK(cudaEventRecord(ctx->sev[2], st));
+        CK(split_wave(SS, SW, nslices, 1, st));
+        CK(cudaEventRecord(ctx->sev[3], st));
+        ctx->launches += (SW.h_prows > 0) + (SW.h_v4cand > 0) + 1;
+      }
       // the host offsets vector is reused next wave: order the copy first
       CK(cudaStreamSynchronize(st));
       for (int q = 0; q < 7; ++q) {
         float ms = 0;
         cudaEventElapsedTime(&ms, ctx->kev[q], ctx->kev[q + 1]);
         kms[1 + q] += ms;
+      }
+      if (split) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ctx->sev[0], ctx->sev[1]);
+        kms[1] += ms;
+        cudaEventElapsedTime(&ms, ctx->sev[2], ctx->sev[3]);
+        kms[7] += ms;
+        unsigned long long tm[2] = {0, 0};
+        CK(cudaMemcpy(tm, ctx->d_tmacs.p, sizeof(tm), cudaMemcpyDeviceToHost));
+        tmac_y += (double)tm[0];
+        tmac_v4 += (double)tm[1];
       }
       ++nwaves;
       w0 = w1;
@@ -810,6 +1085,16 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
   S.kernel_flops[0] = 0.0;
   for (int q = 0; q < 7; ++q) S.kernel_flops[1 + q] = 2.0 * (double)kmacs[q];
   S.n_launches = ctx->launches;
+  S.mirror = ctx->sym ? 1 : 0;
+  S.nslices = split ? nslices : 0;
+  if (split) {
+    const double pairs = (double)nslices * (nslices + 1) / 2;
+    S.kernel_flops[1] += 2.0 * tmac_y;
+    S.kernel_flops[7] += 2.0 * tmac_v4;
+    S.executed_flops += 2.0 * (tmac_y + tmac_v4);
+    S.kernel_tensor_flops[1] = 2.0 * tmac_y * pairs;
+    S.kernel_tensor_flops[7] = 2.0 * tmac_v4 * pairs;
+  }
   S.ms_screen = ms01;
   S.ms_contract = ms12;
   S.ms_reduce = ms23;

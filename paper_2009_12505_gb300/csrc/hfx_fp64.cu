@@ -10,6 +10,9 @@
 //   k_v2     Sigma_AG[a][g] -= sum_{al,b} (sum_{F in M2(G)} Q_F[al][a][b]) Y_G[al][b][g]
 //   k_v3     Sigma_FB[f][b] -= sum_{al,a} C_AF[al][a][f] (sum_{G in M3(F)} T3_G[al][a][b])
 //   k_v4     Sigma_FG[f][g] -= sum_{al,a} C_AF[al][a][f] P_G[al][a][g]       for F in M4(G)
+// Layouts in a work item's scratch (ncol = sum of nao over N[B], the G
+// columns concatenated in neighbour order, column of (G,g) = aopre(G) + g):
+//   Y[al][b][ncol], P[al][a][ncol], T3[G][al][a][b], Q[F][al][a][b].
 // M_v are the surviving-term bitmasks from the screen.  Every term is the
 // same multilinear form as Algorithm 3's Ht; the D_FB and D_AG pieces sum the
 // masked F (G) contributions before the last contraction, which is exact
@@ -18,6 +21,15 @@
 // Summation order inside a kernel is fixed (masks are scanned in index order),
 // and Sigma receives each block through the deterministic fixed-point adder,
 // so results are bitwise reproducible.
+//
+// Mirror pieces (A.sym, set only when every V and D block has its mirror
+// block equal to its transpose): the D_AG piece of <A,B> at (F,G) is the
+// transpose of the D_FB piece of <B,A> at (G,F) -- the same factors and the
+// same screening product -- so k_v2 adds each block both to Sigma_AG and,
+// transposed, to Sigma_GA, and k_v3 is not run.  Likewise the D_FG and D_AB
+// pieces of the mirror pair <B,A> are the transposes of those of <A,B>: they
+// run on canonical pairs only (role 1), adding each block and its transpose,
+// and on pairs whose B is A itself (role 0) without a mirror.
 #include "hfx_internal.h"
 
 namespace {
@@ -83,14 +95,15 @@ __global__ void __launch_bounds__(kThreads) k_y(ContractArgs A) {
   const int pA = A.nabf[it.a], pB = A.nabf[it.b], nb = A.nao[it.b], ng = A.nao[eg.other];
   const double *V = A.V.data + A.V.offs[it.vblk];
   const double *Cb = A.C.data + A.C.offs[eg.cblk];
-  double *Y = A.scratch + A.y_off[L.w - A.w0] + (int64_t)pA * nb * eg.aopre;
+  const int ncol = A.ncol[it.b];
+  double *Y = A.scratch + A.y_off[L.w - A.w0] + eg.aopre;
   const int N = nb * ng;
   for (int idx = threadIdx.x; idx < pA * N; idx += kThreads) {
-    const int al = idx / N, c = idx - al * N;
+    const int al = idx / N, c = idx - al * N, b = c / ng, g = c - b * ng;
     const double *v = V + (int64_t)al * pB;
     double s = 0.0;
     for (int be = 0; be < pB; ++be) s = fma(v[be], Cb[(int64_t)be * N + c], s);
-    Y[idx] = s;
+    Y[((int64_t)al * nb + b) * ncol + g] = s;
   }
   if (threadIdx.x == 0) atomicAdd(A.macs + 0, (unsigned long long)pA * pB * N);
 }
@@ -102,23 +115,25 @@ __global__ void __launch_bounds__(kThreads) k_dstage(ContractArgs A) {
   if (!(bits & 0xCu)) return;
   const NbrEntry eg = A.nbr[it.gbase + L.idx];
   const int pA = A.nabf[it.a], na = A.nao[it.a], nb = A.nao[it.b], ng = A.nao[eg.other];
-  const double *Y = A.scratch + A.y_off[L.w - A.w0] + (int64_t)pA * nb * eg.aopre;
+  const int ncol = A.ncol[it.b];
+  const double *Y = A.scratch + A.y_off[L.w - A.w0] + eg.aopre;  // Y[al][b][ncol]
   unsigned long long macs = 0;
-  if ((bits & 8u) && it.dab >= 0) {  // P_G[al][a][g] = sum_b D_AB[a][b] Y_G[al][b][g]
+  if ((bits & 8u) && it.dab >= 0 && !(A.sym && it.role == 2)) {
+    // P_G[al][a][g] = sum_b D_AB[a][b] Y_G[al][b][g]
     const double *Dab = A.D.data + A.D.offs[it.dab];
-    double *P = A.scratch + A.p_off[L.w - A.w0] + (int64_t)pA * na * eg.aopre;
+    double *P = A.scratch + A.p_off[L.w - A.w0] + eg.aopre;  // P[al][a][ncol]
     const int per = na * ng;
     for (int idx = threadIdx.x; idx < pA * per; idx += kThreads) {
       const int al = idx / per, r = idx - al * per, a = r / ng, g = r - a * ng;
-      const double *y = Y + (int64_t)al * nb * ng + g;
+      const double *y = Y + (int64_t)al * nb * ncol + g;
       const double *d = Dab + a * nb;
       double s = 0.0;
-      for (int b = 0; b < nb; ++b) s = fma(d[b], y[b * ng], s);
-      P[idx] = s;
+      for (int b = 0; b < nb; ++b) s = fma(d[b], y[(int64_t)b * ncol], s);
+      P[((int64_t)al * na + a) * ncol + g] = s;
     }
     macs += (unsigned long long)pA * per * nb;
   }
-  if (bits & 4u) {  // T3_G[al][a][b] = sum_g D_AG[a][g] Y_G[al][b][g]
+  if ((bits & 4u) && !A.sym) {  // T3_G[al][a][b] = sum_g D_AG[a][g] Y_G[al][b][g]
     const int n0 = it.n[0] + eg.n[0], n1 = it.n[1] + eg.n[1], n2 = it.n[2] + eg.n[2];
     const int64_t dag = dh_find(A.dhash, hk_pack(it.a, eg.other, n0, n1, n2));
     if (dag < 0) { atomicOr(A.err, HFX_DEV_ERR_MISSING); return; }
@@ -127,7 +142,7 @@ __global__ void __launch_bounds__(kThreads) k_dstage(ContractArgs A) {
     const int per = na * nb;
     for (int idx = threadIdx.x; idx < pA * per; idx += kThreads) {
       const int al = idx / per, r = idx - al * per, a = r / nb, b = r - a * nb;
-      const double *y = Y + ((int64_t)al * nb + b) * ng;
+      const double *y = Y + ((int64_t)al * nb + b) * ncol;
       const double *d = Dag + a * ng;
       double s = 0.0;
       for (int g = 0; g < ng; ++g) s = fma(d[g], y[g], s);
@@ -171,6 +186,7 @@ __global__ void __launch_bounds__(kThreads) k_v1(ContractArgs A) {
   const PairLoc L = locate(A, blockIdx.x, false);
   const WorkItem it = A.items[L.w];
   if (!(A.wf_flags[it.wf_off + L.idx] & 1u)) return;
+  if (A.sym && it.role == 2) return;
   if (it.nG > 1024) { if (threadIdx.x == 0) atomicOr(A.err, HFX_DEV_ERR_BOUNDS); return; }
   const int f_ = L.idx;
   const NbrEntry ef = A.nbr[it.fbase + f_];
@@ -185,6 +201,7 @@ __global__ void __launch_bounds__(kThreads) k_v1(ContractArgs A) {
   __syncthreads();
   const double *Caf = A.C.data + A.C.offs[ef.cblk];
   const double *Ybase = A.scratch + A.y_off[L.w - A.w0];
+  const int ncol = A.ncol[it.b];
   const int nout = na * nb;
   double acc[kMaxOut];
 #pragma unroll
@@ -201,10 +218,10 @@ __global__ void __launch_bounds__(kThreads) k_v1(ContractArgs A) {
       const int64_t dfg = dlist[s];
       if (dfg < 0) continue;
       const double *Dfg = A.D.data + A.D.offs[dfg];
-      const double *Y = Ybase + (int64_t)pA * nb * eg.aopre + (int64_t)al0 * nb * ng;
+      const double *Y = Ybase + eg.aopre + (int64_t)al0 * nb * ncol;
       for (int idx = threadIdx.x; idx < ac * per; idx += kThreads) {
         const int ab = idx / nf, f = idx - ab * nf;  // ab = al*nb + b
-        const double *y = Y + (int64_t)ab * ng;
+        const double *y = Y + (int64_t)ab * ncol;
         const double *d = Dfg + f * ng;
         double t = 0.0;
         for (int g = 0; g < ng; ++g) t = fma(y[g], d[g], t);
@@ -229,12 +246,14 @@ __global__ void __launch_bounds__(kThreads) k_v1(ContractArgs A) {
     __syncthreads();
   }
   const int64_t off = sig_offset(A, it.a, it.b, it.n[0], it.n[1], it.n[2]);
-  if (off >= 0)
-    for (int q = 0; q < kMaxOut; ++q) {
-      const int o = threadIdx.x + q * kThreads;
-      if (o >= nout) break;
-      fx_add(A.acc + 2 * (off + o), -acc[q]);
-    }
+  const int64_t moff = (A.sym && it.role == 1)
+                           ? sig_offset(A, it.b, it.a, -it.n[0], -it.n[1], -it.n[2]) : -1;
+  for (int q = 0; q < kMaxOut; ++q) {
+    const int o = threadIdx.x + q * kThreads;
+    if (o >= nout) break;
+    if (off >= 0) fx_add(A.acc + 2 * (off + o), -acc[q]);
+    if (moff >= 0) fx_add(A.acc + 2 * (moff + (o % nb) * na + o / nb), -acc[q]);
+  }
   if (threadIdx.x == 0) atomicAdd(A.macs + 3, macs);
 }
 
@@ -253,7 +272,8 @@ __global__ void __launch_bounds__(kThreads) k_v2(ContractArgs A) {
   const int nsel = ordered_select(it.nF, [&](int f) { return mask_bit(A, it, g_, 1, f); },
                                   flist, &nsel_s);
   const double *Qbase = A.scratch + A.q_off[L.w - A.w0];
-  const double *Y = A.scratch + A.y_off[L.w - A.w0] + (int64_t)pA * nb * eg.aopre;
+  const int ncol = A.ncol[it.b];
+  const double *Y = A.scratch + A.y_off[L.w - A.w0] + eg.aopre;  // Y[al][b][ncol]
   const int per = na * nb, nout = na * ng;
   double acc[kMaxOut];
 #pragma unroll
@@ -276,8 +296,8 @@ __global__ void __launch_bounds__(kThreads) k_v2(ContractArgs A) {
       double s = acc[q];
       for (int al = 0; al < ac; ++al) {
         const double *qq = Qs + (al * na + a) * nb;
-        const double *y = Y + (int64_t)(al0 + al) * nb * ng + g;
-        for (int b = 0; b < nb; ++b) s = fma(qq[b], y[b * ng], s);
+        const double *y = Y + (int64_t)(al0 + al) * nb * ncol + g;
+        for (int b = 0; b < nb; ++b) s = fma(qq[b], y[(int64_t)b * ncol], s);
       }
       acc[q] = s;
     }
@@ -286,12 +306,15 @@ __global__ void __launch_bounds__(kThreads) k_v2(ContractArgs A) {
   }
   const int64_t off = sig_offset(A, it.a, eg.other, it.n[0] + eg.n[0], it.n[1] + eg.n[1],
                                  it.n[2] + eg.n[2]);
-  if (off >= 0)
-    for (int q = 0; q < kMaxOut; ++q) {
-      const int o = threadIdx.x + q * kThreads;
-      if (o >= nout) break;
-      fx_add(A.acc + 2 * (off + o), -acc[q]);
-    }
+  const int64_t moff = A.sym ? sig_offset(A, eg.other, it.a, -(it.n[0] + eg.n[0]),
+                                          -(it.n[1] + eg.n[1]), -(it.n[2] + eg.n[2]))
+                             : -1;
+  for (int q = 0; q < kMaxOut; ++q) {
+    const int o = threadIdx.x + q * kThreads;
+    if (o >= nout) break;
+    if (off >= 0) fx_add(A.acc + 2 * (off + o), -acc[q]);
+    if (moff >= 0) fx_add(A.acc + 2 * (moff + (o % ng) * na + o / ng), -acc[q]);
+  }
   if (threadIdx.x == 0) atomicAdd(A.macs + 5, macs);
 }
 
@@ -300,6 +323,7 @@ __global__ void __launch_bounds__(kThreads) k_v3(ContractArgs A) {
   __shared__ int glist[1024];
   __shared__ int nsel_s;
   __shared__ double Ts[kChunk];
+  if (A.sym) return;  // obtained as the mirror of the D_FB piece
   const PairLoc L = locate(A, blockIdx.x, false);
   const WorkItem it = A.items[L.w];
   if (!(A.wf_flags[it.wf_off + L.idx] & 4u)) return;
@@ -357,13 +381,15 @@ __global__ void __launch_bounds__(kThreads) k_v4(ContractArgs A) {
   const PairLoc L = locate(A, blockIdx.x, true);
   const WorkItem it = A.items[L.w];
   if (!(A.wg_flags[it.wg_off + L.idx] & 8u)) return;
+  if (A.sym && it.role == 2) return;
   if (it.nF > 1024) { if (threadIdx.x == 0) atomicOr(A.err, HFX_DEV_ERR_BOUNDS); return; }
   const int g_ = L.idx;
   const NbrEntry eg = A.nbr[it.gbase + g_];
   const int pA = A.nabf[it.a], na = A.nao[it.a], ng = A.nao[eg.other];
   const int nsel = ordered_select(it.nF, [&](int f) { return mask_bit(A, it, g_, 3, f); },
                                   flist, &nsel_s);
-  const double *P = A.scratch + A.p_off[L.w - A.w0] + (int64_t)pA * na * eg.aopre;
+  const int ncol = A.ncol[it.b];
+  const double *P = A.scratch + A.p_off[L.w - A.w0] + eg.aopre;  // P[al][a][ncol]
   const int K = pA * na;
   const int nG0 = it.n[0] + eg.n[0], nG1 = it.n[1] + eg.n[1], nG2 = it.n[2] + eg.n[2];
   unsigned long long macs = 0;
@@ -374,11 +400,16 @@ __global__ void __launch_bounds__(kThreads) k_v4(ContractArgs A) {
     const int nout = nf * ng;
     const int64_t off = sig_offset(A, ef.other, eg.other, nG0 - ef.n[0], nG1 - ef.n[1],
                                    nG2 - ef.n[2]);
+    const int64_t moff = (A.sym && it.role == 1)
+                             ? sig_offset(A, eg.other, ef.other, -(nG0 - ef.n[0]),
+                                          -(nG1 - ef.n[1]), -(nG2 - ef.n[2]))
+                             : -1;
     for (int o = threadIdx.x; o < nout; o += kThreads) {
       const int f = o / ng, g = o - f * ng;
       double s = 0.0;
-      for (int r = 0; r < K; ++r) s = fma(Caf[(int64_t)r * nf + f], P[(int64_t)r * ng + g], s);
+      for (int r = 0; r < K; ++r) s = fma(Caf[(int64_t)r * nf + f], P[(int64_t)r * ncol + g], s);
       if (off >= 0) fx_add(A.acc + 2 * (off + o), -s);
+      if (moff >= 0) fx_add(A.acc + 2 * (moff + g * nf + f), -s);
     }
     macs += (unsigned long long)nout * K;
   }
@@ -394,7 +425,7 @@ cudaError_t launch_contract_fp64(const ContractArgs &a, cudaStream_t st, cudaEve
   };
   const unsigned gg = (unsigned)(a.nwg > 0 ? a.nwg : 0), gf = (unsigned)(a.nwf > 0 ? a.nwf : 0);
   mark(0);
-  if (gg) { k_y<<<gg, kThreads, 0, st>>>(a); ++n; }
+  if (gg && !(a.skip & 1u)) { k_y<<<gg, kThreads, 0, st>>>(a); ++n; }
   mark(1);
   if (gg) { k_dstage<<<gg, kThreads, 0, st>>>(a); ++n; }
   mark(2);
@@ -406,7 +437,7 @@ cudaError_t launch_contract_fp64(const ContractArgs &a, cudaStream_t st, cudaEve
   mark(5);
   if (gg) { k_v2<<<gg, kThreads, 0, st>>>(a); ++n; }
   mark(6);
-  if (gg) { k_v4<<<gg, kThreads, 0, st>>>(a); ++n; }
+  if (gg && !(a.skip & 64u)) { k_v4<<<gg, kThreads, 0, st>>>(a); ++n; }
   mark(7);
   if (nl) *nl = n;
   return cudaGetLastError();

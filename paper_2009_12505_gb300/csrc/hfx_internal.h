@@ -71,6 +71,8 @@ struct WorkItem {
   int64_t mask_off;      // first mask word: [g][variant][nFw]
   int64_t wg_off;        // first (w, g) flag index
   int64_t wf_off;        // first (w, f) flag index
+  int32_t role;          // 0: B is A itself; 1: canonical pair; 2: mirror of a canonical pair
+  int32_t pad;
 };
 
 // Device view of one block kind.
@@ -143,6 +145,7 @@ struct ContractArgs {
   int64_t nwg, nwf;          // (w,g) and (w,f) pairs in the wave
   const NbrEntry *nbr;
   const int32_t *nao, *nabf;
+  const int32_t *ncol;       // per atom: sum of nao over its neighbour list
   DevBlocks C, V, D;
   DevHash dhash;             // D keys -> block index
   DevHash shash;             // Sigma keys -> element offset
@@ -154,6 +157,8 @@ struct ContractArgs {
   unsigned long long *acc;   // Sigma fixed-point words, 2 per element
   unsigned long long *macs;  // executed multiply-adds per kernel class (7 slots)
   unsigned *err;
+  int sym;                   // inputs Hermitian: use the mirror pieces (see hfx_fp64.cu)
+  unsigned skip;             // kernels not to launch: bit q = launch order q (0 = Y ... 6 = D_AB)
 };
 
 cudaError_t launch_maxabs(const double *data, const int64_t *offs, int64_t nblk, double *out,
@@ -168,5 +173,10 @@ cudaError_t launch_finalize(const unsigned long long *acc, int64_t nelem, double
                             const uint64_t *skeys, const int64_t *soffs, int64_t nsig,
                             DevBlocks D, DevHash dhash, double *partials, double *ex,
                             cudaStream_t st);
+// Bitwise check that every block has its mirror (index mirror[e], -1 when
+// absent) equal to its transpose; sets *bad on the first mismatch.
+cudaError_t launch_check_mirror(const double *data, const int64_t *offs, const int64_t *mirror,
+                                const int32_t *rows, int64_t nblk, unsigned *bad,
+                                cudaStream_t st);
 cudaError_t launch_gather(const double *const *src, const int64_t *dst_off, const int64_t *len,
                           int64_t nblk, double *dst, cudaStream_t st);

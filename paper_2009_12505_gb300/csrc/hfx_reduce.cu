@@ -60,7 +60,38 @@ __global__ void k_gather(const double *const *src, const int64_t *dst_off, const
   for (int64_t t = lane; t < len[w]; t += 32) d[t] = s[t];
 }
 
+// One warp per block e with nrow rows: block[mirror[e]] must equal block[e]^T.
+__global__ void k_check_mirror(const double *data, const int64_t *offs, const int64_t *mirror,
+                               const int32_t *rows, int64_t nblk, unsigned *bad) {
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (w >= nblk) return;
+  const int64_t m = mirror[w];
+  if (m < 0) {
+    if (lane == 0) atomicOr(bad, 1u);
+    return;
+  }
+  const int64_t len = offs[w + 1] - offs[w];
+  const int nr = rows[w], nc = (int)(len / nr);
+  const double *x = data + offs[w], *y = data + offs[m];
+  bool diff = (offs[m + 1] - offs[m]) != len;
+  for (int64_t t = lane; !diff && t < len; t += 32) {
+    const int r = (int)(t / nc), c = (int)(t - (int64_t)r * nc);
+    diff |= x[t] != y[(int64_t)c * nr + r];
+  }
+  if (__any_sync(0xffffffffu, diff) && lane == 0) atomicOr(bad, 1u);
+}
+
 }  // namespace
+
+cudaError_t launch_check_mirror(const double *data, const int64_t *offs, const int64_t *mirror,
+                                const int32_t *rows, int64_t nblk, unsigned *bad,
+                                cudaStream_t st) {
+  if (nblk <= 0) return cudaSuccess;
+  k_check_mirror<<<(unsigned)((nblk * 32 + 255) / 256), 256, 0, st>>>(data, offs, mirror, rows,
+                                                                      nblk, bad);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_finalize(const unsigned long long *acc, int64_t nelem, double *sigma,
                             const uint64_t *skeys, const int64_t *soffs, int64_t nsig,

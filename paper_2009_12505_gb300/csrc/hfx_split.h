@@ -1,0 +1,67 @@
+// Arguments of the split-precision (HFX_OZAKI) kernels.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "hfx_internal.h"
+
+// One tensor-core job: a 128 x 64 output tile of work item w over K tiles
+// [k0, k0 + nk) of 32.
+struct Job {
+  int64_t w;
+  int32_t mt, nt, k0, nk;
+};
+
+// Per-build data: work items, screen output and the digit-sliced C and V.
+struct SplitShared {
+  int32_t natoms;
+  int64_t nv;                      // V blocks (= work items)
+  const int32_t *nao, *nabf, *ncol, *ktY, *kt4;
+  const int64_t *nc_start;         // per atom: first neighbour entry (natoms + 1)
+  const NbrEntry *nbr;
+  const WorkItem *items;
+  const double *Cd, *Vd;
+  const int64_t *Co, *Vo;
+  const uint32_t *masks;
+  const uint8_t *wg;
+  DevHash shash;
+  unsigned long long *acc;
+  unsigned *err;
+  int32_t sym;
+  // C of each atom transposed for Y: rows (b, G, g), K = beta
+  __nv_bfloat16 *cy;
+  const int64_t *cy_base, *cy_rowpre;
+  int16_t *cy_e;
+  // C of each atom as rows (F, f), K = (alpha, a)
+  __nv_bfloat16 *c4;
+  const int64_t *c4_base, *c4_rowpre;
+  int16_t *c4_e;
+  // V blocks: rows alpha, K = beta
+  __nv_bfloat16 *vs;
+  const int64_t *vs_base, *v_rowpre;
+  int16_t *vs_e;
+  int64_t h_cy_rows, h_c4_rows, h_v_rows;  // host copies of the row totals
+};
+
+// Per-wave data.
+struct SplitWave {
+  int64_t w0;
+  int32_t nw;
+  double *scratch;
+  const int64_t *y_off, *p_off;
+  const int64_t *p_rowpre;         // padded P rows per item (0 without D_AB jobs), nw + 1
+  __nv_bfloat16 *ps;
+  const int64_t *ps_base;          // -1 without D_AB jobs
+  int16_t *ps_e;
+  const int64_t *y_candpre, *v4_candpre;
+  Job *jobs, *jobs4;
+  int *njobs;                      // [0] Y jobs, [1] D_AB jobs
+  unsigned long long *tmacs;       // [0] Y, [1] D_AB: multiply-adds of the launched jobs
+  int64_t h_ycand, h_v4cand, h_prows, h_v4jobs_max;
+};
+
+cudaError_t split_slice_inputs(const SplitShared &S, int ks, cudaStream_t st);
+// phase 0: Y jobs; phase 1: P slices and D_AB jobs
+cudaError_t split_wave(const SplitShared &S, const SplitWave &W, int ks, int phase,
+                       cudaStream_t st);

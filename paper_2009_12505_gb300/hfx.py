@@ -37,7 +37,8 @@ class Stats(ctypes.Structure):
                 ("ms_reduce", ctypes.c_double), ("ms_total", ctypes.c_double),
                 ("n_waves", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64),
                 ("kernel_ms", ctypes.c_double * 8), ("kernel_flops", ctypes.c_double * 8),
-                ("n_launches", ctypes.c_int64)]
+                ("n_launches", ctypes.c_int64), ("mirror", ctypes.c_int32),
+                ("nslices", ctypes.c_int32), ("kernel_tensor_flops", ctypes.c_double * 8)]
 
 KERNELS = ["screen", "Y", "Dstage", "Q", "v1_DFG", "v3_DAG", "v2_DFB", "v4_DAB"]
 
@@ -235,4 +236,5 @@ class Context:
         d["survivors"] = list(s.survivors)
         d["kernel_ms"] = dict(zip(KERNELS, list(s.kernel_ms)))
         d["kernel_flops"] = dict(zip(KERNELS, list(s.kernel_flops)))
+        d["kernel_tensor_flops"] = dict(zip(KERNELS, list(s.kernel_tensor_flops)))
         return d

@@ -44,14 +44,32 @@ def test_tiny_full(make, theta):
 
 
 @pytest.mark.parametrize("theta", [0.0, 1e-2])
-def test_si_shrunk_full(theta):
+@pytest.mark.parametrize("mirror", ["1", "0"])
+def test_si_shrunk_full(theta, mirror, monkeypatch):
     """8-atom Si-like cell, full 13/60 blocks, short cutoffs: several tiles,
-    ragged 13-wide blocks, all four variants."""
+    ragged 13-wide blocks, all four variants; with and without the mirror
+    pieces (Hermitian inputs)."""
+    monkeypatch.setenv("HFX_NO_MIRROR", "0" if mirror == "1" else "1")
     wl = synth.si_shrunk()
     ref = oracle.Oracle.of(wl).build(theta)
     _, g = gpu_build(wl, theta)
+    assert g["stats"]["mirror"] == int(mirror)
     compare_full(wl, theta, g, ref, TOL)
     assert abs(g["ex"] - ref["ex"]) <= TOL * wl.system.natoms
+
+
+def test_non_hermitian_input_uses_full_sum():
+    """A V block whose mirror is not its transpose disables the mirror
+    pieces; the result still equals the oracle's (which needs no symmetry)."""
+    wl = synth.ab_shrunk()
+    V = dict(wl.V.as_dict())
+    k = next(k for k in V if k[0] != k[1])
+    V[k] = V[k] * 1.25
+    wl2 = synth.Workload("t", wl.system, wl.C, synth.pack(V), wl.D, 0, 0, 0, 0)
+    ref = oracle.Oracle.of(wl2).build(1e-3)
+    _, g = gpu_build(wl2, 1e-3)
+    assert g["stats"]["mirror"] == 0
+    compare_full(wl2, 1e-3, g, ref, TOL)
 
 
 def test_two_element_shrunk_full():

@@ -1,0 +1,79 @@
+"""GPU parity of the split-precision build (HFX_OZAKI: Y and the D_AB piece
+as exact bf16-digit tensor-core products) against the CPU oracle.
+
+Bar (mixed mode): identical Sigma key set and surviving-term counts, max
+|dSigma| <= 1e-8 Ha, |dE_X| <= 1e-8 Ha per atom."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import as_dict, compare_full, gpu_build
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.mark.parametrize("theta", [0.0, 1e-2])
+@pytest.mark.parametrize("mirror", ["1", "0"])
+def test_split_si_shrunk(theta, mirror, monkeypatch):
+    monkeypatch.setenv("HFX_NO_MIRROR", "0" if mirror == "1" else "1")
+    wl = synth.si_shrunk()
+    ref = oracle.Oracle.of(wl).build(theta)
+    _, g = gpu_build(wl, theta, "ozaki", 6)
+    assert g["stats"]["nslices"] == 6
+    err = compare_full(wl, theta, g, ref, TOL)
+    assert abs(g["ex"] - ref["ex"]) <= TOL * wl.system.natoms
+    print(f"max|dSigma| = {err:.3e}")
+
+
+@pytest.mark.parametrize("nslices", [5, 6])
+def test_split_two_element(nslices):
+    """13/60 and 27/90 atoms: two alpha tiles, three K tiles in Y."""
+    wl = synth.ab_shrunk()
+    ref = oracle.Oracle.of(wl).build(1e-3)
+    _, g = gpu_build(wl, 1e-3, "ozaki", nslices)
+    err = compare_full(wl, 1e-3, g, ref, TOL if nslices == 6 else 1e-6)
+    print(f"nslices={nslices} max|dSigma| = {err:.3e}")
+
+
+def test_split_deterministic():
+    wl = synth.si_shrunk()
+    _, a = gpu_build(wl, 1e-3, "ozaki", 6)
+    _, b = gpu_build(wl, 1e-3, "ozaki", 6)
+    np.testing.assert_array_equal(a["data"], b["data"])
+    assert a["ex"] == b["ex"]
+
+
+@pytest.mark.parametrize("theta", [1e-6, 0.0])
+def test_split_si8_full_size(theta):
+    """Full-size 8-atom cell: exact keys and counts; sampled blocks against the
+    oracle; every block against the FP64 GPU build."""
+    wl = synth.si8()
+    o = oracle.Oracle.of(wl)
+    keys, counts = o.keys(theta)
+    _, g = gpu_build(wl, theta, "ozaki", 6)
+    np.testing.assert_array_equal(g["keys"], keys)
+    np.testing.assert_array_equal(np.array(g["stats"]["survivors"]), counts)
+    rng = np.random.default_rng(3)
+    onsite = [k for k in keys.tolist() if k[0] == k[1] and k[2:] == [0, 0, 0]][:2]
+    sample = np.array(onsite + [keys[p].tolist() for p in sorted(rng.choice(len(keys), 8, replace=False))],
+                      np.int32)
+    ref, roffs = o.blocks(theta, sample)
+    gd = as_dict(g, wl.system.nao)
+    for e, k in enumerate(sample.tolist()):
+        err = np.abs(gd[tuple(k)].ravel() - ref[roffs[e]:roffs[e + 1]]).max()
+        assert err <= TOL, (k, err)
+    _, f = gpu_build(wl, theta, "fp64")
+    d = np.abs(g["data"] - f["data"]).max()
+    print(f"theta={theta}: max|Sigma_split - Sigma_fp64| = {d:.3e}, |dEx| = {abs(g['ex'] - f['ex']):.3e}")
+    assert d <= TOL
+    assert abs(g["ex"] - f["ex"]) <= TOL * wl.system.natoms
