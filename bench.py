@@ -236,6 +236,27 @@ def run_gpu(args):
     flops = st["canonical_flops"]
     value = world * flops / (ms / 1e3) / 1e12
 
+    # the plain FP64 GPU build of the same cell, and the split build's deviation from it
+    fp64 = None
+    if prec != "fp64" and not args.no_fp64:
+        ex_split = ctx.build(THETA, prec, nsl)
+        sig_split = ctx.sigma()
+        ctx.build(THETA, "fp64")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            ex64 = ctx.build(THETA, "fp64")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / args.fp64_steps
+        sig64 = ctx.sigma()
+        fp64 = {"build_s": ms64 / 1e3, "value": flops / (ms64 / 1e3) / 1e12, "unit": "TFLOP/s",
+                "split_speedup": ms64 / ms,
+                "max_abs_dsigma_split_vs_fp64_Ha": float(abs(sig_split - sig64).max()),
+                "abs_dex_per_atom_Ha": abs(ex_split - ex64) / wl.system.natoms}
+        ctx.build(THETA, prec, nsl)  # leave the context on the split result
+
     # end to end through the C ABI with host buffers
     e2e = None
     if not args.no_e2e:
@@ -265,7 +286,10 @@ def run_gpu(args):
     top = max(kms, key=kms.get)
     achieved = kfl[top] / (kms[top] / 1e3) / 1e12
     pk, src = peaks()
-    if prec == "fp64":
+    tfl = st.get("kernel_tensor_flops", {}).get(top, 0.0)
+    if tfl > 0:
+        achieved = tfl * args.steps / (kms[top] / 1e3) / 1e12
+    if tfl == 0:
         roof = {"kernel": top, "bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS,
                 "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz",
@@ -289,11 +313,16 @@ def run_gpu(args):
                 "dtype": "f64" if prec == "fp64" else "bf16", "data": "synthetic",
                 "config": {"workload": workload_desc(wl), "theta": THETA, "prec": prec,
                            "nslices": nsl if prec == "ozaki" else None,
+                           "arithmetic": ("Y and D_AB piece: exact products of 7-bit bf16 digits "
+                                          "on tcgen05 (f32 group sums, int64 recombination); "
+                                          "other stages FP64; Sigma in 128-bit fixed point")
+                           if prec == "ozaki" else "FP64 CUDA cores; Sigma in 128-bit fixed point",
                            "l2": f"inputs {sum(getattr(wl, k).data.nbytes for k in 'CVD') / 1e9:.2f} GB per cell (L2 is 129 MB)",
                            "parallelism": f"{world} independent cells" if world > 1 else "1 cell"},
                 "build_s": ms / 1e3, "canonical_tflop": flops / 1e12,
                 "executed_tflop": st["executed_flops"] / 1e12,
                 "sigma_blocks": st["n_sigma_blocks"], "survivors": st["survivors"],
+                "fp64_gpu": fp64, "mirror_pieces": bool(st["mirror"]),
                 "e2e": e2e, "gpu_launches": launches, "roofline": roof, "cpu_baseline": cpu,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
@@ -308,10 +337,12 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
-    ap.add_argument("--prec", choices=["fp64", "ozaki", "bf16x3"], default="fp64")
-    ap.add_argument("--nslices", type=int, default=0)
+    ap.add_argument("--prec", choices=["fp64", "ozaki"], default="ozaki")
+    ap.add_argument("--nslices", type=int, default=6)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison build")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="si64")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--fp64-steps", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

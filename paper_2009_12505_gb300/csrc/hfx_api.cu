@@ -139,8 +139,12 @@ struct hfx_ctx {
 
   // split-precision (HFX_OZAKI) operands
   int split_ks = 0;
-  DevBuf<__nv_bfloat16> d_cy, d_c4, d_vs, d_ps;
-  DevBuf<int16_t> d_cy_e, d_c4_e, d_vs_e, d_ps_e;
+  DevBuf<__nv_bfloat16> d_cy, d_c4, d_vs, d_ps, d_cz;
+  DevBuf<int16_t> d_cy_e, d_c4_e, d_vs_e, d_ps_e, d_cz_e;
+  DevBuf<int64_t> d_cz_meta;      // cz_base, cz_rowpre
+  DevBuf<int32_t> d_kofs, d_ktotZ;
+  int64_t h_cz_rows = 0;
+  DevBuf<Job> d_zjobs;
   DevBuf<int64_t> d_split_meta;   // cy_base, cy_rowpre, c4_base, c4_rowpre, vs_base, v_rowpre, nc_start
   DevBuf<int32_t> d_kt;           // ktY, kt4
   std::vector<int32_t> ktY, kt4;
@@ -152,6 +156,7 @@ struct hfx_ctx {
   cudaEvent_t sev[4] = {nullptr, nullptr, nullptr, nullptr};
 
   bool sym = false;             // V and D blocks all have transposed mirrors
+  bool c_reordered = false;     // C values changed: neighbour order must be rebuilt
   bool results_valid = false;
   double ex = 0.0;
   hfx_stats_v1 stats{};
@@ -317,7 +322,7 @@ hfx_status pack_kind(hfx_ctx *ctx, int k) {
 hfx_status build_plan(hfx_ctx *ctx) {
   Kind &C = ctx->K[0], &V = ctx->K[1], &D = ctx->K[2];
   cudaStream_t st = ctx->stream;
-  const bool cv_changed = C.keys_changed || V.keys_changed || !ctx->plan_valid;
+  const bool cv_changed = C.keys_changed || V.keys_changed || !ctx->plan_valid || ctx->c_reordered;
   if (cv_changed) {
     const int n = ctx->natoms;
     ctx->nc_start.assign(n + 1, 0);
@@ -329,15 +334,30 @@ hfx_status build_plan(hfx_ctx *ctx) {
     }
     for (int a = 0; a < n; ++a) ctx->nc_start[a + 1] += ctx->nc_start[a];
     ctx->aotot.assign(n, 0);
-    for (size_t e = 0; e < C.keys.size(); ++e) {  // keys sorted: grouped by atom
+    // Each atom's neighbours in descending order of their C block's upper
+    // limit: surviving (F, G) terms then gather in the leading rows and
+    // columns of the D_AB products, so whole tiles can be skipped.
+    std::vector<double> cmax(C.keys.size());
+    if (!C.keys.empty()) {
+      CK(cudaMemcpyAsync(cmax.data(), C.maxabs.p, sizeof(double) * C.keys.size(),
+                         cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    std::vector<int64_t> order(C.keys.size());
+    for (size_t e = 0; e < order.size(); ++e) order[e] = (int64_t)e;
+    for (int a = 0; a < n; ++a)
+      std::stable_sort(order.begin() + ctx->nc_start[a], order.begin() + ctx->nc_start[a + 1],
+                       [&](int64_t x, int64_t y) { return cmax[x] > cmax[y]; });
+    for (size_t q = 0; q < C.keys.size(); ++q) {  // keys sorted: grouped by atom
+      const int64_t e = order[q];
       int32_t k[5];
       hk_unpack(C.keys[e], k);
-      NbrEntry &ne = ctx->nbr[e];
+      NbrEntry &ne = ctx->nbr[q];
       ne.other = k[1];
       ne.n[0] = k[2]; ne.n[1] = k[3]; ne.n[2] = k[4];
       ne.aopre = (int32_t)ctx->aotot[k[0]];
       ne.pad = 0;
-      ne.cblk = (int64_t)e;
+      ne.cblk = e;
       ctx->aotot[k[0]] += ctx->nao[k[1]];
     }
     ctx->items.resize(V.keys.size());
@@ -475,6 +495,35 @@ hfx_status split_prepare(hfx_ctx *ctx, int ks) {
     v_row[e + 1] = v_row[e] + ntv * NT;
     vs_base[e + 1] = vs_base[e] + ntv * ctx->ktY[it.b] * ks * NT * TK;
   }
+  // C as rows (al, a), K = F blocks of width 16 or 32
+  std::vector<int64_t> cz_base(n + 1, 0), cz_row(n + 1, 0);
+  std::vector<int32_t> kofs(ctx->nbr.size()), ktotZ(n);
+  for (int x = 0; x < n; ++x) {
+    int32_t k = 0;
+    for (int64_t q = ctx->nc_start[x]; q < ctx->nc_start[x + 1]; ++q) {
+      kofs[q] = k;
+      k += ctx->nao[ctx->nbr[q].other] <= 16 ? 16 : 32;
+    }
+    ktotZ[x] = k;
+    const int64_t mtz = ((int64_t)ctx->nabf[x] * ctx->nao[x] + TM - 1) / TM;
+    cz_row[x + 1] = cz_row[x] + mtz * TM;
+    cz_base[x + 1] = cz_base[x] + mtz * (int64_t)k * ks * TM;
+  }
+  ctx->h_cz_rows = cz_row[n];
+  CK(ctx->d_cz.reserve(cz_base[n]));
+  CK(ctx->d_cz_e.reserve(cz_row[n]));
+  std::vector<int64_t> czm(cz_base);
+  czm.insert(czm.end(), cz_row.begin(), cz_row.end());
+  CK(ctx->d_cz_meta.reserve(czm.size()));
+  CK(cudaMemcpyAsync(ctx->d_cz_meta.p, czm.data(), sizeof(int64_t) * czm.size(),
+                     cudaMemcpyHostToDevice, st));
+  CK(ctx->d_kofs.reserve(std::max<size_t>(kofs.size(), 1)));
+  CK(ctx->d_ktotZ.reserve(n));
+  if (!kofs.empty())
+    CK(cudaMemcpyAsync(ctx->d_kofs.p, kofs.data(), sizeof(int32_t) * kofs.size(),
+                       cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_ktotZ.p, ktotZ.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
   ctx->h_cy_rows = cy_row[n];
   ctx->h_c4_rows = c4_row[n];
   ctx->h_v_rows = v_row[nv];
@@ -545,6 +594,16 @@ SplitShared split_shared(hfx_ctx *ctx) {
   S.h_cy_rows = ctx->h_cy_rows;
   S.h_c4_rows = ctx->h_c4_rows;
   S.h_v_rows = ctx->h_v_rows;
+  S.cz = ctx->d_cz.p;
+  S.cz_e = ctx->d_cz_e.p;
+  S.cz_base = ctx->d_cz_meta.p;
+  S.cz_rowpre = ctx->d_cz_meta.p + (n + 1);
+  S.kofs = ctx->d_kofs.p;
+  S.ktotZ = ctx->d_ktotZ.p;
+  S.Dd = ctx->K[2].data.p;
+  S.Do = ctx->K[2].d_offs.p;
+  S.dhash = DevHash{ctx->d_dhkeys.p, ctx->d_dhvals.p, ctx->dmask};
+  S.h_cz_rows = ctx->h_cz_rows;
   return S;
 }
 
@@ -747,6 +806,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
   CK(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(unsigned), st));
   const bool vd_dirty = ctx->K[1].dirty || ctx->K[2].dirty;
   const bool cv_dirty = ctx->K[0].dirty || ctx->K[1].dirty || !ctx->plan_valid;
+  ctx->c_reordered = ctx->K[0].dirty;
   for (int k = 0; k < 3; ++k) {
     hfx_status s = pack_kind(ctx, k);
     if (s != HFX_OK) return s;
@@ -872,13 +932,15 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
       if (s != HFX_OK) return s;
       SS = split_shared(ctx);
       CK(split_slice_inputs(SS, nslices, st));
-      ctx->launches += (SS.h_cy_rows > 0) + (SS.h_c4_rows > 0) + (SS.h_v_rows > 0);
+      CK(split_slice_cz(SS, nslices, st));
+      ctx->launches += (SS.h_cy_rows > 0) + (SS.h_c4_rows > 0) + (SS.h_v_rows > 0) +
+                       (SS.h_cz_rows > 0);
     }
     SS = split_shared(ctx);
-    CK(ctx->d_njobs.reserve(2));
-    CK(ctx->d_tmacs.reserve(2));
+    CK(ctx->d_njobs.reserve(3));
+    CK(ctx->d_tmacs.reserve(3));
   }
-  double tmac_y = 0, tmac_v4 = 0;
+  double tmac_y = 0, tmac_v4 = 0, tmac_z = 0;
   CK(cudaEventRecord(ctx->ev[1], st));
   // ---- contraction waves
   const size_t budget = scratch_budget_doubles();
@@ -892,7 +954,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
       size_t w1 = w0;
       size_t used = 0;
       offs4.clear();
-      std::vector<int64_t> yo, po, to, qo;
+      std::vector<int64_t> yo, po, to, qo, y2o;
       while (w1 < nit) {
         const WorkItem &it = ctx->items[w1];
         const int64_t pA = ctx->nabf[it.a], na = ctx->nao[it.a], nb = ctx->nao[it.b];
@@ -901,14 +963,16 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         const int64_t tsz = (int64_t)it.nG * pA * na * nb;
         const int64_t qsz = (int64_t)it.nF * pA * na * nb;
         int64_t pssz = 0;  // bf16 P digits, in doubles
+        if (split) pssz += ysz;  // Y as f32 pairs
         if (split && it.dab >= 0 && !(ctx->sym && it.role == 2))
-          pssz = ((ctx->aotot[it.b] + 63) / 64) * ctx->kt4[it.a] * nslices * 64 * 32 / 4 + 64;
+          pssz += ((ctx->aotot[it.b] + 63) / 64) * ctx->kt4[it.a] * nslices * 64 * 32 / 4 + 64;
         const size_t need = (size_t)(ysz + psz + tsz + qsz + pssz);
         if (w1 > w0 && used + need > budget) break;
         yo.push_back((int64_t)used);
         po.push_back((int64_t)used + ysz);
         to.push_back((int64_t)used + ysz + psz);
         qo.push_back((int64_t)used + ysz + psz + tsz);
+        y2o.push_back((int64_t)used + ysz + psz + tsz + qsz);
         used += need;
         ++w1;
       }
@@ -917,6 +981,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
       offs4.insert(offs4.end(), po.begin(), po.end());
       offs4.insert(offs4.end(), to.begin(), to.end());
       offs4.insert(offs4.end(), qo.begin(), qo.end());
+      offs4.insert(offs4.end(), y2o.begin(), y2o.end());
       CK(ctx->d_scratch.reserve(std::max<size_t>(used, 1)));
       CK(ctx->d_waveoffs.reserve(offs4.size()));
       CK(cudaMemcpyAsync(ctx->d_waveoffs.p, offs4.data(), sizeof(int64_t) * offs4.size(),
@@ -957,13 +1022,15 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
       SplitWave SW{};
       if (split) {
         // per-wave split metadata
-        std::vector<int64_t> prow(nw + 1, 0), psb(nw, -1), ycand(nw + 1, 0), v4cand(nw + 1, 0);
+        std::vector<int64_t> prow(nw + 1, 0), psb(nw, -1), ycand(nw + 1, 0), v4cand(nw + 1, 0),
+            zcand(nw + 1, 0);
         int64_t ps_elems = 0, v4max = 0;
         for (size_t q = 0; q < nw; ++q) {
           const WorkItem &it = ctx->items[w0 + q];
           const int64_t ntv = (ctx->nabf[it.a] + 63) / 64;
           const int64_t mty = ((int64_t)ctx->nao[it.b] * ctx->aotot[it.b] + 127) / 128;
           ycand[q + 1] = ycand[q] + mty * ntv;
+          zcand[q + 1] = zcand[q] + it.nG;
           const bool has = it.dab >= 0 && !(ctx->sym && it.role == 2);
           const int64_t ntp = (ctx->aotot[it.b] + 63) / 64, mt4 = (ctx->aotot[it.a] + 127) / 128;
           prow[q + 1] = prow[q] + (has ? ntp * 64 : 0);
@@ -979,6 +1046,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         wm.insert(wm.end(), psb.begin(), psb.end());
         wm.insert(wm.end(), ycand.begin(), ycand.end());
         wm.insert(wm.end(), v4cand.begin(), v4cand.end());
+        wm.insert(wm.end(), zcand.begin(), zcand.end());
         CK(ctx->d_wave_split.reserve(wm.size()));
         CK(cudaMemcpyAsync(ctx->d_wave_split.p, wm.data(), sizeof(int64_t) * wm.size(),
                            cudaMemcpyHostToDevice, st));
@@ -986,8 +1054,8 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         CK(ctx->d_ps_e.reserve(std::max<int64_t>(prow[nw], 1)));
         CK(ctx->d_jobs.reserve(std::max<int64_t>(ycand[nw], 1)));
         CK(ctx->d_jobs4.reserve(std::max<int64_t>(v4max, 1)));
-        CK(cudaMemsetAsync(ctx->d_njobs.p, 0, 2 * sizeof(int), st));
-        CK(cudaMemsetAsync(ctx->d_tmacs.p, 0, 2 * sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(ctx->d_njobs.p, 0, 3 * sizeof(int), st));
+        CK(cudaMemsetAsync(ctx->d_tmacs.p, 0, 3 * sizeof(unsigned long long), st));
         SW.w0 = (int64_t)w0;
         SW.nw = (int32_t)nw;
         SW.scratch = ctx->d_scratch.p;
@@ -997,6 +1065,9 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         SW.ps_base = ctx->d_wave_split.p + (nw + 1);
         SW.y_candpre = ctx->d_wave_split.p + (nw + 1) + nw;
         SW.v4_candpre = ctx->d_wave_split.p + 2 * (nw + 1) + nw;
+        SW.z_candpre = ctx->d_wave_split.p + 3 * (nw + 1) + nw;
+        SW.y2_off = ctx->d_waveoffs.p + 4 * nw;
+        SW.h_zcand = zcand[nw];
         SW.ps = ctx->d_ps.p;
         SW.ps_e = ctx->d_ps_e.p;
         SW.jobs = ctx->d_jobs.p;
@@ -1011,7 +1082,8 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         CK(split_wave(SS, SW, nslices, 0, st));
         CK(cudaEventRecord(ctx->sev[1], st));
         ctx->launches += 2;
-        c.skip = 1u | 64u;  // Y and the D_AB piece run on the tensor cores
+        // Y, Q, the D_FG, D_FB and D_AB pieces run on the tensor cores
+        c.skip = 1u | 4u | 8u | 32u | 64u;
       }
       CK(launch_contract_fp64(c, st, ctx->kev, &nl));
       ctx->launches += nl;
@@ -1020,6 +1092,20 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         CK(split_wave(SS, SW, nslices, 1, st));
         CK(cudaEventRecord(ctx->sev[3], st));
         ctx->launches += (SW.h_prows > 0) + (SW.h_v4cand > 0) + 1;
+        // D_FG and D_FB pieces: count the jobs, size the list, build and run
+        SW.zjobs = nullptr;
+        CK(split_zwave(SS, SW, nslices, st));
+        int nz = 0;
+        CK(cudaMemcpyAsync(&nz, ctx->d_njobs.p + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        CK(ctx->d_zjobs.reserve(std::max(nz, 1)));
+        CK(cudaMemsetAsync(ctx->d_njobs.p + 2, 0, sizeof(int), st));
+        SW.zjobs = ctx->d_zjobs.p;
+        SW.h_zjobs_max = nz;
+        CK(cudaEventRecord(ctx->kev[8], st));
+        CK(split_zwave(SS, SW, nslices, st));
+        CK(cudaEventRecord(ctx->kev[9], st));
+        ctx->launches += 2 * (SW.h_zcand > 0) + (nz > 0);
       }
       // the host offsets vector is reused next wave: order the copy first
       CK(cudaStreamSynchronize(st));
@@ -1034,10 +1120,14 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         kms[1] += ms;
         cudaEventElapsedTime(&ms, ctx->sev[2], ctx->sev[3]);
         kms[7] += ms;
-        unsigned long long tm[2] = {0, 0};
-        CK(cudaMemcpy(tm, ctx->d_tmacs.p, sizeof(tm), cudaMemcpyDeviceToHost));
+        cudaEventElapsedTime(&ms, ctx->kev[8], ctx->kev[9]);
+        kms[4] += ms;
+        unsigned long long tm[3] = {0, 0, 0};
+        CK(cudaMemcpyAsync(tm, ctx->d_tmacs.p, sizeof(tm), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
         tmac_y += (double)tm[0];
         tmac_v4 += (double)tm[1];
+        tmac_z += (double)tm[2];
       }
       ++nwaves;
       w0 = w1;
@@ -1094,6 +1184,9 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
     S.executed_flops += 2.0 * (tmac_y + tmac_v4);
     S.kernel_tensor_flops[1] = 2.0 * tmac_y * pairs;
     S.kernel_tensor_flops[7] = 2.0 * tmac_v4 * pairs;
+    S.kernel_flops[4] += 2.0 * tmac_z;
+    S.executed_flops += 2.0 * tmac_z;
+    S.kernel_tensor_flops[4] = 2.0 * tmac_z * pairs;
   }
   S.ms_screen = ms01;
   S.ms_contract = ms12;

@@ -427,15 +427,15 @@ cudaError_t launch_contract_fp64(const ContractArgs &a, cudaStream_t st, cudaEve
   mark(0);
   if (gg && !(a.skip & 1u)) { k_y<<<gg, kThreads, 0, st>>>(a); ++n; }
   mark(1);
-  if (gg) { k_dstage<<<gg, kThreads, 0, st>>>(a); ++n; }
+  if (gg && !(a.skip & 2u)) { k_dstage<<<gg, kThreads, 0, st>>>(a); ++n; }
   mark(2);
-  if (gf) { k_q<<<gf, kThreads, 0, st>>>(a); ++n; }
+  if (gf && !(a.skip & 4u)) { k_q<<<gf, kThreads, 0, st>>>(a); ++n; }
   mark(3);
-  if (gf) { k_v1<<<gf, kThreads, 0, st>>>(a); ++n; }
+  if (gf && !(a.skip & 8u)) { k_v1<<<gf, kThreads, 0, st>>>(a); ++n; }
   mark(4);
-  if (gf) { k_v3<<<gf, kThreads, 0, st>>>(a); ++n; }
+  if (gf && !(a.skip & 16u)) { k_v3<<<gf, kThreads, 0, st>>>(a); ++n; }
   mark(5);
-  if (gg) { k_v2<<<gg, kThreads, 0, st>>>(a); ++n; }
+  if (gg && !(a.skip & 32u)) { k_v2<<<gg, kThreads, 0, st>>>(a); ++n; }
   mark(6);
   if (gg && !(a.skip & 64u)) { k_v4<<<gg, kThreads, 0, st>>>(a); ++n; }
   mark(7);

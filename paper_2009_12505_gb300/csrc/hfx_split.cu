@@ -22,85 +22,7 @@
 
 #include "umma.cuh"
 
-namespace split {
-
-constexpr int TM = 128, TK = 32, NT = 64, NSTAGE = 2;
-constexpr int KT_CHUNK = 20;  // K tiles per job: exact group sums need K <= 640
-
-__host__ __device__ __forceinline__ int tile_off(int r, int c) {
-  return ((r >> 3) * 4 + (c >> 3)) * 64 + (r & 7) * 8 + (c & 7);
-}
-
-// Row exponent e (|x| < 2^(e-1)) from the largest magnitude's bit pattern.
-__device__ __forceinline__ int row_exponent(long long mbits) {
-  if (mbits == 0) return -1000;
-  const int ef = (int)(mbits >> 52);
-  return (ef == 0 ? -1022 : ef - 1023) + 2;
-}
-
-// k balanced base-128 digits of x 2^(-e): x = 2^e sum_s d_s 2^(-7 s).
-template <int KS>
-__device__ __forceinline__ void to_digits(double x, int e, int (&d)[KS]) {
-  long long X = (e > -1000) ? __double2ll_rn(ldexp(x, 7 * KS - e)) : 0ll;
-#pragma unroll
-  for (int s = KS - 1; s > 0; --s) {
-    const int dd = (int)(((X + 64) & 127) - 64);
-    d[s] = dd;
-    X = (X - dd) >> 7;
-  }
-  d[0] = (int)X;
-}
-
-// W * 2^e as a double using integer operations only (round to nearest).
-__device__ __forceinline__ double scaled_i64(long long W, int e) {
-  if (W == 0) return 0.0;
-  const unsigned long long sgn = W < 0 ? 0x8000000000000000ull : 0ull;
-  unsigned long long m = W < 0 ? (unsigned long long)(-W) : (unsigned long long)W;
-  const int nbits = 64 - __clzll(m);
-  int ex = nbits - 1 + e;
-  if (nbits > 53) {
-    const int sh = nbits - 53;
-    m = (m + (1ull << (sh - 1))) >> sh;
-    if (m >> 53) { m >>= 1; ++ex; }
-  } else {
-    m <<= (53 - nbits);
-  }
-  if (ex < -1000) return 0.0;
-  return __longlong_as_double(sgn | ((unsigned long long)(ex + 1023) << 52) |
-                              (m & ((1ull << 52) - 1)));
-}
-
-// Add W * 2^e to a fixed-point Sigma element (hi: 2^-32 units, lo: 2^-64
-// units) with integer arithmetic; |W 2^e| < 2^31.
-__device__ __forceinline__ void fx_add_scaled(unsigned long long *hi_lo, long long W, int e) {
-  if (W == 0) return;
-  const int t = e + 64;  // W * 2^t in units of 2^-64
-  __int128 V;
-  if (t >= 0) {
-    V = (__int128)W << t;
-  } else if (t > -64) {
-    V = (__int128)(W >> (-t));
-  } else {
-    V = W < 0 ? -1 : 0;
-  }
-  const long long hi = (long long)(V >> 32);
-  const long long lo = (long long)(V & (__int128)0xFFFFFFFFll);
-  if (hi) atomicAdd(hi_lo, (unsigned long long)hi);
-  if (lo) atomicAdd(hi_lo + 1, (unsigned long long)lo);
-}
-
-// Index of the neighbour entry of [base, base + n) whose column range holds col.
-__device__ __forceinline__ int entry_of(const NbrEntry *nbr, int64_t base, int n, int col) {
-  int lo = 0, hi = n - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (nbr[base + mid].aopre <= col) lo = mid; else hi = mid - 1;
-  }
-  return lo;
-}
-
-}  // namespace split
-
+#include "split_common.cuh"
 #include "hfx_split.h"
 
 namespace split {
@@ -263,9 +185,23 @@ __global__ void k_jobs_y(SplitShared S, SplitWave W) {
   const int local = (int)(t - W.y_candpre[wl]);
   const int ntv = (S.nabf[it.a] + NT - 1) / NT;
   const int mt = local / ntv, nt = local - mt * ntv;
-  // skip pairs with no surviving term at all
+  // skip tiles whose rows (b, G, g) belong only to G without a surviving term
+  const int ncol = S.ncol[it.b], nrow = S.nao[it.b] * ncol;
+  const int r0 = mt * TM, r1 = min(nrow, r0 + TM) - 1;
+  const int b0 = r0 / ncol, b1 = r1 / ncol;
+  const int c0 = r0 - b0 * ncol, c1 = r1 - b1 * ncol;
+  int G0 = entry_of(S.nbr, it.gbase, it.nG, c0), G1 = entry_of(S.nbr, it.gbase, it.nG, c1);
   bool any = false;
-  for (int g = 0; g < it.nG && !any; ++g) any = S.wg[it.wg_off + g] != 0;
+  if (b1 > b0 + 1 || (b1 == b0 + 1 && G1 >= G0)) {
+    G0 = 0;
+    G1 = it.nG - 1;
+  }
+  if (b1 == b0 || G0 == 0) {
+    for (int g = G0; g <= G1 && !any; ++g) any = S.wg[it.wg_off + g] != 0;
+  } else {  // wraps: [G0, nG) then [0, G1]
+    for (int g = G0; g < it.nG && !any; ++g) any = S.wg[it.wg_off + g] != 0;
+    for (int g = 0; g <= G1 && !any; ++g) any = S.wg[it.wg_off + g] != 0;
+  }
   if (!any) return;
   const int j = atomicAdd(W.njobs, 1);
   W.jobs[j] = Job{W.w0 + wl, mt, nt, 0, S.ktY[it.b]};
@@ -417,6 +353,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm(SplitShared S, SplitWave W) {
     const int rowY = jb.mt * TM + row;
     const int pA = S.nabf[it.a];
     double *Y = W.scratch + W.y_off[wl];
+    float2 *Y2 = reinterpret_cast<float2 *>(W.scratch + W.y2_off[wl]);
     for (int c0 = 0; c0 < NT; c0 += 32) {
       long long Wv[32];
 #pragma unroll
@@ -433,7 +370,11 @@ __global__ void __launch_bounds__(128, 1) k_gemm(SplitShared S, SplitWave W) {
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int al = jb.nt * NT + c0 + i;
-          if (al < pA) Y[(int64_t)al * nrow + rowY] = scaled_i64(Wv[i], ea + eb_p[c0 + i] - SH);
+          if (al < pA) {
+            const int e = ea + eb_p[c0 + i] - SH;
+            Y[(int64_t)al * nrow + rowY] = scaled_i64(Wv[i], e);
+            Y2[(int64_t)al * nrow + rowY] = pair_i64(Wv[i], e);
+          }
         }
       }
     }

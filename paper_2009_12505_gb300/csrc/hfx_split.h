@@ -41,7 +41,16 @@ struct SplitShared {
   __nv_bfloat16 *vs;
   const int64_t *vs_base, *v_rowpre;
   int16_t *vs_e;
-  int64_t h_cy_rows, h_c4_rows, h_v_rows;  // host copies of the row totals
+  // C of each atom as rows (alpha, a), K = F blocks of width kb(F) = 16 ceil(nao(F)/16)
+  __nv_bfloat16 *cz;
+  const int64_t *cz_base, *cz_rowpre;
+  int16_t *cz_e;
+  const int32_t *kofs;             // per neighbour entry: K offset of its F block
+  const int32_t *ktotZ;            // per atom: total K of its F blocks
+  const double *Dd;
+  const int64_t *Do;
+  DevHash dhash;
+  int64_t h_cy_rows, h_c4_rows, h_v_rows, h_cz_rows;  // host copies of the row totals
 };
 
 // Per-wave data.
@@ -56,12 +65,22 @@ struct SplitWave {
   int16_t *ps_e;
   const int64_t *y_candpre, *v4_candpre;
   Job *jobs, *jobs4;
-  int *njobs;                      // [0] Y jobs, [1] D_AB jobs
-  unsigned long long *tmacs;       // [0] Y, [1] D_AB: multiply-adds of the launched jobs
+  int *njobs;                      // [0] Y jobs, [1] D_AB jobs, [2] Z jobs
+  unsigned long long *tmacs;       // [0] Y, [1] D_AB, [2] Z: multiply-adds of the launched jobs
   int64_t h_ycand, h_v4cand, h_prows, h_v4jobs_max;
+  // Y as (hi, lo) f32 pairs, [al][b][ncol], for the Z-job epilogues
+  const int64_t *y2_off;
+  // Z jobs (D_FG and D_FB pieces): candidates (pair, G) and the job list
+  const int64_t *z_candpre;        // per item: nG if it has such work else 0, nw + 1
+  Job *zjobs;                      // null: count the jobs only
+  int64_t h_zcand, h_zjobs_max;
 };
 
 cudaError_t split_slice_inputs(const SplitShared &S, int ks, cudaStream_t st);
+// Z jobs (D_FG and D_FB pieces) for one wave; after phase 0 (needs Y pairs).
+// With W.zjobs null only counts the jobs into W.njobs[2].
+cudaError_t split_zwave(const SplitShared &S, const SplitWave &W, int ks, cudaStream_t st);
+cudaError_t split_slice_cz(const SplitShared &S, int ks, cudaStream_t st);
 // phase 0: Y jobs; phase 1: P slices and D_AB jobs
 cudaError_t split_wave(const SplitShared &S, const SplitWave &W, int ks, int phase,
                        cudaStream_t st);

@@ -1,0 +1,119 @@
+// Device helpers shared by the split-precision kernels: digit slicing,
+// integer recombination and fixed-point accumulation, double-float (f32
+// pair) arithmetic.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "umma.cuh"
+
+namespace split {
+
+constexpr int TM = 128, TK = 32, NT = 64, NSTAGE = 2;
+constexpr int KT_CHUNK = 20;  // K tiles per job: exact group sums need K <= 640
+
+__host__ __device__ __forceinline__ int tile_off(int r, int c) {
+  return ((r >> 3) * 4 + (c >> 3)) * 64 + (r & 7) * 8 + (c & 7);
+}
+
+// Row exponent e (|x| < 2^(e-1)) from the largest magnitude's bit pattern.
+__device__ __forceinline__ int row_exponent(long long mbits) {
+  if (mbits == 0) return -1000;
+  const int ef = (int)(mbits >> 52);
+  return (ef == 0 ? -1022 : ef - 1023) + 2;
+}
+
+// k balanced base-128 digits of x 2^(-e): x = 2^e sum_s d_s 2^(-7 s).
+template <int KS>
+__device__ __forceinline__ void to_digits(double x, int e, int (&d)[KS]) {
+  long long X = (e > -1000) ? __double2ll_rn(ldexp(x, 7 * KS - e)) : 0ll;
+#pragma unroll
+  for (int s = KS - 1; s > 0; --s) {
+    const int dd = (int)(((X + 64) & 127) - 64);
+    d[s] = dd;
+    X = (X - dd) >> 7;
+  }
+  d[0] = (int)X;
+}
+
+// W * 2^e as a double using integer operations only (round to nearest).
+__device__ __forceinline__ double scaled_i64(long long W, int e) {
+  if (W == 0) return 0.0;
+  const unsigned long long sgn = W < 0 ? 0x8000000000000000ull : 0ull;
+  unsigned long long m = W < 0 ? (unsigned long long)(-W) : (unsigned long long)W;
+  const int nbits = 64 - __clzll(m);
+  int ex = nbits - 1 + e;
+  if (nbits > 53) {
+    const int sh = nbits - 53;
+    m = (m + (1ull << (sh - 1))) >> sh;
+    if (m >> 53) { m >>= 1; ++ex; }
+  } else {
+    m <<= (53 - nbits);
+  }
+  if (ex < -1000) return 0.0;
+  return __longlong_as_double(sgn | ((unsigned long long)(ex + 1023) << 52) |
+                              (m & ((1ull << 52) - 1)));
+}
+
+// Add W * 2^e to a fixed-point Sigma element (hi: 2^-32 units, lo: 2^-64
+// units) with integer arithmetic; |W 2^e| < 2^31.
+__device__ __forceinline__ void fx_add_scaled(unsigned long long *hi_lo, long long W, int e) {
+  if (W == 0) return;
+  const int t = e + 64;  // W * 2^t in units of 2^-64
+  __int128 V;
+  if (t >= 0) {
+    V = (__int128)W << t;
+  } else if (t > -64) {
+    V = (__int128)(W >> (-t));
+  } else {
+    V = W < 0 ? -1 : 0;
+  }
+  const long long hi = (long long)(V >> 32);
+  const long long lo = (long long)(V & (__int128)0xFFFFFFFFll);
+  if (hi) atomicAdd(hi_lo, (unsigned long long)hi);
+  if (lo) atomicAdd(hi_lo + 1, (unsigned long long)lo);
+}
+
+// Index of the neighbour entry of [base, base + n) whose column range holds col.
+__device__ __forceinline__ int entry_of(const NbrEntry *nbr, int64_t base, int n, int col) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (nbr[base + mid].aopre <= col) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace split
+
+
+namespace split {
+
+// (hi, lo) f32 pair of W * 2^e with integer conversions only; hi + lo carries
+// about 48 significant bits.  Requires -126 <= e + 63 and e <= 100.
+__device__ __forceinline__ float2 pair_i64(long long W, int e) {
+  if (W == 0) return make_float2(0.f, 0.f);
+  const float h = __ll2float_rn(W);
+  const long long r = W - __float2ll_rn(h);
+  const float l = __ll2float_rn(r);
+  // multiply by 2^e in two steps so neither factor leaves the normal range
+  const int e1 = e / 2, e2 = e - e1;
+  const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
+  return make_float2(__fmul_rn(__fmul_rn(h, s1), s2), __fmul_rn(__fmul_rn(l, s1), s2));
+}
+
+// (sh, sl) += (ah, al) * (bh, bl), error-free products and sums (no
+// contraction: every operation is an explicit round-to-nearest intrinsic).
+__device__ __forceinline__ void df_mac(float &sh, float &sl, float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+}  // namespace split
