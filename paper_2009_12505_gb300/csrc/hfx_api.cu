@@ -941,6 +941,8 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
     CK(ctx->d_tmacs.reserve(3));
   }
   double tmac_y = 0, tmac_v4 = 0, tmac_z = 0;
+  const char *zenv = std::getenv("HFX_ZJOBS");
+  const bool zjobs = split && zenv && zenv[0] && zenv[0] != '0';
   CK(cudaEventRecord(ctx->ev[1], st));
   // ---- contraction waves
   const size_t budget = scratch_budget_doubles();
@@ -1082,8 +1084,9 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         CK(split_wave(SS, SW, nslices, 0, st));
         CK(cudaEventRecord(ctx->sev[1], st));
         ctx->launches += 2;
-        // Y, Q, the D_FG, D_FB and D_AB pieces run on the tensor cores
-        c.skip = 1u | 4u | 8u | 32u | 64u;
+        // Y and the D_AB piece run on the tensor cores; the D_FG and D_FB pieces
+        // too when the Z-job form is selected (HFX_ZJOBS=1)
+        c.skip = zjobs ? (1u | 4u | 8u | 32u | 64u) : (1u | 64u);
       }
       CK(launch_contract_fp64(c, st, ctx->kev, &nl));
       ctx->launches += nl;
@@ -1092,6 +1095,8 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         CK(split_wave(SS, SW, nslices, 1, st));
         CK(cudaEventRecord(ctx->sev[3], st));
         ctx->launches += (SW.h_prows > 0) + (SW.h_v4cand > 0) + 1;
+      }
+      if (split && zjobs) {
         // D_FG and D_FB pieces: count the jobs, size the list, build and run
         SW.zjobs = nullptr;
         CK(split_zwave(SS, SW, nslices, st));
@@ -1120,8 +1125,10 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         kms[1] += ms;
         cudaEventElapsedTime(&ms, ctx->sev[2], ctx->sev[3]);
         kms[7] += ms;
-        cudaEventElapsedTime(&ms, ctx->kev[8], ctx->kev[9]);
-        kms[4] += ms;
+        if (zjobs) {
+          cudaEventElapsedTime(&ms, ctx->kev[8], ctx->kev[9]);
+          kms[4] += ms;
+        }
         unsigned long long tm[3] = {0, 0, 0};
         CK(cudaMemcpyAsync(tm, ctx->d_tmacs.p, sizeof(tm), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));

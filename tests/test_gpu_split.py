@@ -24,8 +24,12 @@ def _need_gpu():
 
 @pytest.mark.parametrize("theta", [0.0, 1e-2])
 @pytest.mark.parametrize("mirror", ["1", "0"])
-def test_split_si_shrunk(theta, mirror, monkeypatch):
+@pytest.mark.parametrize("zjobs", ["0", "1"])
+def test_split_si_shrunk(theta, mirror, zjobs, monkeypatch):
+    """With and without the mirror pieces, and with the D_FG / D_FB pieces
+    on FP64 CUDA cores or as tensor-core Z jobs."""
     monkeypatch.setenv("HFX_NO_MIRROR", "0" if mirror == "1" else "1")
+    monkeypatch.setenv("HFX_ZJOBS", zjobs)
     wl = synth.si_shrunk()
     ref = oracle.Oracle.of(wl).build(theta)
     _, g = gpu_build(wl, theta, "ozaki", 6)
@@ -36,8 +40,10 @@ def test_split_si_shrunk(theta, mirror, monkeypatch):
 
 
 @pytest.mark.parametrize("nslices", [5, 6])
-def test_split_two_element(nslices):
+@pytest.mark.parametrize("zjobs", ["0", "1"])
+def test_split_two_element(nslices, zjobs, monkeypatch):
     """13/60 and 27/90 atoms: two alpha tiles, three K tiles in Y."""
+    monkeypatch.setenv("HFX_ZJOBS", zjobs)
     wl = synth.ab_shrunk()
     ref = oracle.Oracle.of(wl).build(1e-3)
     _, g = gpu_build(wl, 1e-3, "ozaki", nslices)
