@@ -52,6 +52,7 @@ def _load():
             lib.orc_ex.restype = f64
             lib.orc_ex.argtypes = [P, i64, P, P, P]
             lib.orc_maxabs.argtypes = [P, ctypes.c_char, P]
+            lib.orc_set_maxabs.argtypes = [P, ctypes.c_char, P]
             _lib = lib
     return _lib
 
@@ -138,6 +139,13 @@ class Oracle:
         data, offs = self.blocks(theta, keys, nthreads)
         return {"keys": keys, "data": data, "offs": offs, "counts": counts,
                 "ex": self.ex(keys, data, offs)}
+
+    def set_maxabs(self, which: str, vals) -> None:
+        """Use these block upper limits in the screen (frozen surviving set)."""
+        v = np.ascontiguousarray(vals, np.float64)
+        assert v.shape[0] == self.counts_blocks[which]
+        self._keep.append(v)
+        self._lib.orc_set_maxabs(self._h, which.encode()[0:1], _ptr(v))
 
     def maxabs(self, which: str) -> np.ndarray:
         out = np.zeros(self.counts_blocks[which], np.float64)

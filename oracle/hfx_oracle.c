@@ -565,6 +565,13 @@ double orc_ex(orc *o, int64_t nkeys, const int32_t *keys, const double *sig, con
   return 0.5 * (s + c);
 }
 
+/* Replace the block upper limits used by the screen (e.g. to keep the set of
+ * surviving terms of an unperturbed input fixed in a finite difference). */
+void orc_set_maxabs(orc *o, char which, const double *vals) {
+  bset_t *b = which == 'C' ? &o->C : which == 'V' ? &o->V : &o->D;
+  memcpy(b->maxabs, vals, sizeof(double) * (size_t)b->n);
+}
+
 /* Block upper limits as computed here (exposed for tests). */
 void orc_maxabs(orc *o, char which, double *out) {
   const bset_t *b = which == 'C' ? &o->C : which == 'V' ? &o->V : &o->D;

@@ -5,8 +5,8 @@ The compute path is the CUDA library ``libhfx`` (C ABI in ``include/hfx.h``);
 There is no CPU fallback: loading fails loudly if the library cannot be built
 or loaded.
 """
-from .hfx import (HFX_BF16X3, HFX_FP64, HFX_OZAKI, Context, HfxError, build_library,
-                  load_library)
+from .hfx import (HFX_BF16X3, HFX_FP64, HFX_OZAKI, Context, ExchangeEnergy, HfxError,
+                  build_library, load_library)
 
-__all__ = ["Context", "HfxError", "HFX_FP64", "HFX_BF16X3", "HFX_OZAKI", "build_library",
+__all__ = ["Context", "ExchangeEnergy", "HfxError", "HFX_FP64", "HFX_BF16X3", "HFX_OZAKI", "build_library",
            "load_library"]

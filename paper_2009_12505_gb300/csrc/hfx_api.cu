@@ -1258,10 +1258,86 @@ hfx_status hfx_get_H_all(const hfx_ctx *ctx, double *out, int on_device) {
 
 hfx_status hfx_grad(hfx_ctx *ctx, double *dC, double *dV) {
   if (!ctx) return HFX_E_ARG;
-  (void)dC;
-  (void)dV;
   if (!ctx->results_valid) return fail(ctx, HFX_E_STATE, "no build to differentiate");
-  return fail(ctx, HFX_E_ARG, "adjoint not available in this build");
+  cudaStream_t st = ctx->stream;
+  const int64_t nC = ctx->K[0].offs.back(), nV = ctx->K[1].offs.back();
+  DevBuf<unsigned long long> dcacc;
+  DevBuf<double> dcout, dvout;
+  CK(dcacc.reserve(2 * nC));
+  CK(dcout.reserve(nC));
+  CK(dvout.reserve(nV));
+  CK(cudaMemsetAsync(dcacc.p, 0, sizeof(unsigned long long) * 2 * (nC ? nC : 1), st));
+  CK(cudaMemsetAsync(dvout.p, 0, sizeof(double) * (nV ? nV : 1), st));
+  CK(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(unsigned), st));
+  CK(cudaMemsetAsync(ctx->d_counters.p + 8, 0, sizeof(unsigned long long) * 7, st));
+  // waves over the pairs: Y and R per pair
+  const size_t budget = scratch_budget_doubles();
+  const size_t nit = ctx->items.size();
+  size_t w0 = 0;
+  while (w0 < nit) {
+    size_t w1 = w0, used = 0;
+    std::vector<int64_t> yo, ro;
+    while (w1 < nit) {
+      const WorkItem &it = ctx->items[w1];
+      const int64_t ysz = (int64_t)ctx->nabf[it.a] * ctx->nao[it.b] * ctx->aotot[it.b];
+      if (w1 > w0 && used + 2 * ysz > budget) break;
+      yo.push_back((int64_t)used);
+      ro.push_back((int64_t)used + ysz);
+      used += 2 * ysz;
+      ++w1;
+    }
+    const size_t nw = w1 - w0;
+    std::vector<int64_t> offs(yo);
+    offs.insert(offs.end(), ro.begin(), ro.end());
+    CK(ctx->d_scratch.reserve(std::max<size_t>(used, 1)));
+    CK(ctx->d_waveoffs.reserve(offs.size()));
+    CK(cudaMemcpyAsync(ctx->d_waveoffs.p, offs.data(), sizeof(int64_t) * offs.size(),
+                       cudaMemcpyHostToDevice, st));
+    ContractArgs c{};
+    c.items = ctx->d_items.p;
+    c.w0 = (int64_t)w0;
+    c.w1 = (int64_t)w1;
+    c.wg_base = ctx->items[w0].wg_off;
+    c.wf_base = ctx->items[w0].wf_off;
+    c.nwg = ((w1 < nit) ? ctx->items[w1].wg_off : ctx->nwg) - c.wg_base;
+    c.nwf = ((w1 < nit) ? ctx->items[w1].wf_off : ctx->nwf) - c.wf_base;
+    c.nbr = ctx->d_nbr.p;
+    c.nao = ctx->d_nao.p;
+    c.nabf = ctx->d_nabf.p;
+    c.ncol = ctx->d_ncol.p;
+    c.C = DevBlocks{ctx->K[0].data.p, ctx->K[0].d_offs.p, ctx->K[0].maxabs.p};
+    c.V = DevBlocks{ctx->K[1].data.p, ctx->K[1].d_offs.p, ctx->K[1].maxabs.p};
+    c.D = DevBlocks{ctx->K[2].data.p, ctx->K[2].d_offs.p, ctx->K[2].maxabs.p};
+    c.dhash = DevHash{ctx->d_dhkeys.p, ctx->d_dhvals.p, ctx->dmask};
+    c.shash = DevHash{ctx->d_shkeys.p, ctx->d_shvals.p, ctx->smask};
+    c.masks = ctx->d_masks.p;
+    c.wg_flags = ctx->d_wg.p;
+    c.wf_flags = ctx->d_wf.p;
+    c.scratch = ctx->d_scratch.p;
+    c.y_off = ctx->d_waveoffs.p;
+    c.p_off = ctx->d_waveoffs.p + nw;
+    c.t3_off = c.q_off = c.y_off;
+    c.acc = ctx->d_acc.p;
+    c.macs = ctx->d_counters.p + 8;
+    c.err = ctx->d_err.p;
+    c.sym = 0;
+    c.skip = 2u | 4u | 8u | 16u | 32u | 64u;  // Y only
+    c.dcacc = dcacc.p;
+    c.dv = dvout.p;
+    int nl = 0;
+    CK(launch_contract_fp64(c, st, nullptr, &nl));
+    CK(launch_adjoint(c, st));
+    CK(cudaStreamSynchronize(st));
+    w0 = w1;
+  }
+  CK(launch_fx_to_double(dcacc.p, nC, dcout.p, st));
+  unsigned herr = 0;
+  CK(cudaMemcpyAsync(&herr, ctx->d_err.p, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+  if (dC) CK(cudaMemcpyAsync(dC, dcout.p, sizeof(double) * nC, cudaMemcpyDeviceToHost, st));
+  if (dV) CK(cudaMemcpyAsync(dV, dvout.p, sizeof(double) * nV, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (herr) return fail(ctx, HFX_E_CUDA, "adjoint kernels reported error " + std::to_string(herr));
+  return HFX_OK;
 }
 
 hfx_status hfx_stats(const hfx_ctx *ctx, void *stats) {

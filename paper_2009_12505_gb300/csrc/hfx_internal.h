@@ -159,6 +159,8 @@ struct ContractArgs {
   unsigned *err;
   int sym;                   // inputs Hermitian: use the mirror pieces (see hfx_fp64.cu)
   unsigned skip;             // kernels not to launch: bit q = launch order q (0 = Y ... 6 = D_AB)
+  unsigned long long *dcacc; // adjoint: fixed-point dE/dC (2 words per C element)
+  double *dv;                // adjoint: dE/dV in the V block layout
 };
 
 cudaError_t launch_maxabs(const double *data, const int64_t *offs, int64_t nblk, double *out,
@@ -169,6 +171,10 @@ cudaError_t launch_collect_keys(const unsigned long long *keys, uint64_t cap,
 // Launches the seven FP64 contraction kernels; ev (8 events or null) is recorded
 // before the first and after each kernel.  Returns the number of launches in *nl.
 cudaError_t launch_contract_fp64(const ContractArgs &a, cudaStream_t st, cudaEvent_t *ev, int *nl);
+// Adjoint kernels for one wave (Y in y_off, R in p_off).
+cudaError_t launch_adjoint(const ContractArgs &a, cudaStream_t st);
+cudaError_t launch_fx_to_double(const unsigned long long *acc, int64_t n, double *out,
+                                cudaStream_t st);
 cudaError_t launch_finalize(const unsigned long long *acc, int64_t nelem, double *sigma,
                             const uint64_t *skeys, const int64_t *soffs, int64_t nsig,
                             DevBlocks D, DevHash dhash, double *partials, double *ex,

@@ -123,6 +123,42 @@ def term_noalloc(cA, V, cB, D, out, stream=None):
     return out
 
 
+class ExchangeEnergy:
+    """torch.autograd.Function wrapper: E_X(C, V) with D fixed.
+
+    ``apply(ctx, theta, prec, nslices, C, V, D)`` with C, V, D the packed
+    block data (CUDA float64 tensors, key-sorted layout of ``ctx``'s keys)
+    returns E_X as a 0-d tensor; backward returns dE_X/dC and dE_X/dV from
+    hfx_grad with the surviving-term set of the forward build."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, ctx, theta, prec, nslices, C, V, D):
+        import torch
+        if cls._fn is None:
+            class _Fn(torch.autograd.Function):
+                @staticmethod
+                def forward(fctx, hctx, theta_, prec_, nsl_, C_, V_, D_):
+                    for k, t in (("C", C_), ("V", V_), ("D", D_)):
+                        keys, offs = hctx._layout[k]
+                        hctx.set_many(k, keys, t.detach().contiguous(), offs, on_device=True)
+                    ex = hctx.build(theta_, prec_, nsl_)
+                    fctx.hctx = hctx
+                    fctx.shapes = (C_.numel(), V_.numel())
+                    return torch.tensor(ex, dtype=torch.float64, device=C_.device)
+
+                @staticmethod
+                def backward(fctx, gout):
+                    nC, nV = fctx.shapes
+                    dC, dV = fctx.hctx.grad(nC, nV)
+                    dev = gout.device
+                    return (None, None, None, None, torch.from_numpy(dC).to(dev) * gout,
+                            torch.from_numpy(dV).to(dev) * gout, None)
+            cls._fn = _Fn
+        return cls._fn.apply(ctx, theta, prec, nslices, C, V, D)
+
+
 class Context:
     """One periodic system.  nao/nabf are per-atom sizes."""
 
@@ -142,6 +178,7 @@ class Context:
         if rc != 0:
             raise HfxError(rc, "hfx_create failed")
         self._h = h
+        self._layout = {}
 
     def _check(self, rc):
         if rc != 0:
@@ -183,6 +220,8 @@ class Context:
     def set_blocks(self, which: str, blocks, on_device: bool = False):
         """blocks: object with keys/data/offs (e.g. synth.Blocks)."""
         self.set_many(which, blocks.keys, blocks.data, blocks.offs, on_device)
+        self._layout[which] = (np.ascontiguousarray(blocks.keys, np.int32),
+                               np.ascontiguousarray(blocks.offs, np.int64))
 
     def clear(self, which: str):
         self._check(self._lib.hfx_clear(self._h, which.encode()))

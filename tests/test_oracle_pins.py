@@ -213,3 +213,29 @@ def test_block_maxabs():
         b = getattr(wl, which)
         ref = [np.abs(b.data[b.offs[e]:b.offs[e + 1]]).max() for e in range(b.count)]
         np.testing.assert_array_equal(o.maxabs(which), ref)
+
+
+def test_frozen_screen_for_finite_differences():
+    """With the unperturbed block norms frozen, E_X is exactly linear in V and
+    quadratic in C, so central differences of any step reproduce each other
+    (the property the gradient tests rely on)."""
+    wl = tiny3()
+    o0 = oracle.Oracle.of(wl)
+    norms = {k: o0.maxabs(k) for k in "CVD"}
+    theta = 2e-2
+
+    def ex_with(which, idx, delta):
+        b = getattr(wl, which)
+        d = b.data.copy()
+        d[idx] += delta
+        w = scaled(wl, which, 1.0)
+        setattr(w, which, synth.Blocks(b.keys, d, b.offs))
+        o = oracle.Oracle.of(w)
+        for k in "CVD":
+            o.set_maxabs(k, norms[k])
+        return o.build(theta)["ex"]
+
+    for which, idx in (("V", 7), ("C", 11)):
+        g1 = (ex_with(which, idx, 1e-3) - ex_with(which, idx, -1e-3)) / 2e-3
+        g2 = (ex_with(which, idx, 0.25) - ex_with(which, idx, -0.25)) / 0.5
+        assert abs(g1 - g2) <= 1e-9 * max(1.0, abs(g1))
