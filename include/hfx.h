@@ -134,6 +134,32 @@ hfx_status hfx_clear(hfx_ctx *ctx, char which);
  */
 hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices, double *ex_out);
 
+/*
+ * Shard the contraction over central atoms (Sec. III.D: pairs <A,B> are
+ * distributed over processes; here every pair of central atom A goes to
+ * owner[A]).  owner: natoms ranks (host memory, copied); rank: this
+ * context's rank.  NULL owner removes the shard.  The screen and the Sigma
+ * key set stay global; hfx_build then adds only this rank's terms, and the
+ * ranks' fixed-point accumulators (hfx_get_H_fixed) summed elementwise as
+ * 64-bit integers equal, bit for bit, those of an unsharded build.
+ * Errors: HFX_E_ARG (rank or owner out of range).
+ */
+hfx_status hfx_set_shard(hfx_ctx *ctx, const int32_t *owner, int32_t rank);
+
+/*
+ * The last build's Sigma accumulators: two int64 words per element (units of
+ * 2^-32 and 2^-64; element value = w0 2^-32 + w1 2^-64), elements in the
+ * hfx_get_H_all layout.  on_device as in hfx_get_H_all.
+ */
+hfx_status hfx_get_H_fixed(const hfx_ctx *ctx, int64_t *words, int on_device);
+
+/*
+ * Replace the last build's accumulators by words (e.g. the elementwise sum
+ * over ranks of hfx_get_H_fixed) and recompute Sigma and E_X from them;
+ * ex_out (nullable) receives E_X.  The key set must be the last build's.
+ */
+hfx_status hfx_set_H_fixed(hfx_ctx *ctx, const int64_t *words, int on_device, double *ex_out);
+
 /* Number of Sigma blocks of the last build.  HFX_E_STATE if inputs changed since. */
 hfx_status hfx_H_count(const hfx_ctx *ctx, int64_t *nblk);
 

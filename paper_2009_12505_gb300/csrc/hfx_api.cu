@@ -156,6 +156,8 @@ struct hfx_ctx {
   cudaEvent_t sev[4] = {nullptr, nullptr, nullptr, nullptr};
 
   bool sym = false;             // V and D blocks all have transposed mirrors
+  std::vector<int32_t> owner;   // shard: central atom -> rank (empty: no shard)
+  int32_t rank = 0;
   bool c_reordered = false;     // C values changed: neighbour order must be rebuilt
   bool results_valid = false;
   double ex = 0.0;
@@ -949,9 +951,23 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
   int64_t nwaves = 0;
   size_t peak = 0;
   {
-    const size_t nit = ctx->items.size();
-    size_t w0 = 0;
+    const size_t nit_all = ctx->items.size();
+    // item ranges of the central atoms this context owns (all without a shard)
+    std::vector<std::pair<size_t, size_t>> ranges;
+    for (size_t q = 0; q < nit_all;) {
+      size_t e = q;
+      while (e < nit_all && ctx->items[e].a == ctx->items[q].a) ++e;
+      const bool mine = ctx->owner.empty() || ctx->owner[ctx->items[q].a] == ctx->rank;
+      if (mine) {
+        if (!ranges.empty() && ranges.back().second == q) ranges.back().second = e;
+        else ranges.push_back({q, e});
+      }
+      q = e;
+    }
     std::vector<int64_t> offs4;
+    for (const auto &rg : ranges) {
+    const size_t nit = rg.second;
+    size_t w0 = rg.first;
     while (w0 < nit) {
       size_t w1 = w0;
       size_t used = 0;
@@ -995,8 +1011,8 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
       c.w1 = (int64_t)w1;
       c.wg_base = ctx->items[w0].wg_off;
       c.wf_base = ctx->items[w0].wf_off;
-      const int64_t wg_end = (w1 < nit) ? ctx->items[w1].wg_off : ctx->nwg;
-      const int64_t wf_end = (w1 < nit) ? ctx->items[w1].wf_off : ctx->nwf;
+      const int64_t wg_end = (w1 < nit_all) ? ctx->items[w1].wg_off : ctx->nwg;
+      const int64_t wf_end = (w1 < nit_all) ? ctx->items[w1].wf_off : ctx->nwf;
       c.nwg = wg_end - c.wg_base;
       c.nwf = wf_end - c.wf_base;
       c.nbr = ctx->d_nbr.p;
@@ -1139,6 +1155,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
       ++nwaves;
       w0 = w1;
     }
+    }
   }
   CK(cudaEventRecord(ctx->ev[2], st));
   // ---- finalize
@@ -1203,6 +1220,57 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
   S.scratch_bytes = (int64_t)(peak * sizeof(double));
   ctx->ex = ex;
   ctx->results_valid = true;
+  if (ex_out) *ex_out = ex;
+  return HFX_OK;
+}
+
+hfx_status hfx_set_shard(hfx_ctx *ctx, const int32_t *owner, int32_t rank) {
+  if (!ctx) return HFX_E_ARG;
+  if (!owner) {
+    ctx->owner.clear();
+    ctx->rank = 0;
+    ctx->results_valid = false;
+    return HFX_OK;
+  }
+  if (rank < 0) return fail(ctx, HFX_E_ARG, "rank must be >= 0");
+  for (int a = 0; a < ctx->natoms; ++a)
+    if (owner[a] < 0) return fail(ctx, HFX_E_ARG, "owner ranks must be >= 0");
+  ctx->owner.assign(owner, owner + ctx->natoms);
+  ctx->rank = rank;
+  ctx->results_valid = false;
+  return HFX_OK;
+}
+
+hfx_status hfx_get_H_fixed(const hfx_ctx *ctx, int64_t *words, int on_device) {
+  if (!ctx || !words) return HFX_E_ARG;
+  if (!ctx->results_valid) return HFX_E_STATE;
+  const int64_t n = ctx->sig_offs.empty() ? 0 : ctx->sig_offs.back();
+  if (n == 0) return HFX_OK;
+  if (cudaMemcpyAsync(words, ctx->d_acc.p, sizeof(int64_t) * 2 * n,
+                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                      ctx->stream) != cudaSuccess ||
+      cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+    return HFX_E_CUDA;
+  return HFX_OK;
+}
+
+hfx_status hfx_set_H_fixed(hfx_ctx *ctx, const int64_t *words, int on_device, double *ex_out) {
+  if (!ctx || !words) return HFX_E_ARG;
+  if (!ctx->results_valid) return fail(ctx, HFX_E_STATE, "no build whose key set to use");
+  cudaStream_t st = ctx->stream;
+  const int64_t nsig = (int64_t)ctx->sig_keys.size();
+  const int64_t nelem = ctx->sig_offs.empty() ? 0 : ctx->sig_offs.back();
+  if (nelem > 0)
+    CK(cudaMemcpyAsync(ctx->d_acc.p, words, sizeof(int64_t) * 2 * nelem,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  CK(launch_finalize(ctx->d_acc.p, nelem, ctx->d_sigma.p, ctx->d_skeys.p, ctx->d_soffs.p, nsig,
+                     DevBlocks{ctx->K[2].data.p, ctx->K[2].d_offs.p, ctx->K[2].maxabs.p},
+                     DevHash{ctx->d_dhkeys.p, ctx->d_dhvals.p, ctx->dmask}, ctx->d_partials.p,
+                     ctx->d_ex.p, st));
+  double ex = 0.0;
+  CK(cudaMemcpyAsync(&ex, ctx->d_ex.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->ex = ex;
   if (ex_out) *ex_out = ex;
   return HFX_OK;
 }

@@ -74,6 +74,9 @@ def load_library():
             "hfx_stats": (S, [P, P]),
             "hfx_last_error": (ctypes.c_char_p, [P]),
             "hfx_term_noalloc": (S, [i32, i32, i32, i32, i32, i32, P, P, P, P, P, P]),
+            "hfx_set_shard": (S, [P, P, i32]),
+            "hfx_get_H_fixed": (S, [P, P, ctypes.c_int]),
+            "hfx_set_H_fixed": (S, [P, P, ctypes.c_int, P]),
             "hfx_selftest_ozaki": (S, [i32, i32, i32, P, P, P, i32]),
             "hfx_destroy": (None, [P]),
         }
@@ -261,6 +264,29 @@ class Context:
         nn = np.ascontiguousarray(n, np.int32)
         self._check(self._lib.hfx_get_H(self._h, i, j, _p(nn), _p(out)))
         return out
+
+    def set_shard(self, owner, rank: int):
+        """Contract only the pairs of central atoms with owner[a] == rank (None: all)."""
+        if owner is None:
+            self._check(self._lib.hfx_set_shard(self._h, None, 0))
+            return
+        o = np.ascontiguousarray(owner, np.int32)
+        if o.shape[0] != len(self.nao):
+            raise HfxError(1, "owner needs one rank per atom")
+        self._check(self._lib.hfx_set_shard(self._h, _p(o), int(rank)))
+
+    def sigma_fixed(self) -> np.ndarray:
+        """The Sigma accumulators, (nelem, 2) int64 (units 2^-32, 2^-64)."""
+        out = np.zeros((int(self.offsets()[-1]), 2), np.int64)
+        self._check(self._lib.hfx_get_H_fixed(self._h, _p(out), 0))
+        return out
+
+    def set_sigma_fixed(self, words) -> float:
+        """Load summed accumulators and recompute Sigma and E_X; returns E_X."""
+        w = np.ascontiguousarray(words, np.int64)
+        ex = ctypes.c_double()
+        self._check(self._lib.hfx_set_H_fixed(self._h, _p(w), 0, ctypes.byref(ex)))
+        return ex.value
 
     def grad(self, nC: int, nV: int):
         dC = np.zeros(nC, np.float64)

@@ -172,9 +172,11 @@ def cluster_sigma(wl):
     return sig, ao
 
 
-def ab_form(wl, theta: float):
+def ab_form(wl, theta: float, atoms=None, each=None):
     """Algorithm 3 with the block-norm screen; returns ({key: block}, counts,
-    {key: bound}) where bound sums (pA pB nK nL) * S over DROPPED terms."""
+    {key: bound}) where bound sums (pA pB nK nL) * S over DROPPED terms.
+    ``atoms`` limits the central atoms A; ``each(key, block)`` is called with
+    every surviving term's contribution."""
     S = Sites(wl)
     mx = {k: float(np.max(np.abs(v))) for k, v in S.C.items()}
     mv = {k: float(np.max(np.abs(v))) for k, v in S.V.items()}
@@ -190,6 +192,8 @@ def ab_form(wl, theta: float):
             dct[key] = val
 
     for a in range(wl.system.natoms):
+        if atoms is not None and a not in atoms:
+            continue
         A = (a, z3)
         Fs = [(f, n) for (f, n) in S.Cnbr.get(a, [])]
         for (b, nb) in S.Vnbr.get(a, []):
@@ -239,6 +243,8 @@ def ab_form(wl, theta: float):
                         if s > theta:
                             counts[v] += 1
                             add(sig, tk, -ht)
+                            if each is not None:
+                                each(tk, -ht)
                         else:
                             add(bound, tk, dims * s)
     return sig, counts, bound
