@@ -143,8 +143,20 @@ struct hfx_ctx {
   DevBuf<int16_t> d_cy_e, d_c4_e, d_vs_e, d_ps_e, d_cz_e;
   DevBuf<int64_t> d_cz_meta;      // cz_base, cz_rowpre
   DevBuf<int32_t> d_kofs, d_ktotZ;
+  std::vector<int32_t> ktotZ_h;  // per atom: sum of 16 ceil(nao / 16) over its neighbours
   int64_t h_cz_rows = 0;
-  DevBuf<Job> d_zjobs;
+  // D digit tiles for the D_FG / D_FB products
+  DevBuf<__nv_bfloat16> d_dz, d_dzero;
+  DevBuf<int64_t> d_dz_off;
+  DevBuf<int32_t> d_dij, d_aoff;
+  DevBuf<unsigned long long> d_de;
+  int64_t dz_nd = -1;           // D blocks the tile metadata was built for (-1: stale)
+  int dz_ks = 0;
+  int kbmax = 16;
+  ZcPlanShape zc_shape{16, 16, 0};
+  int nsm = 0;
+  DevBuf<ZcJob> d_zcjobs;
+  DevBuf<ZcEnt> d_zcents;
   DevBuf<int64_t> d_split_meta;   // cy_base, cy_rowpre, c4_base, c4_rowpre, vs_base, v_rowpre, nc_start
   DevBuf<int32_t> d_kt;           // ktY, kt4
   std::vector<int32_t> ktY, kt4;
@@ -201,6 +213,7 @@ bool key_ok(const hfx_ctx *ctx, const int32_t *k) {
 void invalidate(hfx_ctx *ctx, int k, bool keys) {
   ctx->K[k].dirty = true;
   if (keys) ctx->K[k].keys_changed = true;
+  if (keys && k == 2) ctx->dz_nd = -1;
   ctx->results_valid = false;
 }
 
@@ -525,6 +538,7 @@ hfx_status split_prepare(hfx_ctx *ctx, int ks) {
     CK(cudaMemcpyAsync(ctx->d_kofs.p, kofs.data(), sizeof(int32_t) * kofs.size(),
                        cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->d_ktotZ.p, ktotZ.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
+  ctx->ktotZ_h = ktotZ;
   CK(cudaStreamSynchronize(st));
   ctx->h_cy_rows = cy_row[n];
   ctx->h_c4_rows = c4_row[n];
@@ -553,6 +567,62 @@ hfx_status split_prepare(hfx_ctx *ctx, int ks) {
                      st));
   CK(cudaStreamSynchronize(st));
   ctx->split_ks = ks;
+  return HFX_OK;
+}
+
+// D digit-tile layout: per D block (i, j, n) a [ks][R x kb] tile, R = 16 or
+// 32 rows (nao(j)), kb = 16 or 32 (nao(i)); per (atom, ao) column maxima.
+hfx_status dz_prepare_meta(hfx_ctx *ctx, int ks) {
+  cudaStream_t st = ctx->stream;
+  const Kind &D = ctx->K[2];
+  const int64_t nd = (int64_t)D.keys.size();
+  const int n = ctx->natoms;
+  std::vector<int64_t> off(nd + 1, 0);
+  std::vector<int32_t> ij(2 * nd);
+  for (int64_t e = 0; e < nd; ++e) {
+    int32_t q[5];
+    hk_unpack(D.keys[e], q);
+    ij[2 * e] = q[0];
+    ij[2 * e + 1] = q[1];
+    const int64_t R = ctx->nao[q[1]] <= 16 ? 16 : 32, kb = ctx->nao[q[0]] <= 16 ? 16 : 32;
+    off[e + 1] = off[e] + (int64_t)ks * R * kb;
+  }
+  std::vector<int32_t> aoff(n + 1, 0);
+  int kbmax = 16, naomax = 1, naomin = 1 << 30;
+  for (int x = 0; x < n; ++x) {
+    aoff[x + 1] = aoff[x] + ctx->nao[x];
+    if (ctx->nao[x] > 16) kbmax = 32;
+    if (ctx->nao[x] > 32)
+      return fail(ctx, HFX_E_ARG, "HFX_OZAKI supports at most 32 NAOs per atom");
+    naomax = std::max(naomax, ctx->nao[x]);
+    naomin = std::min(naomin, ctx->nao[x]);
+  }
+  // staged Y rows per tile: al rows spanned by 128 (al, a) rows, all b, the
+  // 16-column blocks of one G
+  ctx->zc_shape = ZcPlanShape{kbmax, naomax,
+                              (127 / naomin + 2) * naomax * 16 * 8 * ((naomax + 15) / 16)};
+  CK(ctx->d_dz.reserve(std::max<int64_t>(off[nd], 1)));
+  CK(ctx->d_dz_off.reserve(std::max<int64_t>(nd, 1)));
+  CK(ctx->d_dij.reserve(std::max<int64_t>(2 * nd, 1)));
+  CK(ctx->d_aoff.reserve(n + 1));
+  CK(ctx->d_de.reserve(std::max<int32_t>(aoff[n], 1)));
+  CK(ctx->d_dzero.reserve(1024));
+  CK(cudaMemsetAsync(ctx->d_dzero.p, 0, 1024 * sizeof(__nv_bfloat16), st));
+  if (nd) {
+    CK(cudaMemcpyAsync(ctx->d_dz_off.p, off.data(), sizeof(int64_t) * nd, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_dij.p, ij.data(), sizeof(int32_t) * 2 * nd, cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaMemcpyAsync(ctx->d_aoff.p, aoff.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->dz_nd = nd;
+  ctx->dz_ks = ks;
+  ctx->kbmax = kbmax;
+  if (!ctx->nsm) {
+    int dev = 0, sm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev));
+    ctx->nsm = sm;
+  }
   return HFX_OK;
 }
 
@@ -606,6 +676,13 @@ SplitShared split_shared(hfx_ctx *ctx) {
   S.Do = ctx->K[2].d_offs.p;
   S.dhash = DevHash{ctx->d_dhkeys.p, ctx->d_dhvals.p, ctx->dmask};
   S.h_cz_rows = ctx->h_cz_rows;
+  S.dz = ctx->d_dz.p;
+  S.dzero = ctx->d_dzero.p;
+  S.dz_off = ctx->d_dz_off.p;
+  S.dij = ctx->d_dij.p;
+  S.de = ctx->d_de.p;
+  S.aoff = ctx->d_aoff.p;
+  S.h_nd = ctx->dz_nd > 0 ? ctx->dz_nd : 0;
   return S;
 }
 
@@ -938,13 +1015,23 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
       ctx->launches += (SS.h_cy_rows > 0) + (SS.h_c4_rows > 0) + (SS.h_v_rows > 0) +
                        (SS.h_cz_rows > 0);
     }
+    if (ctx->dz_nd < 0 || ctx->dz_ks != nslices) {
+      hfx_status s = dz_prepare_meta(ctx, nslices);
+      if (s != HFX_OK) return s;
+    }
     SS = split_shared(ctx);
-    CK(ctx->d_njobs.reserve(3));
+    // D digit tiles (D may change every build)
+    CK(cudaMemsetAsync(ctx->d_de.p, 0, sizeof(unsigned long long) *
+                                           std::max<size_t>(ctx->d_de.n, 1), st));
+    CK(split_dz_prepare(SS, nslices, st));
+    ctx->launches += 2 * (SS.h_nd > 0);
+    CK(ctx->d_njobs.reserve(4));
     CK(ctx->d_tmacs.reserve(3));
   }
   double tmac_y = 0, tmac_v4 = 0, tmac_z = 0;
+  // D_FG and D_FB pieces on the tensor cores (HFX_ZJOBS=0 keeps them in FP64)
   const char *zenv = std::getenv("HFX_ZJOBS");
-  const bool zjobs = split && zenv && zenv[0] && zenv[0] != '0';
+  const bool zjobs = split && !(zenv && zenv[0] == '0');
   CK(cudaEventRecord(ctx->ev[1], st));
   // ---- contraction waves
   const size_t budget = scratch_budget_doubles();
@@ -976,14 +1063,15 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
       while (w1 < nit) {
         const WorkItem &it = ctx->items[w1];
         const int64_t pA = ctx->nabf[it.a], na = ctx->nao[it.a], nb = ctx->nao[it.b];
-        const int64_t ysz = pA * nb * ctx->aotot[it.b];
-        const int64_t psz = it.dab >= 0 ? pA * na * ctx->aotot[it.b] : 0;
-        const int64_t tsz = (int64_t)it.nG * pA * na * nb;
-        const int64_t qsz = (int64_t)it.nF * pA * na * nb;
-        int64_t pssz = 0;  // bf16 P digits, in doubles
-        if (split) pssz += ysz;  // Y as f32 pairs
-        if (split && it.dab >= 0 && !(ctx->sym && it.role == 2))
-          pssz += ((ctx->aotot[it.b] + 63) / 64) * ctx->kt4[it.a] * nslices * 64 * 32 / 4 + 64;
+        // every region starts on a 256-byte boundary (bulk copies read Y2)
+        auto pad = [](int64_t x) { return (x + 31) / 32 * 32; };
+        const int64_t ysz = pad(pA * nb * ctx->aotot[it.b]);
+        const int64_t psz = it.dab >= 0 ? pad(pA * na * ctx->aotot[it.b]) : 0;
+        // T3 only for the D_AG piece without mirrors; Q only for the FP64 D_FB piece
+        const int64_t tsz = ctx->sym ? 0 : pad((int64_t)it.nG * pA * na * nb);
+        const int64_t qsz = zjobs ? 0 : pad((int64_t)it.nF * pA * na * nb);
+        // Y as f32 pairs in 16-column blocks (D_FG / D_FB products)
+        const int64_t pssz = (split && zjobs) ? pad(pA * nb * ctx->ktotZ_h[it.b]) : 0;
         const size_t need = (size_t)(ysz + psz + tsz + qsz + pssz);
         if (w1 > w0 && used + need > budget) break;
         yo.push_back((int64_t)used);
@@ -1040,15 +1128,13 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
       SplitWave SW{};
       if (split) {
         // per-wave split metadata
-        std::vector<int64_t> prow(nw + 1, 0), psb(nw, -1), ycand(nw + 1, 0), v4cand(nw + 1, 0),
-            zcand(nw + 1, 0);
+        std::vector<int64_t> prow(nw + 1, 0), psb(nw, -1), ycand(nw + 1, 0), v4cand(nw + 1, 0);
         int64_t ps_elems = 0, v4max = 0;
         for (size_t q = 0; q < nw; ++q) {
           const WorkItem &it = ctx->items[w0 + q];
           const int64_t ntv = (ctx->nabf[it.a] + 63) / 64;
           const int64_t mty = ((int64_t)ctx->nao[it.b] * ctx->aotot[it.b] + 127) / 128;
           ycand[q + 1] = ycand[q] + mty * ntv;
-          zcand[q + 1] = zcand[q] + it.nG;
           const bool has = it.dab >= 0 && !(ctx->sym && it.role == 2);
           const int64_t ntp = (ctx->aotot[it.b] + 63) / 64, mt4 = (ctx->aotot[it.a] + 127) / 128;
           prow[q + 1] = prow[q] + (has ? ntp * 64 : 0);
@@ -1064,7 +1150,6 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         wm.insert(wm.end(), psb.begin(), psb.end());
         wm.insert(wm.end(), ycand.begin(), ycand.end());
         wm.insert(wm.end(), v4cand.begin(), v4cand.end());
-        wm.insert(wm.end(), zcand.begin(), zcand.end());
         CK(ctx->d_wave_split.reserve(wm.size()));
         CK(cudaMemcpyAsync(ctx->d_wave_split.p, wm.data(), sizeof(int64_t) * wm.size(),
                            cudaMemcpyHostToDevice, st));
@@ -1072,7 +1157,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         CK(ctx->d_ps_e.reserve(std::max<int64_t>(prow[nw], 1)));
         CK(ctx->d_jobs.reserve(std::max<int64_t>(ycand[nw], 1)));
         CK(ctx->d_jobs4.reserve(std::max<int64_t>(v4max, 1)));
-        CK(cudaMemsetAsync(ctx->d_njobs.p, 0, 3 * sizeof(int), st));
+        CK(cudaMemsetAsync(ctx->d_njobs.p, 0, 4 * sizeof(int), st));
         CK(cudaMemsetAsync(ctx->d_tmacs.p, 0, 3 * sizeof(unsigned long long), st));
         SW.w0 = (int64_t)w0;
         SW.nw = (int32_t)nw;
@@ -1083,9 +1168,8 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         SW.ps_base = ctx->d_wave_split.p + (nw + 1);
         SW.y_candpre = ctx->d_wave_split.p + (nw + 1) + nw;
         SW.v4_candpre = ctx->d_wave_split.p + 2 * (nw + 1) + nw;
-        SW.z_candpre = ctx->d_wave_split.p + 3 * (nw + 1) + nw;
         SW.y2_off = ctx->d_waveoffs.p + 4 * nw;
-        SW.h_zcand = zcand[nw];
+        SW.y2_on = zjobs ? 1 : 0;
         SW.ps = ctx->d_ps.p;
         SW.ps_e = ctx->d_ps_e.p;
         SW.jobs = ctx->d_jobs.p;
@@ -1113,20 +1197,22 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         ctx->launches += (SW.h_prows > 0) + (SW.h_v4cand > 0) + 1;
       }
       if (split && zjobs) {
-        // D_FG and D_FB pieces: count the jobs, size the list, build and run
-        SW.zjobs = nullptr;
-        CK(split_zwave(SS, SW, nslices, st));
-        int nz = 0;
-        CK(cudaMemcpyAsync(&nz, ctx->d_njobs.p + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        CK(ctx->d_zjobs.reserve(std::max(nz, 1)));
-        CK(cudaMemsetAsync(ctx->d_njobs.p + 2, 0, sizeof(int), st));
-        SW.zjobs = ctx->d_zjobs.p;
-        SW.h_zjobs_max = nz;
+        // D_FG and D_FB pieces: count jobs and entries, size the lists, plan and run
         CK(cudaEventRecord(ctx->kev[8], st));
-        CK(split_zwave(SS, SW, nslices, st));
+        CK(split_zc_plan(SS, SW, 0, st));
+        int nz[2] = {0, 0};
+        CK(cudaMemcpyAsync(nz, ctx->d_njobs.p + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        CK(ctx->d_zcjobs.reserve(std::max(nz[0], 1)));
+        CK(ctx->d_zcents.reserve(std::max(nz[1], 1)));
+        CK(cudaMemsetAsync(ctx->d_njobs.p + 2, 0, 2 * sizeof(int), st));
+        SW.zc_jobs = ctx->d_zcjobs.p;
+        SW.zc_ents = ctx->d_zcents.p;
+        SW.h_zc_jobs = nz[0];
+        CK(split_zc_plan(SS, SW, 1, st));
+        CK(split_zc_run(SS, SW, nslices, ctx->zc_shape, ctx->nsm, st));
         CK(cudaEventRecord(ctx->kev[9], st));
-        ctx->launches += 2 * (SW.h_zcand > 0) + (nz > 0);
+        ctx->launches += 2 * (nw > 0) + (nz[0] > 0);
       }
       // the host offsets vector is reused next wave: order the copy first
       CK(cudaStreamSynchronize(st));

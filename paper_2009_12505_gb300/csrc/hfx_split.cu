@@ -348,12 +348,22 @@ __global__ void __launch_bounds__(128, 1) k_gemm(SplitShared S, SplitWave W) {
   const int ea = ea_p[row];
   constexpr int SH = 7 * (KS + 1);
   if (JOB == 0) {
-    // Y[al][rowY] with rowY = b * ncol + col(G,g); columns al of this tile
-    const int nrow = S.nao[it.b] * S.ncol[it.b];
+    // Y[al][rowY] with rowY = b * ncol + col(G,g); columns al of this tile.
+    // Y2 (f32 pairs) in 16-column blocks: [cb][al][b][16], cb = kofs(G) / 16 + g / 16
+    const int nb = S.nao[it.b], ncol = S.ncol[it.b];
+    const int nrow = nb * ncol;
     const int rowY = jb.mt * TM + row;
     const int pA = S.nabf[it.a];
     double *Y = W.scratch + W.y_off[wl];
     float2 *Y2 = reinterpret_cast<float2 *>(W.scratch + W.y2_off[wl]);
+    int64_t y2row = -1;
+    if (W.y2_on && rowY < nrow) {
+      const int b = rowY / ncol, col = rowY - b * ncol;
+      const int G = entry_of(S.nbr, it.gbase, it.nG, col);
+      const int g = col - S.nbr[it.gbase + G].aopre;
+      const int cb = S.kofs[it.gbase + G] / 16 + g / 16;
+      y2row = (((int64_t)cb * pA) * nb + b) * 16 + (g & 15);
+    }
     for (int c0 = 0; c0 < NT; c0 += 32) {
       long long Wv[32];
 #pragma unroll
@@ -373,7 +383,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm(SplitShared S, SplitWave W) {
           if (al < pA) {
             const int e = ea + eb_p[c0 + i] - SH;
             Y[(int64_t)al * nrow + rowY] = scaled_i64(Wv[i], e);
-            Y2[(int64_t)al * nrow + rowY] = pair_i64(Wv[i], e);
+            if (y2row >= 0) Y2[y2row + (int64_t)al * nb * 16] = pair_i64(Wv[i], e);
           }
         }
       }

@@ -13,6 +13,27 @@ struct Job {
   int32_t mt, nt, k0, nk;
 };
 
+// One job of the D_FG / D_FB product: up to two column blocks (G index in
+// N[B], piece 1 = D_FG or 2 = D_FB) of work item w, over the F entries
+// [ent, ent + nent) of the union of their survivors.
+struct ZcJob {
+  int32_t w;
+  int16_t g[2];
+  int8_t piece[2];
+  int8_t nblk;
+  int8_t pad;
+  int32_t nent;
+  int32_t pad2;
+  int64_t ent;
+};
+
+// One F of a job: its K offset and width in the A operand, and per column
+// block the element offset of the D digit tile (-1: screened out, zeros).
+struct ZcEnt {
+  int32_t kofs, kb;
+  int64_t dz[2];
+};
+
 // Per-build data: work items, screen output and the digit-sliced C and V.
 struct SplitShared {
   int32_t natoms;
@@ -50,6 +71,14 @@ struct SplitShared {
   const double *Dd;
   const int64_t *Do;
   DevHash dhash;
+  // D blocks as transposed digit tiles for the D_FG / D_FB products
+  __nv_bfloat16 *dz;
+  const __nv_bfloat16 *dzero;      // zero tile (2 KB)
+  const int64_t *dz_off;           // per D block
+  const int32_t *dij;              // per D block: (i, j)
+  unsigned long long *de;          // per (atom, ao) column maximum (bit pattern)
+  const int32_t *aoff;             // per atom: first (atom, ao) index
+  int64_t h_nd;                    // D blocks
   int64_t h_cy_rows, h_c4_rows, h_v_rows, h_cz_rows;  // host copies of the row totals
 };
 
@@ -65,22 +94,34 @@ struct SplitWave {
   int16_t *ps_e;
   const int64_t *y_candpre, *v4_candpre;
   Job *jobs, *jobs4;
-  int *njobs;                      // [0] Y jobs, [1] D_AB jobs, [2] Z jobs
+  int *njobs;                      // [0] Y jobs, [1] D_AB jobs, [2] Z jobs, [3] Z entries
   unsigned long long *tmacs;       // [0] Y, [1] D_AB, [2] Z: multiply-adds of the launched jobs
   int64_t h_ycand, h_v4cand, h_prows, h_v4jobs_max;
-  // Y as (hi, lo) f32 pairs, [al][b][ncol], for the Z-job epilogues
+  // Y as (hi, lo) f32 pairs in 16-column blocks, [cb][al][b][16], for the
+  // D_FG / D_FB product epilogues; written only when y2_on (the region exists)
   const int64_t *y2_off;
-  // Z jobs (D_FG and D_FB pieces): candidates (pair, G) and the job list
-  const int64_t *z_candpre;        // per item: nG if it has such work else 0, nw + 1
-  Job *zjobs;                      // null: count the jobs only
-  int64_t h_zcand, h_zjobs_max;
+  int32_t y2_on;
+  // D_FG and D_FB products: job list and F entries
+  ZcJob *zc_jobs;
+  ZcEnt *zc_ents;
+  int64_t h_zc_jobs;
 };
 
 cudaError_t split_slice_inputs(const SplitShared &S, int ks, cudaStream_t st);
-// Z jobs (D_FG and D_FB pieces) for one wave; after phase 0 (needs Y pairs).
-// With W.zjobs null only counts the jobs into W.njobs[2].
-cudaError_t split_zwave(const SplitShared &S, const SplitWave &W, int ks, cudaStream_t st);
 cudaError_t split_slice_cz(const SplitShared &S, int ks, cudaStream_t st);
+// D digit tiles (needs S.de zeroed); run whenever D changes.
+cudaError_t split_dz_prepare(const SplitShared &S, int ks, cudaStream_t st);
+// D_FG / D_FB job plan for one wave: fill == 0 counts jobs and entries into
+// W.njobs[2], W.njobs[3]; fill == 1 writes W.zc_jobs and W.zc_ents.
+cudaError_t split_zc_plan(const SplitShared &S, const SplitWave &W, int fill, cudaStream_t st);
+// Launch shape of the D_FG / D_FB products: widest F block (16 or 32),
+// largest block output count, shared bytes of one staged Y block.
+struct ZcPlanShape {
+  int kbmax, nout_max, ybytes;
+};
+// D_FG / D_FB products of one wave (after phase 0: needs the Y pairs).
+cudaError_t split_zc_run(const SplitShared &S, const SplitWave &W, int ks, const ZcPlanShape &P,
+                         int nsm, cudaStream_t st);
 // phase 0: Y jobs; phase 1: P slices and D_AB jobs
 cudaError_t split_wave(const SplitShared &S, const SplitWave &W, int ks, int phase,
                        cudaStream_t st);

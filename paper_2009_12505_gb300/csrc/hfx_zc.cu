@@ -1,0 +1,783 @@
+// HFX_OZAKI: the D_FG and D_FB pieces of Algorithm 3 on the tensor cores.
+//
+// For a pair <A,B> and a neighbour G of B, with F running over the neighbours
+// of A that survive the screen for the piece,
+//   D_FG piece:  Z_G[(al,a)][g] = sum_F sum_f C_AF[al][a][f] D_FG[f][g]
+//                Sigma_AB[a][b] -= sum_{al,g} Z_G[(al,a)][g] Y_G[al][b][g]
+//   D_FB piece:  X_G[(al,a)][b] = sum_F sum_f C_AF[al][a][f] D_FB[f][b]
+//                Sigma_AG[a][g] -= sum_{al,b} X_G[(al,a)][b] Y_G[al][b][g]
+// These are Algorithm 3's T and Ht stages contracted D-first: the sums over F
+// and the final contraction are reassociations of exact sums.
+//
+// Column blocks and jobs.  A column block is one (G, piece) with survivors:
+// its Z columns are the rows of the transposed D blocks D_FG^T (piece 1) or
+// D_FB^T (piece 2), 16 or 32 of them.  Consecutive blocks of a pair (in G
+// order, D_FG before D_FB) are packed into groups of 32 columns; a job is one
+// group and a run of the union of its blocks' surviving F with at most 640 K
+// (so every digit-order group sum stays an exact f32 integer), over every
+// 128-row tile of (al, a).  Within a job, a D block that is screened out for
+// one of the blocks is a zero tile.
+//
+// Digit-stacked products.  A (C of atom A, rows (al,a), K = F blocks) and B
+// (D blocks, transposed) are split into KS balanced base-128 digits, exact in
+// bf16.  The B digits of one K step are stacked along N (digit j at rows
+// 32 j .. 32 j + 31), so one tcgen05.mma with A digit i, N = 32 (KS - i) and
+// accumulator column offset 32 i adds every product of digit order i + j
+// into TMEM columns [32 (i + j), 32 (i + j + 1)): KS MMAs per K step instead of
+// KS (KS + 1) / 2 narrow ones.  The epilogue recombines the order groups into
+// one exact int64 per element.
+//
+// Roles (one CTA per SM, persistent over a static round-robin job split):
+// warp 8 streams A and B tiles with 1-D bulk copies into a ring of shared
+// stages; warp 9 issues the MMAs into one of two TMEM accumulators; warp 10
+// copies the Y rows of each tile (f32 pairs, laid out [16-column block][al]
+// [b][16] so a tile's rows are contiguous) into one of two shared buffers;
+// warps 0-7 read an accumulator (warp w: TMEM lanes 32 (w % 4).., columns
+// 16 (w / 4)..), turn Z into f32 pairs, contract with Y in double-float
+// arithmetic, reduce over al through shared memory in a fixed order and add
+// each finished block to the fixed-point Sigma (and its mirror for Hermitian
+// inputs) once per job.  Every wait is bounded; on expiry the kernel records
+// HFX_DEV_ERR_TIMEOUT, drains its copies and MMAs, frees TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "hfx_split.h"
+#include "split_common.cuh"
+
+namespace split {
+
+constexpr int ZC_COLS = 32;                      // Z columns per job
+constexpr int ZC_EPI = 8;                        // epilogue warps
+constexpr int ZC_THREADS = (ZC_EPI + 3) * 32;    // + A/B loader, MMA issuer, Y loader
+constexpr int ZC_KMAX = 640;                     // K per job: exact f32 group sums
+constexpr int ZC_OWN = 8;                        // owned outputs per epilogue thread (2 x 32 x 32 / 256)
+constexpr long long ZC_WAIT = 2000000000ll;      // cycles per bounded wait
+
+__host__ __device__ __forceinline__ int kb_of(int nao) { return nao <= 16 ? 16 : 32; }
+
+// element offset of (r, c) in an [R x kb] K-major core-matrix tile
+__device__ __forceinline__ int tile_off_kb(int r, int c, int kb) {
+  return ((r >> 3) * (kb >> 3) + (c >> 3)) * 64 + (r & 7) * 8 + (c & 7);
+}
+
+// ---------------------------------------------------------------- operands
+
+// C of atom x as rows (al, a), K = F blocks (one exponent per row).
+template <int KS>
+__global__ void k_slice_cz(SplitShared S) {
+  const int64_t grow = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (grow >= S.cz_rowpre[S.natoms]) return;
+  int lo = 0, hi = S.natoms - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (S.cz_rowpre[mid] <= grow) lo = mid; else hi = mid - 1;
+  }
+  const int x = lo;
+  const int r = (int)(grow - S.cz_rowpre[x]);
+  const int nx = S.nao[x], px = S.nabf[x];
+  const bool live = r < px * nx;
+  const int64_t base = S.nc_start[x];
+  const int n = (int)(S.nc_start[x + 1] - base);
+  const int ktot = S.ktotZ[x];
+  long long mbits = 0;
+  if (live)
+    for (int q = 0; q < n; ++q) {
+      const NbrEntry &e = S.nbr[base + q];
+      const int nf = S.nao[e.other];
+      for (int f = lane; f < nf; f += 32)
+        mbits = max(mbits, __double_as_longlong(S.Cd[S.Co[e.cblk] + (int64_t)r * nf + f]) &
+                               0x7FFFFFFFFFFFFFFFll);
+    }
+  for (int o = 16; o; o >>= 1) mbits = max(mbits, __shfl_xor_sync(0xffffffffu, mbits, o));
+  const int ex = row_exponent(mbits);
+  if (lane == 0) S.cz_e[grow] = (int16_t)max(-30000, ex);
+  const int mt = r / 128, rr = r - mt * 128;
+  __nv_bfloat16 *tile0 = S.cz + S.cz_base[x] + (int64_t)mt * ktot * KS * 128;
+  for (int q = 0; q < n; ++q) {
+    const NbrEntry &e = S.nbr[base + q];
+    const int nf = S.nao[e.other], kb = kb_of(nf);
+    __nv_bfloat16 *tile = tile0 + (int64_t)S.kofs[base + q] * KS * 128;
+    for (int f = lane; f < kb; f += 32) {
+      const double v = (live && f < nf) ? S.Cd[S.Co[e.cblk] + (int64_t)r * nf + f] : 0.0;
+      int d[KS];
+      to_digits<KS>(v, ex, d);
+#pragma unroll
+      for (int s = 0; s < KS; ++s)
+        tile[(int64_t)s * kb * 128 + tile_off_kb(rr, f, kb)] = __int2bfloat16_rn(d[s]);
+    }
+  }
+}
+
+// Column maxima of D: de[aoff[j] + y] = max over every block (i, j, n) and x of
+// |D[x][y]| (bit pattern; nonnegative doubles order as integers).
+__global__ void k_dz_exp(SplitShared S) {
+  const int64_t e = blockIdx.x;
+  const int i = S.dij[2 * e], j = S.dij[2 * e + 1];
+  const int nr = S.nao[i], nc = S.nao[j];
+  const double *D = S.Dd + S.Do[e];
+  for (int idx = threadIdx.x; idx < nr * nc; idx += blockDim.x) {
+    const int y = idx % nc;
+    const unsigned long long b =
+        (unsigned long long)(__double_as_longlong(D[idx]) & 0x7FFFFFFFFFFFFFFFll);
+    atomicMax(S.de + S.aoff[j] + y, b);
+  }
+}
+
+// D block (i, j, n) as the transposed digit tile [digit][R x kb]: rows y of
+// atom j (R = 16 or 32), K = x of atom i (kb = 16 or 32), exponent per y.
+template <int KS>
+__global__ void k_dz_slice(SplitShared S) {
+  const int64_t e = blockIdx.x;
+  const int i = S.dij[2 * e], j = S.dij[2 * e + 1];
+  const int nr = S.nao[i], nc = S.nao[j];
+  const int R = nc <= 16 ? 16 : 32, kb = kb_of(nr);
+  const double *D = S.Dd + S.Do[e];
+  __nv_bfloat16 *t = S.dz + S.dz_off[e];
+  for (int idx = threadIdx.x; idx < R * kb; idx += blockDim.x) {
+    const int y = idx / kb, x = idx - y * kb;
+    const bool live = y < nc && x < nr;
+    const double v = live ? D[x * nc + y] : 0.0;
+    const int ex = y < nc ? row_exponent((long long)S.de[S.aoff[j] + y]) : -1000;
+    int d[KS];
+    to_digits<KS>(v, ex, d);
+#pragma unroll
+    for (int s = 0; s < KS; ++s)
+      t[(int64_t)s * R * kb + tile_off_kb(y, x, kb)] = __int2bfloat16_rn(d[s]);
+  }
+}
+
+// ---------------------------------------------------------------- job plan
+
+// Runs of the union of a group's surviving F with at most ZC_KMAX K each: one
+// job per run.  Called by one lane per group.  fill == 0 only counts.
+__device__ void zc_plan_group(const SplitShared &S, const SplitWave &W, const WorkItem &it,
+                              int32_t w, const int (&bg)[2], const int (&bp)[2], int nblk,
+                              int mtz, int fill, unsigned long long &macs) {
+  const uint32_t *mr[2] = {nullptr, nullptr};
+  for (int q = 0; q < nblk; ++q)
+    mr[q] = S.masks + it.mask_off + ((int64_t)bg[q] * 4 + (bp[q] - 1)) * it.nFw;
+  int64_t eg_n[2][4];
+  for (int q = 0; q < nblk; ++q) {
+    const NbrEntry eg = S.nbr[it.gbase + bg[q]];
+    eg_n[q][0] = eg.other;
+    eg_n[q][1] = eg.n[0];
+    eg_n[q][2] = eg.n[1];
+    eg_n[q][3] = eg.n[2];
+  }
+  // cursor over the union bits: word wd, remaining bits u
+  int wd = 0;
+  uint32_t u = 0;
+  auto next = [&](int &f) -> bool {
+    while (!u) {
+      if (wd >= it.nFw) return false;
+      for (int q = 0; q < nblk; ++q) u |= mr[q][wd];
+      ++wd;
+      if (!u) continue;
+    }
+    const int b = __ffs(u) - 1;
+    u &= u - 1;
+    f = (wd - 1) * 32 + b;
+    return true;
+  };
+  int f;
+  bool more = next(f);
+  while (more) {
+    // this run: F from f on while K <= ZC_KMAX (scan ahead on a copy of the cursor)
+    const int wd0 = wd;
+    const uint32_t u0 = u;
+    const int f0 = f;
+    int n = 0, k = 0;
+    int fa = f;
+    bool ma = true;
+    while (ma) {
+      const int kb = kb_of(S.nao[S.nbr[it.fbase + fa].other]);
+      if (k + kb > ZC_KMAX) break;
+      k += kb;
+      ++n;
+      ma = next(fa);
+    }
+    macs += (unsigned long long)mtz * 128 * ZC_COLS * k;
+    int64_t eo = 0;
+    if (!fill) {
+      atomicAdd(W.njobs + 2, 1);
+      atomicAdd(W.njobs + 3, n);
+    } else {
+      const int js = atomicAdd(W.njobs + 2, 1);
+      eo = (int64_t)atomicAdd(W.njobs + 3, n);
+      ZcJob jb{};
+      jb.w = w;
+      jb.nblk = (int8_t)nblk;
+      for (int q = 0; q < 2; ++q) {
+        jb.g[q] = (int16_t)(q < nblk ? bg[q] : -1);
+        jb.piece[q] = (int8_t)(q < nblk ? bp[q] : 0);
+      }
+      jb.nent = n;
+      jb.ent = eo;
+      W.zc_jobs[js] = jb;
+      // entries: rewind to the run start
+      wd = wd0;
+      u = u0;
+      int fe = f0;
+      for (int q = 0; q < n; ++q) {
+        const NbrEntry ef = S.nbr[it.fbase + fe];
+        ZcEnt en{};
+        en.kofs = S.kofs[it.fbase + fe];
+        en.kb = kb_of(S.nao[ef.other]);
+        for (int c = 0; c < 2; ++c) {
+          en.dz[c] = -1;
+          if (c >= nblk || !((mr[c][fe >> 5] >> (fe & 31)) & 1u)) continue;
+          int64_t d;
+          if (bp[c] == 1)
+            d = dh_find(S.dhash, hk_pack(ef.other, (int)eg_n[c][0],
+                                         it.n[0] + (int)eg_n[c][1] - ef.n[0],
+                                         it.n[1] + (int)eg_n[c][2] - ef.n[1],
+                                         it.n[2] + (int)eg_n[c][3] - ef.n[2]));
+          else
+            d = dh_find(S.dhash, hk_pack(ef.other, it.b, it.n[0] - ef.n[0], it.n[1] - ef.n[1],
+                                         it.n[2] - ef.n[2]));
+          if (d < 0) atomicOr(S.err, HFX_DEV_ERR_MISSING);
+          else en.dz[c] = S.dz_off[d];
+        }
+        W.zc_ents[eo + q] = en;
+        if (q + 1 < n) next(fe);
+      }
+      // leave the cursor after the run
+      more = next(fe);
+      f = fe;
+      continue;
+    }
+    more = ma;
+    f = fa;
+  }
+}
+
+// One warp per work item of the wave.  Lane 0 walks the column blocks in G
+// order (D_FG before D_FB) and packs them into groups of at most 32 columns,
+// 32 groups at a time; the lanes then plan one group each.  With fill == 0
+// only counts jobs and entries (W.njobs[2], W.njobs[3]).
+__global__ void __launch_bounds__(128) k_zc_plan(SplitShared S, SplitWave W, int fill) {
+  __shared__ int sgrp[4][32][5];  // g0, p0, g1, p1, nblk
+  const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int wl = blockIdx.x * 4 + wib;
+  if (wl >= W.nw) return;
+  const WorkItem it = S.items[W.w0 + wl];
+  const int pA = S.nabf[it.a], na = S.nao[it.a], nb = S.nao[it.b];
+  const int mtz = (pA * na + 127) / 128;
+  unsigned long long macs = 0;
+  // lane 0 state: cursor (g, piece) and the open group
+  int g = 0, piece = 1, nblk = 0, rows = 0, cg[2] = {0, 0}, cp[2] = {0, 0};
+  bool finished = false;
+  while (true) {
+    int cnt = 0;
+    if (lane == 0) {
+      while (cnt < 32) {
+        // next block
+        int R = 0;
+        bool found = false;
+        while (g < it.nG) {
+          const unsigned bits = S.wg[it.wg_off + g];
+          const bool on = (bits & (piece == 1 ? 1u : 2u)) &&
+                          !(piece == 1 && S.sym && it.role == 2);
+          if (on) {
+            const int ncb = piece == 1 ? S.nao[S.nbr[it.gbase + g].other] : nb;
+            R = ncb <= 16 ? 16 : 32;
+            found = true;
+            break;
+          }
+          if (++piece > 2) { piece = 1; ++g; }
+        }
+        if (!found) {
+          if (nblk) {
+            int *o = sgrp[wib][cnt++];
+            o[0] = cg[0]; o[1] = cp[0]; o[2] = cg[1]; o[3] = cp[1]; o[4] = nblk;
+            nblk = 0;
+            rows = 0;
+          }
+          finished = true;
+          break;
+        }
+        if (rows + R > ZC_COLS && nblk) {
+          int *o = sgrp[wib][cnt++];
+          o[0] = cg[0]; o[1] = cp[0]; o[2] = cg[1]; o[3] = cp[1]; o[4] = nblk;
+          nblk = 0;
+          rows = 0;
+        }
+        cg[nblk] = g;
+        cp[nblk] = piece;
+        ++nblk;
+        rows += R;
+        if (++piece > 2) { piece = 1; ++g; }
+      }
+    }
+    cnt = __shfl_sync(0xffffffffu, cnt, 0);
+    const bool fin = __shfl_sync(0xffffffffu, (int)finished, 0) != 0;
+    __syncwarp();
+    if (lane < cnt) {
+      const int *o = sgrp[wib][lane];
+      const int bg[2] = {o[0], o[2]}, bp[2] = {o[1], o[3]};
+      zc_plan_group(S, W, it, (int32_t)(W.w0 + wl), bg, bp, o[4], mtz, fill, macs);
+    }
+    __syncwarp();
+    if (fin) break;
+  }
+  for (int o = 16; o; o >>= 1) macs += __shfl_xor_sync(0xffffffffu, macs, o);
+  if (fill && lane == 0 && macs) atomicAdd(W.tmacs + 2, macs);
+}
+
+// ---------------------------------------------------------------- product
+
+struct ZcSmem {
+  uint64_t full[4], empty[4], tfull[2], tempty[2], yfull[2], yempty[2], drain;
+  uint32_t tslot;
+  int abort_f;
+};
+
+// Launch shape of k_zc: ybytes = shared bytes per staged Y block (0: the
+// epilogue reads Y from global memory), rs = row stride of the reduction
+// buffer (outputs per block, 16 or 32).
+struct ZcCfg {
+  int ybytes, rs;
+};
+
+// Y rows al in [al0, al0 + nal) of the 16-column block cb: [al][b][16] pairs.
+__device__ __forceinline__ const float2 *zc_y_global(const float2 *Y2, int cb, int pA, int nb,
+                                                     int al) {
+  return Y2 + (((int64_t)cb * pA + al) * nb) * 16;
+}
+
+template <int KS, int KBM>
+__global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W, ZcCfg cfg) {
+  constexpr int NST = KBM == 16 ? 3 : 2;
+  constexpr int A_BYTES = KS * 128 * KBM * 2;
+  constexpr int B_BYTES = KS * ZC_COLS * KBM * 2;
+  constexpr int STG = A_BYTES + B_BYTES;
+  constexpr int SH = 7 * (KS + 1);
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t *ybuf = smem + NST * STG;                                     // [2][2][ybytes]
+  double *red = reinterpret_cast<double *>(ybuf + 4 * cfg.ybytes);     // [2][128][rs]
+  ZcSmem *ctl = reinterpret_cast<ZcSmem *>(red + 2 * 128 * cfg.rs);
+  volatile int *abort_f = &ctl->abort_f;
+  const bool ystage = cfg.ybytes > 0;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int njobs = W.njobs[2];
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      umma::mbar_init(&ctl->full[s], 1);
+      umma::mbar_init(&ctl->empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      umma::mbar_init(&ctl->tfull[b], 1);
+      umma::mbar_init(&ctl->tempty[b], ZC_EPI);
+      umma::mbar_init(&ctl->yfull[b], 1);
+      umma::mbar_init(&ctl->yempty[b], ZC_EPI);
+    }
+    umma::mbar_init(&ctl->drain, 1);
+    ctl->abort_f = 0;
+    umma::fence_barrier_init();
+  }
+  if (warp == 0) {
+    umma::tmem_alloc(&ctl->tslot, 512);
+    umma::tmem_relinquish();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tbase = ctl->tslot;
+
+  if (warp == ZC_EPI) {
+    // ------------------------------------------------------------ A / B loader
+    if (lane == 0) {
+      long long step = 0;
+      for (int j = blockIdx.x; j < njobs && !*abort_f; j += gridDim.x) {
+        const ZcJob jb = W.zc_jobs[j];
+        const WorkItem it = S.items[jb.w];
+        const int mtz = (S.nabf[it.a] * S.nao[it.a] + 127) / 128;
+        const __nv_bfloat16 *Abase = S.cz + S.cz_base[it.a];
+        const int64_t ktot = S.ktotZ[it.a];
+        const int rofs[2] = {0, 16};
+        // B rows per block: 16 each for two blocks; 16 or 32 for one
+        int Rb[2] = {16, 16};
+        if (jb.nblk == 1) {
+          const int ncb = jb.piece[0] == 1 ? S.nao[S.nbr[it.gbase + jb.g[0]].other] : S.nao[it.b];
+          Rb[0] = ncb <= 16 ? 16 : 32;
+        }
+        for (int mt = 0; mt < mtz && !*abort_f; ++mt)
+          for (int q = 0; q < jb.nent; ++q, ++step) {
+            const ZcEnt en = W.zc_ents[jb.ent + q];
+            const int s = (int)(step % NST);
+            if (step >= NST &&
+                !umma::mbar_wait(&ctl->empty[s], (uint32_t)((step / NST - 1) & 1), S.err,
+                                 ZC_WAIT)) {
+              *abort_f = 1;
+              break;
+            }
+            uint8_t *st = smem + s * STG;
+            uint8_t *bs = st + A_BYTES;
+            const int kb = en.kb;
+            const uint32_t abytes = (uint32_t)(KS * 128 * kb * 2);
+            uint32_t bbytes = 0;
+            for (int b = 0; b < jb.nblk; ++b) bbytes += (uint32_t)(KS * Rb[b] * kb * 2);
+            umma::mbar_arrive_expect_tx(&ctl->full[s], abytes + bbytes);
+            umma::bulk_g2s(st, Abase + ((int64_t)mt * ktot + en.kofs) * KS * 128, abytes,
+                           &ctl->full[s]);
+            for (int b = 0; b < jb.nblk; ++b) {
+              const uint32_t tb = (uint32_t)(Rb[b] * kb * 2);
+              for (int d = 0; d < KS; ++d) {
+                const __nv_bfloat16 *src =
+                    en.dz[b] >= 0 ? S.dz + en.dz[b] + (int64_t)d * Rb[b] * kb : S.dzero;
+                umma::bulk_g2s(bs + d * (ZC_COLS * kb * 2) + rofs[b] * kb * 2, src, tb,
+                               &ctl->full[s]);
+              }
+            }
+          }
+      }
+      // drain: the last stages issued must have landed before the CTA exits
+      const long long first = step > NST ? step - NST : 0;
+      for (long long t = first; t < step; ++t)
+        umma::mbar_wait(&ctl->full[t % NST], (uint32_t)((t / NST) & 1), S.err, ZC_WAIT);
+    }
+  } else if (warp == ZC_EPI + 2) {
+    // ------------------------------------------------------------ Y loader
+    if (lane == 0 && ystage) {
+      long long hand = 0;
+      for (int j = blockIdx.x; j < njobs && !*abort_f; j += gridDim.x) {
+        const ZcJob jb = W.zc_jobs[j];
+        const WorkItem it = S.items[jb.w];
+        const int wl = (int)(jb.w - W.w0);
+        const int pA = S.nabf[it.a], na = S.nao[it.a], nb = S.nao[it.b];
+        const int mtz = (pA * na + 127) / 128;
+        const float2 *Y2 = reinterpret_cast<const float2 *>(W.scratch + W.y2_off[wl]);
+        for (int mt = 0; mt < mtz && !*abort_f; ++mt, ++hand) {
+          const int tb = (int)(hand & 1);
+          const long long use = hand >> 1;
+          if (use >= 1 &&
+              !umma::mbar_wait(&ctl->yempty[tb], (uint32_t)((use - 1) & 1), S.err, ZC_WAIT)) {
+            *abort_f = 1;
+            break;
+          }
+          const int al0 = mt * 128 / na, al1 = min(pA - 1, (mt * 128 + 127) / na);
+          const int nal = al1 - al0 + 1;
+          uint32_t bytes = 0;
+          for (int b = 0; b < jb.nblk; ++b) {
+            const NbrEntry eg = S.nbr[it.gbase + jb.g[b]];
+            bytes += (uint32_t)(((S.nao[eg.other] + 15) / 16) * nal * nb * 16 * 8);
+          }
+          umma::mbar_arrive_expect_tx(&ctl->yfull[tb], bytes);
+          for (int b = 0; b < jb.nblk; ++b) {
+            const NbrEntry eg = S.nbr[it.gbase + jb.g[b]];
+            const int ncbg = (S.nao[eg.other] + 15) / 16, cb = S.kofs[it.gbase + jb.g[b]] / 16;
+            const uint32_t part = (uint32_t)(nal * nb * 16 * 8);
+            uint8_t *dst = ybuf + (tb * 2 + b) * cfg.ybytes;
+            for (int k = 0; k < ncbg; ++k)
+              umma::bulk_g2s(dst + k * part, zc_y_global(Y2, cb + k, pA, nb, al0), part,
+                             &ctl->yfull[tb]);
+          }
+        }
+      }
+    }
+  } else if (warp == ZC_EPI + 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      long long step = 0, hand = 0;
+      uint32_t idesc[KS];
+#pragma unroll
+      for (int i = 0; i < KS; ++i) idesc[i] = umma::idesc_bf16_f32(128, ZC_COLS * (KS - i));
+      for (int j = blockIdx.x; j < njobs && !*abort_f; j += gridDim.x) {
+        const ZcJob jb = W.zc_jobs[j];
+        const WorkItem it = S.items[jb.w];
+        const int mtz = (S.nabf[it.a] * S.nao[it.a] + 127) / 128;
+        for (int mt = 0; mt < mtz && !*abort_f; ++mt, ++hand) {
+          const int tb = (int)(hand & 1);
+          const long long use = hand >> 1;
+          if (use >= 1 &&
+              !umma::mbar_wait(&ctl->tempty[tb], (uint32_t)((use - 1) & 1), S.err, ZC_WAIT)) {
+            *abort_f = 1;
+            break;
+          }
+          umma::fence_after_sync();
+          const uint32_t dcol = tbase + (uint32_t)(tb * 256);
+          bool ok = true;
+          for (int q = 0; q < jb.nent; ++q, ++step) {
+            const int kb = W.zc_ents[jb.ent + q].kb;
+            const int s = (int)(step % NST);
+            if (!umma::mbar_wait(&ctl->full[s], (uint32_t)((step / NST) & 1), S.err, ZC_WAIT)) {
+              ok = false;
+              break;
+            }
+            umma::fence_after_sync();
+            const uint32_t a0 = umma::smem_u32(smem + s * STG);
+            const uint32_t b0 = a0 + A_BYTES;
+            const uint32_t sbo = (uint32_t)(kb / 8) * 128;
+            for (int ks = 0; ks < kb / 16; ++ks)
+#pragma unroll
+              for (int i = 0; i < KS; ++i) {
+                const uint64_t ad = umma::smem_desc(a0 + i * (128 * kb * 2) + ks * 256, 128, sbo);
+                const uint64_t bd = umma::smem_desc(b0 + ks * 256, 128, sbo);
+                umma::mma_bf16(dcol + (uint32_t)(i * ZC_COLS), ad, bd, idesc[i],
+                               (q | ks | i) ? 1u : 0u);
+              }
+            umma::mma_commit(&ctl->empty[s]);
+          }
+          if (!ok) { *abort_f = 1; break; }
+          umma::mma_commit(&ctl->tfull[tb]);
+        }
+      }
+      umma::mma_commit(&ctl->drain);
+      umma::mbar_wait(&ctl->drain, 0, S.err, ZC_WAIT);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q4 = warp & 3, hf = warp >> 2;
+    const int row = q4 * 32 + lane;
+    const int et = threadIdx.x;  // 0 .. 255
+    const int rs = cfg.rs;
+    long long hand = 0;
+    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+      const ZcJob jb = W.zc_jobs[j];
+      const WorkItem it = S.items[jb.w];
+      const int wl = (int)(jb.w - W.w0);
+      const int pA = S.nabf[it.a], na = S.nao[it.a], nb = S.nao[it.b];
+      const int mtz = (pA * na + 127) / 128;
+      const float2 *Y2 = reinterpret_cast<const float2 *>(W.scratch + W.y2_off[wl]);
+      // blocks: rows, outputs, columns
+      int Rb[2] = {16, 16}, nout[2] = {0, 0}, ncv[2] = {0, 0}, gat[2] = {0, 0}, gcb[2] = {0, 0},
+          gncb[2] = {0, 0};
+      for (int b = 0; b < jb.nblk; ++b) {
+        const NbrEntry eg = S.nbr[it.gbase + jb.g[b]];
+        const int ng = S.nao[eg.other];
+        gat[b] = eg.other;
+        gcb[b] = S.kofs[it.gbase + jb.g[b]] / 16;
+        gncb[b] = (ng + 15) / 16;
+        ncv[b] = jb.piece[b] == 1 ? ng : nb;
+        nout[b] = jb.piece[b] == 1 ? nb : ng;
+        Rb[b] = ncv[b] <= 16 ? 16 : 32;
+      }
+      // this warp's columns: block hb, columns [c0, c0 + 16) of it
+      int hb = -1, c0 = 0;
+      if (hf == 0) hb = 0;
+      else if (jb.nblk == 2) hb = 1;
+      else if (Rb[0] == 32) { hb = 0; c0 = 16; }
+      const int piece = hb >= 0 ? jb.piece[hb] : 0;
+      // column exponents of this warp's 16 columns
+      int ecol[16];
+      {
+        const int at = hb >= 0 ? (piece == 1 ? gat[hb] : it.b) : 0;
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const int cc = c0 + c;
+          ecol[c] = (hb >= 0 && cc < ncv[hb])
+                        ? row_exponent((long long)S.de[S.aoff[at] + cc]) : -1000;
+        }
+      }
+      double jacc[ZC_OWN];
+#pragma unroll
+      for (int k = 0; k < ZC_OWN; ++k) jacc[k] = 0.0;
+      const int own0 = jb.nblk > 0 ? na * nout[0] : 0;
+      const int nown = own0 + (jb.nblk > 1 ? na * nout[1] : 0);
+      bool aborted = false;
+      for (int mt = 0; mt < mtz; ++mt, ++hand) {
+        const int tb = (int)(hand & 1);
+        const uint32_t par = (uint32_t)((hand >> 1) & 1);
+        bool okw = umma::mbar_wait(&ctl->tfull[tb], par, S.err, ZC_WAIT);
+        if (okw && ystage) okw = umma::mbar_wait(&ctl->yfull[tb], par, S.err, ZC_WAIT);
+        // the same decision in every epilogue warp
+        if (umma::bar_any(!okw || *abort_f, 256)) {
+          *abort_f = 1;
+          aborted = true;
+          break;
+        }
+        umma::fence_after_sync();
+        const int rowZ = mt * 128 + row;
+        const bool rvalid = rowZ < pA * na;
+        const int al = rvalid ? rowZ / na : 0;
+        const int al0 = mt * 128 / na, al1 = min(pA - 1, (mt * 128 + 127) / na);
+        const int nal = al1 - al0 + 1;
+        long long Wv[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) Wv[c] = 0;
+        if (hb >= 0) {
+#pragma unroll
+          for (int g = 0; g < KS; ++g) {
+            float v[16];
+            umma::tmem_ld16(tbase + (uint32_t)(tb * 256) + ((uint32_t)(q4 * 32) << 16) +
+                                (uint32_t)(g * ZC_COLS + hf * 16),
+                            v);
+            const long long sc = 1ll << (7 * (KS - 1 - g));
+#pragma unroll
+            for (int c = 0; c < 16; ++c) Wv[c] += (long long)__float2int_rn(v[c]) * sc;
+          }
+        }
+        umma::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&ctl->tempty[tb]);
+        // Y rows of this thread's al in 16-column block k of G: [b][16] pairs
+        auto yrow = [&](int k) -> const float2 * {
+          if (ystage)
+            return reinterpret_cast<const float2 *>(ybuf + (tb * 2 + hb) * cfg.ybytes) +
+                   ((int64_t)k * nal + (al - al0)) * nb * 16;
+          return zc_y_global(Y2, gcb[hb] + k, pA, nb, al);
+        };
+        // Z (f32 pairs) and the contraction with Y, one output at a time
+        if (hb >= 0 && rvalid) {
+          const int eA = S.cz_e[S.cz_rowpre[it.a] + rowZ];
+          const int no = nout[hb];
+          const int cend = min(16, ncv[hb] - c0);
+          float2 z[16];
+#pragma unroll
+          for (int c = 0; c < 16; ++c)
+            z[c] = c < cend ? pair_i64(Wv[c], eA + ecol[c] - SH) : make_float2(0.f, 0.f);
+          double *rr = red + ((int64_t)hf * 128 + row) * rs;
+          if (piece == 1) {  // out b: sum_g Z[g] Y[al][b][G, g],  g = c0 + c
+            const float2 *y0 = yrow(c0 >> 4);
+            for (int o = 0; o < no; ++o) {
+              const float2 *y = y0 + o * 16;
+              float sh = 0.f, sl = 0.f;
+#pragma unroll
+              for (int c = 0; c < 16; ++c)
+                if (c < cend) df_mac(sh, sl, z[c], y[c]);
+              rr[o] = (double)sh + (double)sl;
+            }
+          } else {           // out g: sum_b X[b] Y[al][b][G, g],  b = c0 + c
+            for (int o = 0; o < no; ++o) {
+              const float2 *y = yrow(o >> 4) + c0 * 16 + (o & 15);
+              float sh = 0.f, sl = 0.f;
+#pragma unroll
+              for (int c = 0; c < 16; ++c)
+                if (c < cend) df_mac(sh, sl, z[c], y[c * 16]);
+              rr[o] = (double)sh + (double)sl;
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&ctl->yempty[tb]);
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        // owners: (block, a, o) summed over the tile's rows (al, a) in order
+        const int r0 = mt * 128, rend = min(pA * na, r0 + 128);
+#pragma unroll
+        for (int k = 0; k < ZC_OWN; ++k) {
+          const int idx = et + k * 256;
+          if (idx >= nown) break;
+          const int b = idx < own0 ? 0 : 1;
+          const int rem = idx - (b ? own0 : 0);
+          const int a = rem / nout[b], o = rem - a * nout[b];
+          int r = r0 + ((a - r0 % na) % na + na) % na;
+          double sacc = 0.0;
+          for (; r < rend; r += na) {
+            const int lr = r - r0;
+            if (jb.nblk == 2) sacc += red[((int64_t)b * 128 + lr) * rs + o];
+            else if (Rb[0] == 32) sacc += red[(int64_t)lr * rs + o] + red[(128 + (int64_t)lr) * rs + o];
+            else sacc += red[(int64_t)lr * rs + o];
+          }
+          jacc[k] += sacc;
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+      }
+      if (aborted) break;
+      // add the finished blocks to Sigma (and mirrors)
+#pragma unroll
+      for (int k = 0; k < ZC_OWN; ++k) {
+        const int idx = et + k * 256;
+        if (idx >= nown) break;
+        const int b = idx < own0 ? 0 : 1;
+        const int rem = idx - (b ? own0 : 0);
+        const int a = rem / nout[b], o = rem - a * nout[b];
+        const NbrEntry eg = S.nbr[it.gbase + jb.g[b]];
+        const int nG0 = it.n[0] + eg.n[0], nG1 = it.n[1] + eg.n[1], nG2 = it.n[2] + eg.n[2];
+        int64_t t0, t1 = -1;
+        const bool mir = S.sym && (jb.piece[b] == 2 || it.role == 1);
+        if (jb.piece[b] == 1) {
+          t0 = dh_find(S.shash, hk_pack(it.a, it.b, it.n[0], it.n[1], it.n[2]));
+          if (mir) t1 = dh_find(S.shash, hk_pack(it.b, it.a, -it.n[0], -it.n[1], -it.n[2]));
+        } else {
+          t0 = dh_find(S.shash, hk_pack(it.a, eg.other, nG0, nG1, nG2));
+          if (mir) t1 = dh_find(S.shash, hk_pack(eg.other, it.a, -nG0, -nG1, -nG2));
+        }
+        if (t0 < 0 || (mir && t1 < 0)) {
+          atomicOr(S.err, HFX_DEV_ERR_MISSING);
+          continue;
+        }
+        fx_add(S.acc + 2 * (t0 + (int64_t)a * nout[b] + o), -jacc[k]);
+        if (t1 >= 0) fx_add(S.acc + 2 * (t1 + (int64_t)o * na + a), -jacc[k]);
+      }
+    }
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tbase, 512);
+}
+
+template <int KS>
+cudaError_t zc_run_t(const SplitShared &S, const SplitWave &W, const ZcPlanShape &P, int nsm,
+                     cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>(W.h_zc_jobs, nsm);
+  if (blocks <= 0) return cudaSuccess;
+  auto launch = [&](auto kern, int nst, int stg) -> cudaError_t {
+    const size_t base = (size_t)nst * stg + sizeof(ZcSmem) + 64;
+    ZcCfg cfg{P.ybytes, P.nout_max <= 16 ? 16 : 32};
+    size_t smem = base + 4 * (size_t)cfg.ybytes + 2 * 128 * (size_t)cfg.rs * sizeof(double);
+    if (smem > 227 * 1024) {  // no room to stage Y: read it from global memory
+      cfg.ybytes = 0;
+      smem = base + 2 * 128 * (size_t)cfg.rs * sizeof(double);
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<blocks, ZC_THREADS, smem, st>>>(S, W, cfg);
+    return cudaGetLastError();
+  };
+  if (P.kbmax <= 16) return launch(k_zc<KS, 16>, 3, KS * (128 + ZC_COLS) * 16 * 2);
+  return launch(k_zc<KS, 32>, 2, KS * (128 + ZC_COLS) * 32 * 2);
+}
+
+template <int KS>
+cudaError_t dz_prepare_t(const SplitShared &S, cudaStream_t st) {
+  if (S.h_nd <= 0) return cudaSuccess;
+  k_dz_exp<<<(unsigned)S.h_nd, 128, 0, st>>>(S);
+  k_dz_slice<KS><<<(unsigned)S.h_nd, 128, 0, st>>>(S);
+  return cudaGetLastError();
+}
+
+template <int KS>
+cudaError_t slice_cz_t(const SplitShared &S, cudaStream_t st) {
+  if (S.h_cz_rows > 0)
+    k_slice_cz<KS><<<(unsigned)((S.h_cz_rows * 32 + 255) / 256), 256, 0, st>>>(S);
+  return cudaGetLastError();
+}
+
+}  // namespace split
+
+cudaError_t split_zc_plan(const SplitShared &S, const SplitWave &W, int fill, cudaStream_t st) {
+  if (W.nw <= 0) return cudaSuccess;
+  split::k_zc_plan<<<(unsigned)((W.nw + 3) / 4), 128, 0, st>>>(S, W, fill);
+  return cudaGetLastError();
+}
+
+cudaError_t split_zc_run(const SplitShared &S, const SplitWave &W, int ks, const ZcPlanShape &P,
+                         int nsm, cudaStream_t st) {
+  switch (ks) {
+    case 4: return split::zc_run_t<4>(S, W, P, nsm, st);
+    case 5: return split::zc_run_t<5>(S, W, P, nsm, st);
+    case 6: return split::zc_run_t<6>(S, W, P, nsm, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t split_dz_prepare(const SplitShared &S, int ks, cudaStream_t st) {
+  switch (ks) {
+    case 4: return split::dz_prepare_t<4>(S, st);
+    case 5: return split::dz_prepare_t<5>(S, st);
+    case 6: return split::dz_prepare_t<6>(S, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t split_slice_cz(const SplitShared &S, int ks, cudaStream_t st) {
+  switch (ks) {
+    case 4: return split::slice_cz_t<4>(S, st);
+    case 5: return split::slice_cz_t<5>(S, st);
+    case 6: return split::slice_cz_t<6>(S, st);
+    default: return cudaErrorInvalidValue;
+  }
+}

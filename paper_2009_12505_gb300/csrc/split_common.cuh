@@ -90,9 +90,10 @@ __device__ __forceinline__ int entry_of(const NbrEntry *nbr, int64_t base, int n
 namespace split {
 
 // (hi, lo) f32 pair of W * 2^e with integer conversions only; hi + lo carries
-// about 48 significant bits.  Requires -126 <= e + 63 and e <= 100.
+// about 48 significant bits.  Requires e <= 100.
 __device__ __forceinline__ float2 pair_i64(long long W, int e) {
-  if (W == 0) return make_float2(0.f, 0.f);
+  // |W 2^e| < 2^(63 + e): below 2^-126 it is dropped
+  if (W == 0 || e < -189) return make_float2(0.f, 0.f);
   const float h = __ll2float_rn(W);
   const long long r = W - __float2ll_rn(h);
   const float l = __ll2float_rn(r);
