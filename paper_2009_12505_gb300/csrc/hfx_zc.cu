@@ -327,9 +327,10 @@ __global__ void __launch_bounds__(128) k_zc_plan(SplitShared S, SplitWave W, int
 // ---------------------------------------------------------------- product
 
 struct ZcSmem {
-  uint64_t full[4], empty[4], tfull[2], tempty[2], yfull[2], yempty[2], drain;
+  uint64_t full[8], empty[8], tfull[2], tempty[2], yfull[2], yempty[2], drain;
   uint32_t tslot;
   int abort_f;
+  int ecol[2][16];  // column exponents of the job, per column half
 };
 
 // Launch shape of k_zc: ybytes = shared bytes per staged Y block (0: the
@@ -345,16 +346,15 @@ __device__ __forceinline__ const float2 *zc_y_global(const float2 *Y2, int cb, i
   return Y2 + (((int64_t)cb * pA + al) * nb) * 16;
 }
 
-template <int KS, int KBM>
+template <int KS, int KBM, int NST>
 __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W, ZcCfg cfg) {
-  constexpr int NST = KBM == 16 ? 3 : 2;
   constexpr int A_BYTES = KS * 128 * KBM * 2;
   constexpr int B_BYTES = KS * ZC_COLS * KBM * 2;
   constexpr int STG = A_BYTES + B_BYTES;
   constexpr int SH = 7 * (KS + 1);
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t *ybuf = smem + NST * STG;                                     // [2][2][ybytes]
-  double *red = reinterpret_cast<double *>(ybuf + 4 * cfg.ybytes);     // [2][128][rs]
+  float2 *red = reinterpret_cast<float2 *>(ybuf + 4 * cfg.ybytes);     // [2][128][rs]
   ZcSmem *ctl = reinterpret_cast<ZcSmem *>(red + 2 * 128 * cfg.rs);
   volatile int *abort_f = &ctl->abort_f;
   const bool ystage = cfg.ybytes > 0;
@@ -388,52 +388,64 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
 
   if (warp == ZC_EPI) {
     // ------------------------------------------------------------ A / B loader
-    if (lane == 0) {
-      long long step = 0;
-      for (int j = blockIdx.x; j < njobs && !*abort_f; j += gridDim.x) {
-        const ZcJob jb = W.zc_jobs[j];
-        const WorkItem it = S.items[jb.w];
-        const int mtz = (S.nabf[it.a] * S.nao[it.a] + 127) / 128;
-        const __nv_bfloat16 *Abase = S.cz + S.cz_base[it.a];
-        const int64_t ktot = S.ktotZ[it.a];
-        const int rofs[2] = {0, 16};
-        // B rows per block: 16 each for two blocks; 16 or 32 for one
-        int Rb[2] = {16, 16};
-        if (jb.nblk == 1) {
-          const int ncb = jb.piece[0] == 1 ? S.nao[S.nbr[it.gbase + jb.g[0]].other] : S.nao[it.b];
-          Rb[0] = ncb <= 16 ? 16 : 32;
-        }
-        for (int mt = 0; mt < mtz && !*abort_f; ++mt)
-          for (int q = 0; q < jb.nent; ++q, ++step) {
-            const ZcEnt en = W.zc_ents[jb.ent + q];
-            const int s = (int)(step % NST);
-            if (step >= NST &&
-                !umma::mbar_wait(&ctl->empty[s], (uint32_t)((step / NST - 1) & 1), S.err,
-                                 ZC_WAIT)) {
-              *abort_f = 1;
-              break;
-            }
-            uint8_t *st = smem + s * STG;
-            uint8_t *bs = st + A_BYTES;
-            const int kb = en.kb;
-            const uint32_t abytes = (uint32_t)(KS * 128 * kb * 2);
-            uint32_t bbytes = 0;
-            for (int b = 0; b < jb.nblk; ++b) bbytes += (uint32_t)(KS * Rb[b] * kb * 2);
-            umma::mbar_arrive_expect_tx(&ctl->full[s], abytes + bbytes);
+    // the whole warp walks the steps; lane 0 waits and arms the stage, then
+    // lane 0 copies the A tile and lanes 1 .. nblk KS one B digit tile each
+    long long step = 0;
+    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+      // one decision for the whole warp
+      if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
+      const ZcJob jb = W.zc_jobs[j];
+      const WorkItem it = S.items[jb.w];
+      const int mtz = (S.nabf[it.a] * S.nao[it.a] + 127) / 128;
+      const __nv_bfloat16 *Abase = S.cz + S.cz_base[it.a];
+      const int64_t ktot = S.ktotZ[it.a];
+      // B rows per block: 16 each for two blocks; 16 or 32 for one
+      int R0 = 16;
+      if (jb.nblk == 1) {
+        const int ncb = jb.piece[0] == 1 ? S.nao[S.nbr[it.gbase + jb.g[0]].other] : S.nao[it.b];
+        R0 = ncb <= 16 ? 16 : 32;
+      }
+      // this lane's copy: 0 = A, 1 .. nblk KS = (block, digit)
+      const int cb = lane >= 1 ? (lane - 1) / KS : 0, cd = lane >= 1 ? (lane - 1) % KS : 0;
+      const bool has_b = lane >= 1 && lane <= jb.nblk * KS;
+      const int Rl = jb.nblk == 1 ? R0 : 16;
+      bool ok = true;
+      for (int mt = 0; mt < mtz && ok; ++mt)
+        for (int q = 0; q < jb.nent; ++q, ++step) {
+          const ZcEnt en = W.zc_ents[jb.ent + q];
+          const int s = (int)(step % NST);
+          bool w = true;
+          if (lane == 0) {
+            if (step >= NST)
+              w = umma::mbar_wait(&ctl->empty[s], (uint32_t)((step / NST - 1) & 1), S.err,
+                                  ZC_WAIT);
+            w = w && !*abort_f;
+          }
+          w = __shfl_sync(0xffffffffu, (int)w, 0) != 0;
+          if (!w) {
+            if (lane == 0) *abort_f = 1;
+            ok = false;
+            break;
+          }
+          uint8_t *st = smem + s * STG;
+          const int kb = en.kb;
+          const uint32_t abytes = (uint32_t)(KS * 128 * kb * 2);
+          const uint32_t bbytes = (uint32_t)(KS * kb * 2) * (uint32_t)(jb.nblk * Rl);
+          if (lane == 0) umma::mbar_arrive_expect_tx(&ctl->full[s], abytes + bbytes);
+          __syncwarp();
+          if (lane == 0) {
             umma::bulk_g2s(st, Abase + ((int64_t)mt * ktot + en.kofs) * KS * 128, abytes,
                            &ctl->full[s]);
-            for (int b = 0; b < jb.nblk; ++b) {
-              const uint32_t tb = (uint32_t)(Rb[b] * kb * 2);
-              for (int d = 0; d < KS; ++d) {
-                const __nv_bfloat16 *src =
-                    en.dz[b] >= 0 ? S.dz + en.dz[b] + (int64_t)d * Rb[b] * kb : S.dzero;
-                umma::bulk_g2s(bs + d * (ZC_COLS * kb * 2) + rofs[b] * kb * 2, src, tb,
-                               &ctl->full[s]);
-              }
-            }
+          } else if (has_b) {
+            const int64_t dz = en.dz[cb];
+            const __nv_bfloat16 *src = dz >= 0 ? S.dz + dz + (int64_t)cd * Rl * kb : S.dzero;
+            umma::bulk_g2s(st + A_BYTES + cd * (ZC_COLS * kb * 2) + cb * 16 * kb * 2, src,
+                           (uint32_t)(Rl * kb * 2), &ctl->full[s]);
           }
-      }
-      // drain: the last stages issued must have landed before the CTA exits
+        }
+    }
+    // drain: the last stages issued must have landed before the CTA exits
+    if (lane == 0) {
       const long long first = step > NST ? step - NST : 0;
       for (long long t = first; t < step; ++t)
         umma::mbar_wait(&ctl->full[t % NST], (uint32_t)((t / NST) & 1), S.err, ZC_WAIT);
@@ -560,20 +572,18 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
       else if (jb.nblk == 2) hb = 1;
       else if (Rb[0] == 32) { hb = 0; c0 = 16; }
       const int piece = hb >= 0 ? jb.piece[hb] : 0;
-      // column exponents of this warp's 16 columns
-      int ecol[16];
-      {
+      // column exponents of this warp's 16 columns (shared by the half's warps;
+      // the previous job's last reads are behind the tile barriers)
+      const int *ecol = ctl->ecol[hf];
+      if (q4 == 0 && lane < 16) {
         const int at = hb >= 0 ? (piece == 1 ? gat[hb] : it.b) : 0;
-#pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const int cc = c0 + c;
-          ecol[c] = (hb >= 0 && cc < ncv[hb])
-                        ? row_exponent((long long)S.de[S.aoff[at] + cc]) : -1000;
-        }
+        const int cc = c0 + lane;
+        ctl->ecol[hf][lane] = (hb >= 0 && cc < ncv[hb])
+                                  ? row_exponent((long long)S.de[S.aoff[at] + cc]) : -1000;
       }
-      double jacc[ZC_OWN];
+      float jh[ZC_OWN], jl[ZC_OWN];  // job sums of the owned outputs (f32 pairs)
 #pragma unroll
-      for (int k = 0; k < ZC_OWN; ++k) jacc[k] = 0.0;
+      for (int k = 0; k < ZC_OWN; ++k) { jh[k] = 0.f; jl[k] = 0.f; }
       const int own0 = jb.nblk > 0 ? na * nout[0] : 0;
       const int nown = own0 + (jb.nblk > 1 ? na * nout[1] : 0);
       bool aborted = false;
@@ -619,7 +629,7 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
                    ((int64_t)k * nal + (al - al0)) * nb * 16;
           return zc_y_global(Y2, gcb[hb] + k, pA, nb, al);
         };
-        // Z (f32 pairs) and the contraction with Y, one output at a time
+        // Z (f32 pairs) and the contraction with Y, four outputs at a time
         if (hb >= 0 && rvalid) {
           const int eA = S.cz_e[S.cz_rowpre[it.a] + rowZ];
           const int no = nout[hb];
@@ -628,26 +638,27 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
 #pragma unroll
           for (int c = 0; c < 16; ++c)
             z[c] = c < cend ? pair_i64(Wv[c], eA + ecol[c] - SH) : make_float2(0.f, 0.f);
-          double *rr = red + ((int64_t)hf * 128 + row) * rs;
-          if (piece == 1) {  // out b: sum_g Z[g] Y[al][b][G, g],  g = c0 + c
-            const float2 *y0 = yrow(c0 >> 4);
-            for (int o = 0; o < no; ++o) {
-              const float2 *y = y0 + o * 16;
-              float sh = 0.f, sl = 0.f;
+          float2 *rr = red + ((int64_t)hf * 128 + row) * rs;
+          for (int o0 = 0; o0 < no; o0 += 4) {
+            float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+            const float2 *yp[4];
 #pragma unroll
-              for (int c = 0; c < 16; ++c)
-                if (c < cend) df_mac(sh, sl, z[c], y[c]);
-              rr[o] = (double)sh + (double)sl;
+            for (int u = 0; u < 4; ++u) {
+              const int o = min(o0 + u, no - 1);
+              // piece 1: out b = o, Y[al][b][G, g = c0 + c]; piece 2: out g = o,
+              // Y[al][b = c0 + c][G, g]
+              yp[u] = piece == 1 ? yrow(c0 >> 4) + o * 16 : yrow(o >> 4) + c0 * 16 + (o & 15);
             }
-          } else {           // out g: sum_b X[b] Y[al][b][G, g],  b = c0 + c
-            for (int o = 0; o < no; ++o) {
-              const float2 *y = yrow(o >> 4) + c0 * 16 + (o & 15);
-              float sh = 0.f, sl = 0.f;
+            const int cs = piece == 1 ? 1 : 16;
 #pragma unroll
-              for (int c = 0; c < 16; ++c)
-                if (c < cend) df_mac(sh, sl, z[c], y[c * 16]);
-              rr[o] = (double)sh + (double)sl;
+            for (int c = 0; c < 16; ++c) {
+              if (c >= cend) break;
+#pragma unroll
+              for (int u = 0; u < 4; ++u) df_mac(sh[u], sl[u], z[c], yp[u][c * cs]);
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (o0 + u < no) rr[o0 + u] = make_float2(sh[u], sl[u]);
           }
         }
         __syncwarp();
@@ -663,14 +674,18 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
           const int rem = idx - (b ? own0 : 0);
           const int a = rem / nout[b], o = rem - a * nout[b];
           int r = r0 + ((a - r0 % na) % na + na) % na;
-          double sacc = 0.0;
+          float h = jh[k], l = jl[k];
           for (; r < rend; r += na) {
             const int lr = r - r0;
-            if (jb.nblk == 2) sacc += red[((int64_t)b * 128 + lr) * rs + o];
-            else if (Rb[0] == 32) sacc += red[(int64_t)lr * rs + o] + red[(128 + (int64_t)lr) * rs + o];
-            else sacc += red[(int64_t)lr * rs + o];
+            if (jb.nblk == 2) {
+              df_add(h, l, red[((int64_t)b * 128 + lr) * rs + o]);
+            } else {
+              df_add(h, l, red[(int64_t)lr * rs + o]);
+              if (Rb[0] == 32) df_add(h, l, red[(128 + (int64_t)lr) * rs + o]);
+            }
           }
-          jacc[k] += sacc;
+          jh[k] = h;
+          jl[k] = l;
         }
         asm volatile("bar.sync 1, 256;" ::: "memory");
       }
@@ -698,8 +713,9 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
           atomicOr(S.err, HFX_DEV_ERR_MISSING);
           continue;
         }
-        fx_add(S.acc + 2 * (t0 + (int64_t)a * nout[b] + o), -jacc[k]);
-        if (t1 >= 0) fx_add(S.acc + 2 * (t1 + (int64_t)o * na + a), -jacc[k]);
+        const float2 v = make_float2(jh[k], jl[k]);
+        fx_add_df(S.acc + 2 * (t0 + (int64_t)a * nout[b] + o), v, true);
+        if (t1 >= 0) fx_add_df(S.acc + 2 * (t1 + (int64_t)o * na + a), v, true);
       }
     }
   }
@@ -708,27 +724,36 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
   if (warp == 0) umma::tmem_dealloc(tbase, 512);
 }
 
+// Y staged in shared memory (two buffers per block) with a shorter operand
+// ring, or read from global memory with a deeper ring.
+constexpr bool ZC_STAGE_Y = true;
+
 template <int KS>
 cudaError_t zc_run_t(const SplitShared &S, const SplitWave &W, const ZcPlanShape &P, int nsm,
                      cudaStream_t st) {
   const int blocks = (int)std::min<int64_t>(W.h_zc_jobs, nsm);
   if (blocks <= 0) return cudaSuccess;
-  auto launch = [&](auto kern, int nst, int stg) -> cudaError_t {
-    const size_t base = (size_t)nst * stg + sizeof(ZcSmem) + 64;
-    ZcCfg cfg{P.ybytes, P.nout_max <= 16 ? 16 : 32};
-    size_t smem = base + 4 * (size_t)cfg.ybytes + 2 * 128 * (size_t)cfg.rs * sizeof(double);
-    if (smem > 227 * 1024) {  // no room to stage Y: read it from global memory
-      cfg.ybytes = 0;
-      smem = base + 2 * 128 * (size_t)cfg.rs * sizeof(double);
-    }
+  constexpr size_t kMax = 227 * 1024;
+  const int rs = P.nout_max <= 16 ? 16 : 32;
+  const size_t red = 2 * 128 * (size_t)rs * sizeof(float2) + sizeof(ZcSmem) + 64;
+  auto launch = [&](auto kern, int nst, int kbm, int ybytes) -> cudaError_t {
+    const size_t smem = (size_t)nst * KS * (128 + ZC_COLS) * kbm * 2 + 4 * (size_t)ybytes + red;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<blocks, ZC_THREADS, smem, st>>>(S, W, cfg);
+    kern<<<blocks, ZC_THREADS, smem, st>>>(S, W, ZcCfg{ybytes, rs});
     return cudaGetLastError();
   };
-  if (P.kbmax <= 16) return launch(k_zc<KS, 16>, 3, KS * (128 + ZC_COLS) * 16 * 2);
-  return launch(k_zc<KS, 32>, 2, KS * (128 + ZC_COLS) * 32 * 2);
+  auto fits = [&](int nst, int kbm, int ybytes) {
+    return (size_t)nst * KS * (128 + ZC_COLS) * kbm * 2 + 4 * (size_t)ybytes + red <= kMax;
+  };
+  if (P.kbmax <= 16) {
+    if (ZC_STAGE_Y && fits(3, 16, P.ybytes)) return launch(k_zc<KS, 16, 3>, 3, 16, P.ybytes);
+    if (fits(6, 16, 0)) return launch(k_zc<KS, 16, 6>, 6, 16, 0);
+    return launch(k_zc<KS, 16, 3>, 3, 16, 0);
+  }
+  if (ZC_STAGE_Y && fits(2, 32, P.ybytes)) return launch(k_zc<KS, 32, 2>, 2, 32, P.ybytes);
+  return launch(k_zc<KS, 32, 2>, 2, 32, 0);
 }
 
 template <int KS>

@@ -94,13 +94,57 @@ namespace split {
 __device__ __forceinline__ float2 pair_i64(long long W, int e) {
   // |W 2^e| < 2^(63 + e): below 2^-126 it is dropped
   if (W == 0 || e < -189) return make_float2(0.f, 0.f);
-  const float h = __ll2float_rn(W);
-  const long long r = W - __float2ll_rn(h);
-  const float l = __ll2float_rn(r);
+  // W = a 2^48 + b 2^24 + c with b, c in [0, 2^24): each part exact in f32,
+  // so only 32-bit conversions are needed
+  const float fa = __fmul_rn(__int2float_rn((int)(W >> 48)), 281474976710656.f);
+  const float fb = __fmul_rn(__int2float_rn((int)((W >> 24) & 0xFFFFFF)), 16777216.f);
+  const float fc = __int2float_rn((int)(W & 0xFFFFFF));
+  // (s, t) = fa + fb exactly, then t + fc and a final renormalisation
+  const float s = __fadd_rn(fa, fb);
+  const float bb = __fsub_rn(s, fa);
+  const float t = __fadd_rn(__fsub_rn(fa, __fsub_rn(s, bb)), __fsub_rn(fb, bb));
+  const float l0 = __fadd_rn(t, fc);
+  const float h = __fadd_rn(s, l0);
+  const float hb = __fsub_rn(h, s);
+  const float l = __fadd_rn(__fsub_rn(s, __fsub_rn(h, hb)), __fsub_rn(l0, hb));
   // multiply by 2^e in two steps so neither factor leaves the normal range
   const int e1 = e / 2, e2 = e - e1;
   const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
   return make_float2(__fmul_rn(__fmul_rn(h, s1), s2), __fmul_rn(__fmul_rn(l, s1), s2));
+}
+
+// (sh, sl) += (bh, bl): error-free sum of the high parts, low parts added.
+__device__ __forceinline__ void df_add(float &sh, float &sl, float2 b) {
+  const float s = __fadd_rn(sh, b.x);
+  const float bb = __fsub_rn(s, sh);
+  const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, b.y));
+}
+
+// f in units of 2^-64 as a 128-bit integer (bits below 2^-64 dropped), with
+// integer operations only; |f| < 2^60.
+__device__ __forceinline__ __int128 fx128_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const int ex = (int)((u >> 23) & 255u);
+  if (ex == 0) return 0;  // zero or below 2^-126
+  const long long m = (long long)((u & 0x7FFFFFu) | 0x800000u);
+  const int sh = ex - 150 + 64;  // f = m 2^(ex - 150)
+  __int128 v;
+  if (sh >= 0) v = (__int128)m << sh;
+  else v = sh > -24 ? (__int128)(m >> (-sh)) : (__int128)0;
+  return (u >> 31) ? -v : v;
+}
+
+// Add -(v.x + v.y) (neg) or v.x + v.y to a fixed-point Sigma element
+// (hi: 2^-32 units, lo: 2^-64 units) with integer arithmetic only.
+__device__ __forceinline__ void fx_add_df(unsigned long long *hi_lo, float2 v, bool neg) {
+  __int128 V = fx128_f32(v.x) + fx128_f32(v.y);
+  if (neg) V = -V;
+  const long long hi = (long long)(V >> 32);
+  const long long lo = (long long)(V & (__int128)0xFFFFFFFFll);
+  if (hi) atomicAdd(hi_lo, (unsigned long long)hi);
+  if (lo) atomicAdd(hi_lo + 1, (unsigned long long)lo);
 }
 
 // (sh, sl) += (ah, al) * (bh, bl), error-free products and sums (no
