@@ -683,6 +683,7 @@ SplitShared split_shared(hfx_ctx *ctx) {
   S.de = ctx->d_de.p;
   S.aoff = ctx->d_aoff.p;
   S.h_nd = ctx->dz_nd > 0 ? ctx->dz_nd : 0;
+  S.nsm = ctx->nsm;
   return S;
 }
 

@@ -1,0 +1,320 @@
+// HFX_OZAKI: the Y = V C product and the D_AB piece (Sigma_FG -= C_AF^T P_G)
+// of Algorithm 3 as exact split-precision tcgen05 products, in one persistent
+// kernel per wave.
+//
+// A job is a 128-row x 64-column output tile over up to 20 K tiles of 32 (so
+// every digit-order group sum stays an exact f32 integer):
+//   Y job:    rows (b, G, g) of C_B transposed, columns al of V_AB, K = beta;
+//   D_AB job: rows (F, f) of C_A, columns (G, g) of P, K = (al, a).
+// Both operands are stored as KS balanced base-128 bf16 digits, one exponent
+// per row; the B digits of a K tile are contiguous, so one MMA with A digit i
+// covers up to four B digits j stacked along N at TMEM column 64 (i + j): 9
+// MMAs per K step of 16 instead of KS (KS + 1) / 2 = 21 for KS = 6.
+//
+// Roles (one CTA per SM, static round-robin over the wave's jobs): warp 8
+// copies each K tile's A and B digits (lanes 0 and 1, 1-D bulk copies) into a
+// ring of shared stages; warp 9 issues the MMAs into the TMEM accumulator;
+// warps 0-7 (TMEM lanes 32 (w % 4).., columns 32 (w / 4)..) drain the
+// accumulator into exact int64 sums, release it to the next job's MMAs, and
+// then write Y (FP64 and f32 pairs) or add the surviving Sigma_FG blocks to
+// the fixed-point Sigma.  Every wait is bounded: on expiry the kernel records
+// HFX_DEV_ERR_TIMEOUT, drains its copies and MMAs, frees TMEM and returns.
+#include <cuda_bf16.h>
+
+#include "hfx_split.h"
+#include "split_common.cuh"
+
+namespace split {
+
+constexpr int PG_EPI = 8;                      // epilogue warps
+constexpr int PG_THREADS = (PG_EPI + 2) * 32;  // + loader warp + MMA warp
+constexpr int PG_NST = 3;                      // operand stages
+constexpr long long PG_WAIT = 2000000000ll;    // cycles per bounded wait
+
+struct PgSmem {
+  uint64_t full[PG_NST], empty[PG_NST], tfull, tempty, drain;
+  uint32_t tslot;
+  int abort_f;
+};
+
+// Operand tiles, exponents and K range of job jb.
+template <int KS, int JOB>
+__device__ __forceinline__ void pg_operands(const SplitShared &S, const SplitWave &W,
+                                            const Job &jb, const WorkItem &it,
+                                            const __nv_bfloat16 *&Ab, const __nv_bfloat16 *&Bb,
+                                            const int16_t *&ea_p, const int16_t *&eb_p) {
+  const int wl = (int)(jb.w - W.w0);
+  if (JOB == 0) {
+    const int kt = S.ktY[it.b];
+    Ab = S.cy + S.cy_base[it.b] + ((int64_t)jb.mt * kt + jb.k0) * KS * TM * TK;
+    Bb = S.vs + S.vs_base[it.vblk] + ((int64_t)jb.nt * kt + jb.k0) * KS * NT * TK;
+    ea_p = S.cy_e + S.cy_rowpre[it.b] + jb.mt * TM;
+    eb_p = S.vs_e + S.v_rowpre[it.vblk] + jb.nt * NT;
+  } else {
+    const int kt = S.kt4[it.a];
+    Ab = S.c4 + S.c4_base[it.a] + ((int64_t)jb.mt * kt + jb.k0) * KS * TM * TK;
+    Bb = W.ps + W.ps_base[wl] + ((int64_t)jb.nt * kt + jb.k0) * KS * NT * TK;
+    ea_p = S.c4_e + S.c4_rowpre[it.a] + jb.mt * TM;
+    eb_p = W.ps_e + W.p_rowpre[wl] + jb.nt * NT;
+  }
+}
+
+template <int KS, int JOB>
+__global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWave W) {
+  constexpr int A_BYTES = KS * TM * TK * 2;
+  constexpr int B_BYTES = KS * NT * TK * 2;
+  constexpr int STAGE = A_BYTES + B_BYTES;
+  constexpr int SH = 7 * (KS + 1);
+  extern __shared__ __align__(1024) uint8_t smem[];
+  PgSmem *ctl = reinterpret_cast<PgSmem *>(smem + PG_NST * STAGE);
+  volatile int *abort_f = &ctl->abort_f;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int njobs = W.njobs[JOB];
+  const Job *jobs = JOB == 0 ? W.jobs : W.jobs4;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < PG_NST; ++s) {
+      umma::mbar_init(&ctl->full[s], 1);
+      umma::mbar_init(&ctl->empty[s], 1);
+    }
+    umma::mbar_init(&ctl->tfull, 1);
+    umma::mbar_init(&ctl->tempty, PG_EPI);
+    umma::mbar_init(&ctl->drain, 1);
+    ctl->abort_f = 0;
+    umma::fence_barrier_init();
+  }
+  if (warp == 0) {
+    umma::tmem_alloc(&ctl->tslot, 512);
+    umma::tmem_relinquish();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tbase = ctl->tslot;
+
+  if (warp == PG_EPI) {
+    // ------------------------------------------------------------ loader
+    long long step = 0;
+    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+      if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
+      const Job jb = jobs[j];
+      const WorkItem it = S.items[jb.w];
+      const __nv_bfloat16 *Ab, *Bb;
+      const int16_t *ea_p, *eb_p;
+      pg_operands<KS, JOB>(S, W, jb, it, Ab, Bb, ea_p, eb_p);
+      bool ok = true;
+      for (int kt = 0; kt < jb.nk; ++kt, ++step) {
+        const int s = (int)(step % PG_NST);
+        bool w = true;
+        if (lane == 0) {
+          if (step >= PG_NST)
+            w = umma::mbar_wait(&ctl->empty[s], (uint32_t)((step / PG_NST - 1) & 1), S.err,
+                                PG_WAIT);
+          w = w && !*abort_f;
+        }
+        w = __shfl_sync(0xffffffffu, (int)w, 0) != 0;
+        if (!w) {
+          if (lane == 0) *abort_f = 1;
+          ok = false;
+          break;
+        }
+        uint8_t *st = smem + s * STAGE;
+        if (lane == 0) umma::mbar_arrive_expect_tx(&ctl->full[s], STAGE);
+        __syncwarp();
+        if (lane == 0)
+          umma::bulk_g2s(st, Ab + (int64_t)kt * KS * TM * TK, A_BYTES, &ctl->full[s]);
+        else if (lane == 1)
+          umma::bulk_g2s(st + A_BYTES, Bb + (int64_t)kt * KS * NT * TK, B_BYTES, &ctl->full[s]);
+      }
+      if (!ok) break;
+    }
+    // drain: the last stages issued must have landed before the CTA exits
+    if (lane == 0) {
+      const long long first = step > PG_NST ? step - PG_NST : 0;
+      for (long long t = first; t < step; ++t)
+        umma::mbar_wait(&ctl->full[t % PG_NST], (uint32_t)((t / PG_NST) & 1), S.err, PG_WAIT);
+    }
+  } else if (warp == PG_EPI + 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      long long step = 0, hand = 0;
+      // MMA i, chunk c: A digit i times B digits [4c, 4c + n), n = min(4, KS - i - 4c)
+      uint32_t idesc[4];
+#pragma unroll
+      for (int n = 1; n <= 4; ++n) idesc[n - 1] = umma::idesc_bf16_f32(TM, NT * n);
+      for (int j = blockIdx.x; j < njobs && !*abort_f; j += gridDim.x, ++hand) {
+        const Job jb = jobs[j];
+        if (hand >= 1 &&
+            !umma::mbar_wait(&ctl->tempty, (uint32_t)((hand - 1) & 1), S.err, PG_WAIT)) {
+          *abort_f = 1;
+          break;
+        }
+        umma::fence_after_sync();
+        bool ok = true;
+        for (int kt = 0; kt < jb.nk; ++kt, ++step) {
+          const int s = (int)(step % PG_NST);
+          if (!umma::mbar_wait(&ctl->full[s], (uint32_t)((step / PG_NST) & 1), S.err, PG_WAIT)) {
+            ok = false;
+            break;
+          }
+          umma::fence_after_sync();
+          const uint32_t a0 = umma::smem_u32(smem + s * STAGE), b0 = a0 + A_BYTES;
+#pragma unroll
+          for (int ks = 0; ks < TK / 16; ++ks)
+#pragma unroll
+            for (int i = 0; i < KS; ++i)
+#pragma unroll
+              for (int c = 0; c * 4 < KS - i; ++c) {
+                const int n = min(4, KS - i - 4 * c);
+                const uint64_t ad = umma::smem_desc(a0 + i * TM * TK * 2 + ks * 256, 128, 512);
+                const uint64_t bd =
+                    umma::smem_desc(b0 + 4 * c * NT * TK * 2 + ks * 256, 128, 512);
+                // the two MMAs of digit 0 write every column of the first step
+                umma::mma_bf16(tbase + (uint32_t)((i + 4 * c) * NT), ad, bd, idesc[n - 1],
+                               (kt | ks | i) ? 1u : 0u);
+              }
+          umma::mma_commit(&ctl->empty[s]);
+        }
+        if (!ok) { *abort_f = 1; break; }
+        umma::mma_commit(&ctl->tfull);
+      }
+      umma::mma_commit(&ctl->drain);
+      umma::mbar_wait(&ctl->drain, 0, S.err, PG_WAIT);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q4 = warp & 3, hf = warp >> 2;
+    const int row = q4 * 32 + lane;
+    const int c0 = hf * 32;  // this warp's 32 of the 64 columns
+    long long hand = 0;
+    for (int j = blockIdx.x; j < njobs; j += gridDim.x, ++hand) {
+      const bool okw = umma::mbar_wait(&ctl->tfull, (uint32_t)(hand & 1), S.err, PG_WAIT);
+      if (umma::bar_any(!okw || *abort_f, PG_EPI * 32)) {
+        *abort_f = 1;
+        break;
+      }
+      umma::fence_after_sync();
+      long long Wv[32];
+#pragma unroll
+      for (int i = 0; i < 32; ++i) Wv[i] = 0;
+#pragma unroll
+      for (int g = 0; g < KS; ++g) {
+        float v[32];
+        umma::tmem_ld32(tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(g * NT + c0), v);
+        const long long sc = 1ll << (7 * (KS - 1 - g));
+#pragma unroll
+        for (int i = 0; i < 32; ++i) Wv[i] += (long long)__float2int_rn(v[i]) * sc;
+      }
+      // the accumulator is free for the next job's MMAs
+      umma::fence_before_sync();
+      __syncwarp();
+      if (lane == 0) umma::mbar_arrive(&ctl->tempty);
+
+      const Job jb = jobs[j];
+      const WorkItem it = S.items[jb.w];
+      const int wl = (int)(jb.w - W.w0);
+      const __nv_bfloat16 *Ab, *Bb;
+      const int16_t *ea_p, *eb_p;
+      pg_operands<KS, JOB>(S, W, jb, it, Ab, Bb, ea_p, eb_p);
+      const int ea = ea_p[row];
+      if (JOB == 0) {
+        // Y[al][rowY] with rowY = b * ncol + col(G,g); Y2 (f32 pairs) in 16-column
+        // blocks [cb][al][b][16], cb = kofs(G) / 16 + g / 16
+        const int nb = S.nao[it.b], ncol = S.ncol[it.b];
+        const int nrow = nb * ncol;
+        const int rowY = jb.mt * TM + row;
+        const int pA = S.nabf[it.a];
+        if (rowY >= nrow) continue;
+        double *Y = W.scratch + W.y_off[wl];
+        float2 *Y2 = reinterpret_cast<float2 *>(W.scratch + W.y2_off[wl]);
+        int64_t y2row = -1;
+        if (W.y2_on) {
+          const int b = rowY / ncol, col = rowY - b * ncol;
+          const int G = entry_of(S.nbr, it.gbase, it.nG, col);
+          const int g = col - S.nbr[it.gbase + G].aopre;
+          const int cb = S.kofs[it.gbase + G] / 16 + g / 16;
+          y2row = (((int64_t)cb * pA) * nb + b) * 16 + (g & 15);
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int al = jb.nt * NT + c0 + i;
+          if (al >= pA) break;
+          const int e = ea + eb_p[c0 + i] - SH;
+          Y[(int64_t)al * nrow + rowY] = scaled_i64(Wv[i], e);
+          if (y2row >= 0) Y2[y2row + (int64_t)al * nb * 16] = pair_i64(Wv[i], e);
+        }
+      } else {
+        // Sigma_FG blocks: rows (F,f) of atom A, columns (G,g) of atom B
+        const int ncolA = S.ncol[it.a], ncolB = S.ncol[it.b];
+        const int rF = jb.mt * TM + row;
+        if (rF >= ncolA) continue;
+        const int F = entry_of(S.nbr, it.fbase, it.nF, rF);
+        const NbrEntry ef = S.nbr[it.fbase + F];
+        const int nf = S.nao[ef.other], f = rF - ef.aopre;
+        const bool mir = S.sym && it.role == 1;
+        int lastG = -1;
+        bool live = false;
+        int64_t off = -1, moff = -1;
+        int ng = 0, gpre = 0;
+#pragma unroll 1
+        for (int i = 0; i < 32; ++i) {
+          const int cG = jb.nt * NT + c0 + i;
+          if (cG >= ncolB) break;
+          if (cG >= gpre + ng || lastG < 0) {
+            const int G = entry_of(S.nbr, it.gbase, it.nG, cG);
+            const NbrEntry eg = S.nbr[it.gbase + G];
+            lastG = G;
+            ng = S.nao[eg.other];
+            gpre = eg.aopre;
+            const uint32_t m = S.masks[it.mask_off + ((int64_t)G * 4 + 3) * it.nFw + (F >> 5)];
+            live = (m >> (F & 31)) & 1u;
+            off = moff = -1;
+            if (live) {
+              const int n0 = it.n[0] + eg.n[0] - ef.n[0], n1 = it.n[1] + eg.n[1] - ef.n[1],
+                        n2 = it.n[2] + eg.n[2] - ef.n[2];
+              off = dh_find(S.shash, hk_pack(ef.other, eg.other, n0, n1, n2));
+              if (mir) moff = dh_find(S.shash, hk_pack(eg.other, ef.other, -n0, -n1, -n2));
+              if (off < 0 || (mir && moff < 0)) atomicOr(S.err, HFX_DEV_ERR_MISSING);
+            }
+          }
+          if (!live) continue;
+          const int g = cG - gpre;
+          const int e = ea + eb_p[c0 + i] - SH;
+          if (off >= 0) fx_add_scaled(S.acc + 2 * (off + (int64_t)f * ng + g), -Wv[i], e);
+          if (moff >= 0) fx_add_scaled(S.acc + 2 * (moff + (int64_t)g * nf + f), -Wv[i], e);
+        }
+      }
+    }
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tbase, 512);
+}
+
+template <int KS, int JOB>
+cudaError_t launch_pgemm_t(const SplitShared &S, const SplitWave &W, int64_t maxjobs,
+                           cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>(maxjobs, S.nsm > 0 ? S.nsm : 1);
+  if (blocks <= 0) return cudaSuccess;
+  const size_t smem = (size_t)PG_NST * KS * (TM + NT) * TK * 2 + sizeof(PgSmem) + 64;
+  cudaError_t e = cudaFuncSetAttribute(k_pgemm<KS, JOB>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_pgemm<KS, JOB><<<blocks, PG_THREADS, smem, st>>>(S, W);
+  return cudaGetLastError();
+}
+
+}  // namespace split
+
+cudaError_t split_pgemm(const SplitShared &S, const SplitWave &W, int ks, int job,
+                        int64_t maxjobs, cudaStream_t st) {
+  switch (ks * 2 + job) {
+    case 8: return split::launch_pgemm_t<4, 0>(S, W, maxjobs, st);
+    case 9: return split::launch_pgemm_t<4, 1>(S, W, maxjobs, st);
+    case 10: return split::launch_pgemm_t<5, 0>(S, W, maxjobs, st);
+    case 11: return split::launch_pgemm_t<5, 1>(S, W, maxjobs, st);
+    case 12: return split::launch_pgemm_t<6, 0>(S, W, maxjobs, st);
+    case 13: return split::launch_pgemm_t<6, 1>(S, W, maxjobs, st);
+    default: return cudaErrorInvalidValue;
+  }
+}

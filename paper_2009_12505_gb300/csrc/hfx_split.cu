@@ -1,20 +1,17 @@
-// HFX_OZAKI: the Y = V C product and the D_AB piece of Algorithm 3 on the
-// tensor cores, as exact split-precision products (see hfx_ozaki.cu for the
-// digit scheme and the tcgen05 pipeline it shares).
+// HFX_OZAKI: operand slicing and job lists for the Y = V C product and the
+// D_AB piece of Algorithm 3, which run as exact split-precision tcgen05
+// products in hfx_pgemm.cu (hfx_ozaki.cu documents the digit scheme).
 //
 //   Y job  (one per 128 rows (b,G,g) of a work item <A,B>):
 //       Y^T[(b,G,g)][al] = sum_be C_BG[be][b][g] V_AB[al][be]
 //     A operand: C of atom B transposed (rows (b,G,g), K = be), sliced once
 //     per build; B operand: V_AB (rows al, K = be), sliced once per build.
-//     The epilogue stores Y[al][b][(G,g)] in FP64 for the remaining FP64
-//     kernels and the D-stage.
 //   D_AB job (128 rows (F,f) x 64 columns (G,g) of a pair, K chunk <= 640):
 //       Sigma_FG[f][g] -= sum_{al,a} C_AF[al][a][f] P_G[al][a][g]
 //     A operand: C of atom A as rows (F,f), K = (al,a), sliced once per
 //     build; B operand: P of the pair as rows (G,g), K = (al,a), sliced per
-//     wave.  The epilogue keeps only surviving (F,G) blocks and adds them to
-//     the fixed-point Sigma accumulators with integer arithmetic.
-// Tiles without any surviving block are not launched (device-built job list;
+//     wave.
+// Tiles without any surviving block get no job (device-built job list;
 // Sigma accumulation is order-independent, so job order does not matter).
 #include <cuda_bf16.h>
 
@@ -248,221 +245,6 @@ __global__ void k_jobs_v4(SplitShared S, SplitWave W) {
   }
 }
 
-// ------------------------------------------------------------------- GEMM
-__host__ __device__ constexpr uint32_t tmem_cols(int ks) {
-  return (uint32_t)(ks * NT <= 64 ? 64 : ks * NT <= 128 ? 128 : ks * NT <= 256 ? 256 : 512);
-}
-
-template <int KS, int JOB>
-__global__ void __launch_bounds__(128, 1) k_gemm(SplitShared S, SplitWave W) {
-  const int njobs = W.njobs[JOB];
-  if ((int)blockIdx.x >= njobs) return;
-  extern __shared__ __align__(1024) uint8_t smem[];
-  constexpr int A_BYTES = KS * TM * TK * 2;
-  constexpr int B_BYTES = KS * NT * TK * 2;
-  constexpr int STAGE = A_BYTES + B_BYTES;
-  constexpr uint32_t TCOLS = tmem_cols(KS);
-  uint64_t *full = reinterpret_cast<uint64_t *>(smem + NSTAGE * STAGE);
-  uint64_t *empty = full + NSTAGE;
-  uint64_t *done = empty + NSTAGE;
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(done + 1);
-
-  const Job jb = (JOB == 0 ? W.jobs : W.jobs4)[blockIdx.x];
-  const WorkItem it = S.items[jb.w];
-  const int wl = (int)(jb.w - W.w0);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-
-  const __nv_bfloat16 *Ab, *Bb;
-  const int16_t *ea_p, *eb_p;
-  if (JOB == 0) {
-    const int kt = S.ktY[it.b];
-    Ab = S.cy + S.cy_base[it.b] + ((int64_t)jb.mt * kt + jb.k0) * KS * TM * TK;
-    Bb = S.vs + S.vs_base[it.vblk] + ((int64_t)jb.nt * kt + jb.k0) * KS * NT * TK;
-    ea_p = S.cy_e + S.cy_rowpre[it.b] + jb.mt * TM;
-    eb_p = S.vs_e + S.v_rowpre[it.vblk] + jb.nt * NT;
-  } else {
-    const int kt = S.kt4[it.a];
-    Ab = S.c4 + S.c4_base[it.a] + ((int64_t)jb.mt * kt + jb.k0) * KS * TM * TK;
-    Bb = W.ps + W.ps_base[wl] + ((int64_t)jb.nt * kt + jb.k0) * KS * NT * TK;
-    ea_p = S.c4_e + S.c4_rowpre[it.a] + jb.mt * TM;
-    eb_p = W.ps_e + W.p_rowpre[wl] + jb.nt * NT;
-  }
-
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < NSTAGE; ++s) {
-      umma::mbar_init(&full[s], 1);
-      umma::mbar_init(&empty[s], 1);
-    }
-    umma::mbar_init(done, 1);
-    umma::fence_barrier_init();
-  }
-  if (warp == 0) {
-    umma::tmem_alloc(tslot, TCOLS);
-    umma::tmem_relinquish();
-  }
-  umma::fence_before_sync();
-  __syncthreads();
-  umma::fence_after_sync();
-  const uint32_t tbase = *tslot;
-
-  if (threadIdx.x == 0) {
-    constexpr uint32_t idesc = umma::idesc_bf16_f32(TM, NT);
-    auto load = [&](int s, int kt) {
-      umma::mbar_arrive_expect_tx(&full[s], STAGE);
-      umma::bulk_g2s(smem + s * STAGE, Ab + (int64_t)kt * KS * TM * TK, A_BYTES, &full[s]);
-      umma::bulk_g2s(smem + s * STAGE + A_BYTES, Bb + (int64_t)kt * KS * NT * TK, B_BYTES,
-                     &full[s]);
-    };
-    for (int s = 0; s < NSTAGE && s < jb.nk; ++s) load(s, s);
-    bool ok = true;
-    for (int kt = 0; kt < jb.nk; ++kt) {
-      const int s = kt % NSTAGE;
-      const uint32_t ph = (uint32_t)(kt / NSTAGE) & 1u;
-      if (!umma::mbar_wait(&full[s], ph, S.err)) { ok = false; break; }
-      umma::fence_after_sync();
-      const uint32_t a0 = umma::smem_u32(smem + s * STAGE), b0 = a0 + A_BYTES;
-#pragma unroll
-      for (int j = 0; j < TK / 16; ++j)
-#pragma unroll
-        for (int g = 0; g < KS; ++g)
-#pragma unroll
-          for (int i = 0; i <= g; ++i) {
-            const uint64_t ad = umma::smem_desc(a0 + i * TM * TK * 2 + j * 256, 128, 512);
-            const uint64_t bd = umma::smem_desc(b0 + (g - i) * NT * TK * 2 + j * 256, 128, 512);
-            umma::mma_bf16(tbase + g * NT, ad, bd, idesc, (kt | j | i) ? 1u : 0u);
-          }
-      umma::mma_commit(&empty[s]);
-      if (kt + NSTAGE < jb.nk) {
-        if (!umma::mbar_wait(&empty[s], ph, S.err)) { ok = false; break; }
-        load(s, kt + NSTAGE);
-      }
-    }
-    if (ok) umma::mma_commit(done);
-    else asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(umma::smem_u32(done)) : "memory");
-  }
-  __syncwarp();
-  const bool ready = umma::mbar_wait(done, 0, S.err);
-  umma::fence_after_sync();
-
-  const int row = warp * 32 + lane;
-  const int ea = ea_p[row];
-  constexpr int SH = 7 * (KS + 1);
-  if (JOB == 0) {
-    // Y[al][rowY] with rowY = b * ncol + col(G,g); columns al of this tile.
-    // Y2 (f32 pairs) in 16-column blocks: [cb][al][b][16], cb = kofs(G) / 16 + g / 16
-    const int nb = S.nao[it.b], ncol = S.ncol[it.b];
-    const int nrow = nb * ncol;
-    const int rowY = jb.mt * TM + row;
-    const int pA = S.nabf[it.a];
-    double *Y = W.scratch + W.y_off[wl];
-    float2 *Y2 = reinterpret_cast<float2 *>(W.scratch + W.y2_off[wl]);
-    int64_t y2row = -1;
-    if (W.y2_on && rowY < nrow) {
-      const int b = rowY / ncol, col = rowY - b * ncol;
-      const int G = entry_of(S.nbr, it.gbase, it.nG, col);
-      const int g = col - S.nbr[it.gbase + G].aopre;
-      const int cb = S.kofs[it.gbase + G] / 16 + g / 16;
-      y2row = (((int64_t)cb * pA) * nb + b) * 16 + (g & 15);
-    }
-    for (int c0 = 0; c0 < NT; c0 += 32) {
-      long long Wv[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) Wv[i] = 0;
-#pragma unroll
-      for (int g = 0; g < KS; ++g) {
-        float v[32];
-        umma::tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * NT + c0), v);
-        const long long sc = 1ll << (7 * (KS - 1 - g));
-#pragma unroll
-        for (int i = 0; i < 32; ++i) Wv[i] += (long long)__float2int_rn(v[i]) * sc;
-      }
-      if (ready && rowY < nrow) {
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int al = jb.nt * NT + c0 + i;
-          if (al < pA) {
-            const int e = ea + eb_p[c0 + i] - SH;
-            Y[(int64_t)al * nrow + rowY] = scaled_i64(Wv[i], e);
-            if (y2row >= 0) Y2[y2row + (int64_t)al * nb * 16] = pair_i64(Wv[i], e);
-          }
-        }
-      }
-    }
-  } else {
-    // Sigma_FG blocks: rows (F,f) of atom A, columns (G,g) of atom B
-    const int ncolA = S.ncol[it.a], ncolB = S.ncol[it.b];
-    const int rF = jb.mt * TM + row;
-    const bool rvalid = ready && rF < ncolA;
-    const int F = entry_of(S.nbr, it.fbase, it.nF, rvalid ? rF : 0);
-    const NbrEntry ef = S.nbr[it.fbase + F];
-    const int nf = S.nao[ef.other], f = rF - ef.aopre;
-    const bool mir = S.sym && it.role == 1;
-    int lastG = -1;
-    bool live = false;
-    int64_t off = -1, moff = -1;
-    int ng = 0, gpre = 0;
-    for (int c0 = 0; c0 < NT; c0 += 32) {
-      long long Wv[32];
-#pragma unroll
-      for (int i = 0; i < 32; ++i) Wv[i] = 0;
-#pragma unroll
-      for (int g = 0; g < KS; ++g) {
-        float v[32];
-        umma::tmem_ld32(tbase + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * NT + c0), v);
-        const long long sc = 1ll << (7 * (KS - 1 - g));
-#pragma unroll
-        for (int i = 0; i < 32; ++i) Wv[i] += (long long)__float2int_rn(v[i]) * sc;
-      }
-      if (!rvalid) continue;
-#pragma unroll 1
-      for (int i = 0; i < 32; ++i) {
-        const int cG = jb.nt * NT + c0 + i;
-        if (cG >= ncolB) break;
-        if (cG >= gpre + ng || lastG < 0) {
-          const int G = entry_of(S.nbr, it.gbase, it.nG, cG);
-          const NbrEntry eg = S.nbr[it.gbase + G];
-          lastG = G;
-          ng = S.nao[eg.other];
-          gpre = eg.aopre;
-          const uint32_t m = S.masks[it.mask_off + ((int64_t)G * 4 + 3) * it.nFw + (F >> 5)];
-          live = (m >> (F & 31)) & 1u;
-          off = moff = -1;
-          if (live) {
-            const int n0 = it.n[0] + eg.n[0] - ef.n[0], n1 = it.n[1] + eg.n[1] - ef.n[1],
-                      n2 = it.n[2] + eg.n[2] - ef.n[2];
-            off = dh_find(S.shash, hk_pack(ef.other, eg.other, n0, n1, n2));
-            if (mir) moff = dh_find(S.shash, hk_pack(eg.other, ef.other, -n0, -n1, -n2));
-            if (off < 0 || (mir && moff < 0)) atomicOr(S.err, HFX_DEV_ERR_MISSING);
-          }
-        }
-        if (!live) continue;
-        const int g = cG - gpre;
-        const int e = ea + eb_p[c0 + i] - SH;
-        if (off >= 0) fx_add_scaled(S.acc + 2 * (off + (int64_t)f * ng + g), -Wv[i], e);
-        if (moff >= 0) fx_add_scaled(S.acc + 2 * (moff + (int64_t)g * nf + f), -Wv[i], e);
-      }
-    }
-  }
-  umma::fence_before_sync();
-  __syncthreads();
-  if (warp == 0) umma::tmem_dealloc(tbase, TCOLS);
-}
-
-template <int KS, int JOB>
-cudaError_t launch_gemm_t(const SplitShared &S, const SplitWave &W, int64_t maxjobs,
-                          cudaStream_t st) {
-  if (maxjobs <= 0) return cudaSuccess;
-  constexpr int STAGE = KS * (TM + NT) * TK * 2;
-  const size_t need = (size_t)NSTAGE * STAGE + 64;
-  const int limit = 512 / (int)tmem_cols(KS);
-  const size_t smem = std::max(need, (size_t)(233472 / (limit + 1)) + 1024);
-  cudaError_t e = cudaFuncSetAttribute(k_gemm<KS, JOB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
-  if (e != cudaSuccess) return e;
-  k_gemm<KS, JOB><<<(unsigned)maxjobs, 128, smem, st>>>(S, W);
-  return cudaGetLastError();
-}
-
 template <int KS>
 cudaError_t slice_inputs_t(const SplitShared &S, cudaStream_t st) {
   const int64_t ry = S.h_cy_rows, r4 = S.h_c4_rows, rv = S.h_v_rows;
@@ -479,7 +261,7 @@ cudaError_t wave_t(const SplitShared &S, const SplitWave &W, int phase, cudaStre
       k_jobs_y<<<(unsigned)((W.h_ycand + 255) / 256), 256, 0, st>>>(S, W);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_gemm_t<KS, 0>(S, W, W.h_ycand, st);
+    return split_pgemm(S, W, KS, 0, W.h_ycand, st);
   }
   // phase 1: slice P, build D_AB jobs, run them
   if (W.h_prows > 0)
@@ -488,7 +270,7 @@ cudaError_t wave_t(const SplitShared &S, const SplitWave &W, int phase, cudaStre
     k_jobs_v4<<<(unsigned)((W.h_v4cand + 255) / 256), 256, 0, st>>>(S, W);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  return launch_gemm_t<KS, 1>(S, W, W.h_v4jobs_max, st);
+  return split_pgemm(S, W, KS, 1, W.h_v4jobs_max, st);
 }
 
 }  // namespace split

@@ -79,6 +79,7 @@ struct SplitShared {
   unsigned long long *de;          // per (atom, ao) column maximum (bit pattern)
   const int32_t *aoff;             // per atom: first (atom, ao) index
   int64_t h_nd;                    // D blocks
+  int32_t nsm;                     // SMs of the device (persistent grids)
   int64_t h_cy_rows, h_c4_rows, h_v_rows, h_cz_rows;  // host copies of the row totals
 };
 
@@ -122,6 +123,10 @@ struct ZcPlanShape {
 // D_FG / D_FB products of one wave (after phase 0: needs the Y pairs).
 cudaError_t split_zc_run(const SplitShared &S, const SplitWave &W, int ks, const ZcPlanShape &P,
                          int nsm, cudaStream_t st);
+// Y products (job 0) or D_AB products (job 1) of the wave's job list,
+// persistent over at most maxjobs jobs.
+cudaError_t split_pgemm(const SplitShared &S, const SplitWave &W, int ks, int job,
+                        int64_t maxjobs, cudaStream_t st);
 // phase 0: Y jobs; phase 1: P slices and D_AB jobs
 cudaError_t split_wave(const SplitShared &S, const SplitWave &W, int ks, int phase,
                        cudaStream_t st);
