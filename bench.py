@@ -255,6 +255,16 @@ def run_gpu(args):
                 "split_speedup": ms64 / ms,
                 "max_abs_dsigma_split_vs_fp64_Ha": float(abs(sig_split - sig64).max()),
                 "abs_dex_per_atom_Ha": abs(ex_split - ex64) / wl.system.natoms}
+        # two digits per operand (hi*hi + hi*lo + lo*hi): faster, but misses the bar
+        e0.record(stream)
+        exb = ctx.build(THETA, "bf16x3")
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dsb = float(abs(ctx.sigma() - sig64).max())
+        fp64["bf16x3"] = {"build_s": e0.elapsed_time(e1) / 1e3,
+                          "max_abs_dsigma_vs_fp64_Ha": dsb,
+                          "abs_dex_per_atom_Ha": abs(exb - ex64) / wl.system.natoms,
+                          "meets_1e-8_Ha": dsb <= 1e-8}
         ctx.build(THETA, prec, nsl)  # leave the context on the split result
 
     # end to end through the C ABI with host buffers

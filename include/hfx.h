@@ -37,12 +37,18 @@
  *
  * Precision modes (hfx_prec):
  *   HFX_FP64   -- every contraction in FP64 on CUDA cores;
- *   HFX_BF16X3 -- contractions as three BF16 products with FP32 accumulation
- *                 (about FP32 accuracy);
- *   HFX_OZAKI  -- contractions as exact products of nslices BF16 slices per
- *                 operand on the tensor cores, recombined in FP64.
- * Sigma accumulation and E_X are FP64 and deterministic (bitwise run to run)
- * in every mode.
+ *   HFX_BF16X3 -- tensor-core contractions with every operand row split into
+ *                 two balanced 7-bit digits (exact in BF16) under one
+ *                 power-of-two exponent, and only the three leading digit
+ *                 products hi*hi, hi*lo, lo*hi formed (about 13 significant
+ *                 bits; does not meet 1e-8 Ha, kept for comparison);
+ *   HFX_OZAKI  -- the same with nslices digits (4..6) and every digit product
+ *                 of order <= nslices - 1: each order's f32 tensor-core sum is
+ *                 exact, the orders are recombined in int64 (6 digits: about
+ *                 41 significant bits per operand row).
+ * Sigma is accumulated in 128-bit fixed point (integer adds, 2^-64 Ha
+ * resolution) and converted to FP64 once, and E_X is summed from it in a
+ * fixed order, so results are bitwise reproducible run to run in every mode.
  *
  * Ownership.  hfx_set_* copy the caller's data (host pointers) or read device
  * pointers on the context's stream before returning; the caller may free or
@@ -127,7 +133,8 @@ hfx_status hfx_clear(hfx_ctx *ctx, char which);
  * the staged C((VC)D) contractions of Algorithm 3, then E_X).
  *   theta    screening threshold (>= 0; 0 keeps every term with non-zero blocks)
  *   prec     contraction precision (see above)
- *   nslices  BF16 slices per operand for HFX_OZAKI (2..8); ignored otherwise
+ *   nslices  digits per operand: HFX_OZAKI 4..6 (0 = 6), HFX_BF16X3 0 or 2,
+ *            HFX_FP64 ignored
  *   ex_out   receives E_X in Ha (host pointer), may be NULL
  * Errors: HFX_E_STATE (no C, V or D set), HFX_E_ARG, HFX_E_NOMEM, HFX_E_CUDA,
  *         HFX_E_TIMEOUT.
@@ -211,7 +218,7 @@ typedef struct {
   double kernel_flops[8];   /* multiply-adds x 2 issued by each kernel */
   int64_t n_launches;       /* kernels this build launched */
   int32_t mirror;           /* 1: V and D were exactly Hermitian and the mirror pieces were used */
-  int32_t nslices;          /* digits per operand in HFX_OZAKI mode, else 0 */
+  int32_t nslices;          /* digits per operand in the split modes, else 0 */
   double kernel_tensor_flops[8]; /* bf16 tensor-core flops issued per kernel (HFX_OZAKI) */
 } hfx_stats_v1;
 
@@ -266,6 +273,18 @@ hfx_status hfx_term_noalloc(int32_t nabf_a, int32_t nabf_b, int32_t nao_i, int32
  */
 hfx_status hfx_selftest_ozaki(int32_t M, int32_t N, int32_t K, const double *A, const double *B,
                               double *C, int32_t nslices);
+
+/*
+ * Failure-detection self-test (no counterpart in the paper): launches one
+ * thread that waits on a shared-memory mbarrier that nothing ever arrives at,
+ * through the same bounded wait every tensor-core kernel uses, with a limit
+ * of limit_cycles SM clocks (1 .. 2e9).  The wait expires, the kernel records
+ * the timeout in its error word and returns normally, and so does this call:
+ * HFX_E_TIMEOUT is the expected result, with *waited_cycles (if not NULL) set
+ * to the clocks the kernel spent in the wait.  The CUDA context stays usable.
+ * Errors: HFX_E_ARG (limit out of range), HFX_E_CUDA.
+ */
+hfx_status hfx_selftest_timeout(int64_t limit_cycles, int64_t *waited_cycles);
 
 /* Message for the last failing call on ctx (never NULL; "" when none). */
 const char *hfx_last_error(const hfx_ctx *ctx);

@@ -593,7 +593,7 @@ hfx_status dz_prepare_meta(hfx_ctx *ctx, int ks) {
     aoff[x + 1] = aoff[x] + ctx->nao[x];
     if (ctx->nao[x] > 16) kbmax = 32;
     if (ctx->nao[x] > 32)
-      return fail(ctx, HFX_E_ARG, "HFX_OZAKI supports at most 32 NAOs per atom");
+      return fail(ctx, HFX_E_ARG, "the split modes support at most 32 NAOs per atom");
     naomax = std::max(naomax, ctx->nao[x]);
     naomin = std::min(naomin, ctx->nao[x]);
   }
@@ -869,11 +869,18 @@ hfx_status hfx_clear(hfx_ctx *ctx, char which) {
 hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices, double *ex_out) {
   if (!ctx) return HFX_E_ARG;
   if (!(theta >= 0.0) || !std::isfinite(theta)) return fail(ctx, HFX_E_ARG, "theta must be >= 0");
-  const bool split = prec == HFX_OZAKI;
+  // HFX_BF16X3 is the split path with two digits per operand: of the digit
+  // products only hi*hi, hi*lo and lo*hi (orders 0 and 1) are formed
+  const bool split = prec == HFX_OZAKI || prec == HFX_BF16X3;
   if (prec != HFX_FP64 && !split)
-    return fail(ctx, HFX_E_ARG, "precision mode not available in this build");
-  if (split && nslices == 0) nslices = 6;
-  if (split && (nslices < 4 || nslices > 6))
+    return fail(ctx, HFX_E_ARG, "unknown precision mode");
+  if (prec == HFX_BF16X3) {
+    if (nslices != 0 && nslices != 2)
+      return fail(ctx, HFX_E_ARG, "HFX_BF16X3 uses two digit slices (pass 0 or 2)");
+    nslices = 2;
+  }
+  if (prec == HFX_OZAKI && nslices == 0) nslices = 6;
+  if (prec == HFX_OZAKI && (nslices < 4 || nslices > 6))
     return fail(ctx, HFX_E_ARG, "HFX_OZAKI takes 4 to 6 digit slices");
   for (int k = 0; k < 3; ++k)
     if (ctx->K[k].map.empty())

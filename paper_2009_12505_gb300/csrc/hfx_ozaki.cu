@@ -305,3 +305,46 @@ extern "C" hfx_status hfx_selftest_ozaki(int32_t M, int32_t N, int32_t K, const 
     default: return HFX_E_ARG;
   }
 }
+
+namespace oz {
+
+// One thread waits, with the kernels' bounded wait, on an mbarrier nothing
+// arrives at; the expiry is recorded in *err and the kernel returns.
+__global__ void k_wait_nothing(long long limit, unsigned *err, long long *waited) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  umma::mbar_init(&bar, 1);
+  umma::fence_barrier_init();
+  const long long t0 = clock64();
+  umma::mbar_wait(&bar, 0, err, limit);
+  *waited = clock64() - t0;
+}
+
+}  // namespace oz
+
+extern "C" hfx_status hfx_selftest_timeout(int64_t limit_cycles, int64_t *waited_cycles) {
+  if (limit_cycles < 1 || limit_cycles > 2000000000ll) return HFX_E_ARG;
+  unsigned *d_err = nullptr;
+  long long *d_w = nullptr;
+  if (cudaMalloc((void **)&d_err, sizeof(unsigned)) != cudaSuccess) return HFX_E_CUDA;
+  if (cudaMalloc((void **)&d_w, sizeof(long long)) != cudaSuccess) {
+    cudaFree(d_err);
+    return HFX_E_CUDA;
+  }
+  hfx_status st = HFX_OK;
+  unsigned herr = 0;
+  long long hw = 0;
+  if (cudaMemset(d_err, 0, sizeof(unsigned)) != cudaSuccess) st = HFX_E_CUDA;
+  if (st == HFX_OK) {
+    oz::k_wait_nothing<<<1, 32>>>(limit_cycles, d_err, d_w);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(&herr, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&hw, d_w, sizeof(long long), cudaMemcpyDeviceToHost) != cudaSuccess)
+      st = HFX_E_CUDA;
+  }
+  cudaFree(d_err);
+  cudaFree(d_w);
+  if (st != HFX_OK) return st;
+  if (waited_cycles) *waited_cycles = hw;
+  return (herr & HFX_DEV_ERR_TIMEOUT) ? HFX_E_TIMEOUT : HFX_OK;
+}

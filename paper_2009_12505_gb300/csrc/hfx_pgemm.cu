@@ -309,6 +309,8 @@ cudaError_t launch_pgemm_t(const SplitShared &S, const SplitWave &W, int64_t max
 cudaError_t split_pgemm(const SplitShared &S, const SplitWave &W, int ks, int job,
                         int64_t maxjobs, cudaStream_t st) {
   switch (ks * 2 + job) {
+    case 4: return split::launch_pgemm_t<2, 0>(S, W, maxjobs, st);
+    case 5: return split::launch_pgemm_t<2, 1>(S, W, maxjobs, st);
     case 8: return split::launch_pgemm_t<4, 0>(S, W, maxjobs, st);
     case 9: return split::launch_pgemm_t<4, 1>(S, W, maxjobs, st);
     case 10: return split::launch_pgemm_t<5, 0>(S, W, maxjobs, st);

@@ -277,6 +277,7 @@ cudaError_t wave_t(const SplitShared &S, const SplitWave &W, int phase, cudaStre
 
 cudaError_t split_slice_inputs(const SplitShared &S, int ks, cudaStream_t st) {
   switch (ks) {
+    case 2: return split::slice_inputs_t<2>(S, st);
     case 4: return split::slice_inputs_t<4>(S, st);
     case 5: return split::slice_inputs_t<5>(S, st);
     case 6: return split::slice_inputs_t<6>(S, st);
@@ -287,6 +288,7 @@ cudaError_t split_slice_inputs(const SplitShared &S, int ks, cudaStream_t st) {
 cudaError_t split_wave(const SplitShared &S, const SplitWave &W, int ks, int phase,
                        cudaStream_t st) {
   switch (ks) {
+    case 2: return split::wave_t<2>(S, W, phase, st);
     case 4: return split::wave_t<4>(S, W, phase, st);
     case 5: return split::wave_t<5>(S, W, phase, st);
     case 6: return split::wave_t<6>(S, W, phase, st);

@@ -782,6 +782,7 @@ cudaError_t split_zc_plan(const SplitShared &S, const SplitWave &W, int fill, cu
 cudaError_t split_zc_run(const SplitShared &S, const SplitWave &W, int ks, const ZcPlanShape &P,
                          int nsm, cudaStream_t st) {
   switch (ks) {
+    case 2: return split::zc_run_t<2>(S, W, P, nsm, st);
     case 4: return split::zc_run_t<4>(S, W, P, nsm, st);
     case 5: return split::zc_run_t<5>(S, W, P, nsm, st);
     case 6: return split::zc_run_t<6>(S, W, P, nsm, st);
@@ -791,6 +792,7 @@ cudaError_t split_zc_run(const SplitShared &S, const SplitWave &W, int ks, const
 
 cudaError_t split_dz_prepare(const SplitShared &S, int ks, cudaStream_t st) {
   switch (ks) {
+    case 2: return split::dz_prepare_t<2>(S, st);
     case 4: return split::dz_prepare_t<4>(S, st);
     case 5: return split::dz_prepare_t<5>(S, st);
     case 6: return split::dz_prepare_t<6>(S, st);
@@ -800,6 +802,7 @@ cudaError_t split_dz_prepare(const SplitShared &S, int ks, cudaStream_t st) {
 
 cudaError_t split_slice_cz(const SplitShared &S, int ks, cudaStream_t st) {
   switch (ks) {
+    case 2: return split::slice_cz_t<2>(S, st);
     case 4: return split::slice_cz_t<4>(S, st);
     case 5: return split::slice_cz_t<5>(S, st);
     case 6: return split::slice_cz_t<6>(S, st);

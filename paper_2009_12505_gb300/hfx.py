@@ -78,6 +78,7 @@ def load_library():
             "hfx_get_H_fixed": (S, [P, P, ctypes.c_int]),
             "hfx_set_H_fixed": (S, [P, P, ctypes.c_int, P]),
             "hfx_selftest_ozaki": (S, [i32, i32, i32, P, P, P, i32]),
+            "hfx_selftest_timeout": (S, [i64, P]),
             "hfx_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
@@ -109,6 +110,15 @@ def selftest_ozaki(A, B, nslices: int):
     if rc != 0:
         raise HfxError(rc, "hfx_selftest_ozaki failed")
     return C
+
+
+def selftest_timeout(limit_cycles: int):
+    """Run the bounded-wait expiry self-test; returns (status, cycles waited).
+    HFX_E_TIMEOUT (6) is the expected status."""
+    lib = load_library()
+    w = ctypes.c_int64(0)
+    rc = lib.hfx_selftest_timeout(int(limit_cycles), ctypes.byref(w))
+    return int(rc), int(w.value)
 
 
 def term_noalloc(cA, V, cB, D, out, stream=None):
