@@ -219,7 +219,9 @@ typedef struct {
   int64_t n_launches;       /* kernels this build launched */
   int32_t mirror;           /* 1: V and D were exactly Hermitian and the mirror pieces were used */
   int32_t nslices;          /* digits per operand in the split modes, else 0 */
-  double kernel_tensor_flops[8]; /* bf16 tensor-core flops issued per kernel (HFX_OZAKI) */
+  double kernel_tensor_flops[8]; /* bf16 tensor-core flops issued per kernel (split modes) */
+  double canonical_flops_piece[4]; /* canonical_flops split by piece (T and Ht stages) ... */
+  double canonical_flops_y;        /* ... and the Y = V C part; the five sum to canonical_flops */
 } hfx_stats_v1;
 
 hfx_status hfx_stats(const hfx_ctx *ctx, void *stats);

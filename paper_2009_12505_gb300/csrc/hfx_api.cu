@@ -740,7 +740,7 @@ hfx_status hfx_create(const double lattice[9], int32_t natoms, const double *pos
   if (ctx->d_nao.reserve(natoms) != cudaSuccess || ctx->d_nabf.reserve(natoms) != cudaSuccess ||
       ctx->d_err.reserve(1) != cudaSuccess || ctx->d_counters.reserve(8) != cudaSuccess ||
       ctx->d_ex.reserve(1) != cudaSuccess || ctx->d_collect.reserve(1) != cudaSuccess ||
-      ctx->d_counters.reserve(16) != cudaSuccess)
+      ctx->d_counters.reserve(24) != cudaSuccess)
     s = HFX_E_NOMEM;
   if (s == HFX_OK &&
       (cudaMemcpy(ctx->d_nao.p, ctx->nao.data(), sizeof(int32_t) * natoms,
@@ -923,14 +923,14 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
   CK(ctx->d_wf.reserve(ctx->nwf));
   if (ctx->stab_cap == 0)
     ctx->stab_cap = pow2_at_least(64 * (uint64_t)ctx->K[0].keys.size() + 1024);
-  unsigned long long counters[16] = {0};
+  unsigned long long counters[24] = {0};
   unsigned herr = 0;
   for (int attempt = 0;; ++attempt) {
     CK(ctx->d_stab.reserve(ctx->stab_cap));
     CK(cudaMemsetAsync(ctx->d_stab.p, 0xFF, sizeof(unsigned long long) * ctx->stab_cap, st));
     CK(cudaMemsetAsync(ctx->d_wg.p, 0, ctx->nwg ? ctx->nwg : 1, st));
     CK(cudaMemsetAsync(ctx->d_wf.p, 0, sizeof(uint32_t) * (ctx->nwf ? ctx->nwf : 1), st));
-    CK(cudaMemsetAsync(ctx->d_counters.p, 0, sizeof(unsigned long long) * 16, st));
+    CK(cudaMemsetAsync(ctx->d_counters.p, 0, sizeof(unsigned long long) * 24, st));
     CK(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(unsigned), st));
     ScreenArgs a{};
     a.items = ctx->d_items.p;
@@ -1284,6 +1284,8 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
   S.n_active_abg = (int64_t)counters[4];
   for (int v = 0; v < 4; ++v) S.survivors[v] = (int64_t)counters[v];
   S.canonical_flops = 2.0 * (double)counters[5];
+  for (int v = 0; v < 4; ++v) S.canonical_flops_piece[v] = 2.0 * (double)counters[16 + v];
+  S.canonical_flops_y = 2.0 * (double)counters[20];
   double macs = 0;
   for (int q = 0; q < 7; ++q) macs += (double)kmacs[q];
   S.executed_flops = 2.0 * macs;

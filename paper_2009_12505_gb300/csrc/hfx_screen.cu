@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A) {
   const int pA = A.nabf[it.a];
   const int na = A.nao[it.a], nb = A.nao[it.b], ng = A.nao[gt];
   unsigned long long cnt[4] = {0, 0, 0, 0};
-  unsigned long long macs = 0;
+  unsigned long long macs = 0, pm[4] = {0, 0, 0, 0};
   unsigned any = 0;
   uint32_t *mrow = A.masks + it.mask_off + (int64_t)g * 4 * it.nFw;
   for (int f0 = 0; f0 < it.nF; f0 += 32) {
@@ -126,10 +126,10 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A) {
       const unsigned fb = (b1 ? 1u : 0u) | (b2 ? 2u : 0u) | (b3 ? 4u : 0u) | (b4 ? 8u : 0u);
       if (fb) atomicOr(&A.wf_flags[it.wf_off + f], fb);
       // Algorithm 3 multiply-adds per surviving term (T stage + Ht stage)
-      if (b1) macs += (unsigned long long)pA * nb * nf * (ng + na);
-      if (b2) macs += (unsigned long long)pA * nf * ng * (nb + na);
-      if (b3) macs += (unsigned long long)pA * na * nb * (ng + nf);
-      if (b4) macs += (unsigned long long)pA * na * ng * (nb + nf);
+      if (b1) pm[0] += (unsigned long long)pA * nb * nf * (ng + na);
+      if (b2) pm[1] += (unsigned long long)pA * nf * ng * (nb + na);
+      if (b3) pm[2] += (unsigned long long)pA * na * nb * (ng + nf);
+      if (b4) pm[3] += (unsigned long long)pA * na * ng * (nb + nf);
       if (b3) sig_insert(A.sig_keys, A.sig_mask,
                          hk_pack(ft, it.b, it.n[0] - mF0, it.n[1] - mF1, it.n[2] - mF2),
                          A.sig_count, A.sig_limit, A.err);
@@ -137,7 +137,11 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A) {
                          A.sig_count, A.sig_limit, A.err);
     }
   }
-  for (int o = 16; o; o >>= 1) macs += __shfl_xor_sync(0xffffffffu, macs, o);
+#pragma unroll
+  for (int v = 0; v < 4; ++v) {
+    for (int o = 16; o; o >>= 1) pm[v] += __shfl_xor_sync(0xffffffffu, pm[v], o);
+    macs += pm[v];
+  }
   if (lane == 0) {
     A.wg_flags[it.wg_off + g] = (uint8_t)any;
     if (any & 1u) sig_insert(A.sig_keys, A.sig_mask, hk_pack(it.a, it.b, it.n[0], it.n[1], it.n[2]),
@@ -149,9 +153,13 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A) {
     if (any) {
       atomicAdd(&A.counters[4], 1ull);
       const int pB = A.nabf[it.b];
-      macs += (unsigned long long)pA * pB * nb * ng;  // Y = V C_BG once per active (A,B,G)
+      const unsigned long long ym = (unsigned long long)pA * pB * nb * ng;
+      macs += ym;  // Y = V C_BG once per active (A,B,G)
+      atomicAdd(&A.counters[20], ym);
     }
     if (macs) atomicAdd(&A.counters[5], macs);
+    for (int v = 0; v < 4; ++v)
+      if (pm[v]) atomicAdd(&A.counters[16 + v], pm[v]);
   }
 }
 

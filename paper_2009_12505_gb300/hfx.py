@@ -38,7 +38,8 @@ class Stats(ctypes.Structure):
                 ("n_waves", ctypes.c_int64), ("scratch_bytes", ctypes.c_int64),
                 ("kernel_ms", ctypes.c_double * 8), ("kernel_flops", ctypes.c_double * 8),
                 ("n_launches", ctypes.c_int64), ("mirror", ctypes.c_int32),
-                ("nslices", ctypes.c_int32), ("kernel_tensor_flops", ctypes.c_double * 8)]
+                ("nslices", ctypes.c_int32), ("kernel_tensor_flops", ctypes.c_double * 8),
+                ("canonical_flops_piece", ctypes.c_double * 4), ("canonical_flops_y", ctypes.c_double)]
 
 KERNELS = ["screen", "Y", "Dstage", "Q", "v1_DFG", "v3_DAG", "v2_DFB", "v4_DAB"]
 
@@ -312,4 +313,6 @@ class Context:
         d["kernel_ms"] = dict(zip(KERNELS, list(s.kernel_ms)))
         d["kernel_flops"] = dict(zip(KERNELS, list(s.kernel_flops)))
         d["kernel_tensor_flops"] = dict(zip(KERNELS, list(s.kernel_tensor_flops)))
+        d["canonical_flops_piece"] = list(s.canonical_flops_piece)
+        d["canonical_flops_y"] = s.canonical_flops_y
         return d
