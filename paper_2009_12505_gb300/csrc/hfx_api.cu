@@ -1073,7 +1073,11 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         const int64_t pA = ctx->nabf[it.a], na = ctx->nao[it.a], nb = ctx->nao[it.b];
         // every region starts on a 256-byte boundary (bulk copies read Y2)
         auto pad = [](int64_t x) { return (x + 31) / 32 * 32; };
-        const int64_t ysz = pad(pA * nb * ctx->aotot[it.b]);
+        // FP64 Y: with the tensor D_FG / D_FB products and mirror pieces only the
+        // D-stage of items whose D_AB piece runs here reads it
+        const bool y64 = !(split && zjobs && ctx->sym) ||
+                         (it.dab >= 0 && !(ctx->sym && it.role == 2));
+        const int64_t ysz = y64 ? pad(pA * nb * ctx->aotot[it.b]) : 0;
         const int64_t psz = it.dab >= 0 ? pad(pA * na * ctx->aotot[it.b]) : 0;
         // T3 only for the D_AG piece without mirrors; Q only for the FP64 D_FB piece
         const int64_t tsz = ctx->sym ? 0 : pad((int64_t)it.nG * pA * na * nb);
@@ -1178,6 +1182,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         SW.v4_candpre = ctx->d_wave_split.p + 2 * (nw + 1) + nw;
         SW.y2_off = ctx->d_waveoffs.p + 4 * nw;
         SW.y2_on = zjobs ? 1 : 0;
+        SW.y64_mode = (zjobs && ctx->sym) ? 2 : 1;
         SW.ps = ctx->d_ps.p;
         SW.ps_e = ctx->d_ps_e.p;
         SW.jobs = ctx->d_jobs.p;

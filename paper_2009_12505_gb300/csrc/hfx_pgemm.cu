@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         if (rowY >= nrow) continue;
         double *Y = W.scratch + W.y_off[wl];
         float2 *Y2 = reinterpret_cast<float2 *>(W.scratch + W.y2_off[wl]);
+        const bool need64 = W.y64_mode == 1 || (it.dab >= 0 && !(S.sym && it.role == 2));
         int64_t y2row = -1;
         if (W.y2_on) {
           const int b = rowY / ncol, col = rowY - b * ncol;
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
           const int al = jb.nt * NT + c0 + i;
           if (al >= pA) break;
           const int e = ea + eb_p[c0 + i] - SH;
-          Y[(int64_t)al * nrow + rowY] = scaled_i64(Wv[i], e);
+          if (need64) Y[(int64_t)al * nrow + rowY] = scaled_i64(Wv[i], e);
           if (y2row >= 0) Y2[y2row + (int64_t)al * nb * 16] = pair_i64(Wv[i], e);
         }
       } else {

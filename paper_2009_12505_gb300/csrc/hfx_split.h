@@ -102,6 +102,9 @@ struct SplitWave {
   // D_FG / D_FB product epilogues; written only when y2_on (the region exists)
   const int64_t *y2_off;
   int32_t y2_on;
+  // FP64 Y: 1 = every item; 2 = only items whose D_AB piece runs here (the
+  // D-stage is then its only reader)
+  int32_t y64_mode;
   // D_FG and D_FB products: job list and F entries
   ZcJob *zc_jobs;
   ZcEnt *zc_ents;

@@ -608,15 +608,24 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
 #pragma unroll
         for (int c = 0; c < 16; ++c) Wv[c] = 0;
         if (hb >= 0) {
+          // the digit-order groups, three loads in flight per wait
+          const uint32_t ta = tbase + (uint32_t)(tb * 256) + ((uint32_t)(q4 * 32) << 16) +
+                              (uint32_t)(hf * 16);
 #pragma unroll
-          for (int g = 0; g < KS; ++g) {
-            float v[16];
-            umma::tmem_ld16(tbase + (uint32_t)(tb * 256) + ((uint32_t)(q4 * 32) << 16) +
-                                (uint32_t)(g * ZC_COLS + hf * 16),
-                            v);
-            const long long sc = 1ll << (7 * (KS - 1 - g));
+          for (int g0 = 0; g0 < KS; g0 += 3) {
+            uint32_t r[3][16];
 #pragma unroll
-            for (int c = 0; c < 16; ++c) Wv[c] += (long long)__float2int_rn(v[c]) * sc;
+            for (int u = 0; u < 3; ++u)
+              if (g0 + u < KS) umma::tmem_ld16_nowait(ta + (uint32_t)((g0 + u) * ZC_COLS), r[u]);
+            umma::tmem_wait_ld();
+#pragma unroll
+            for (int u = 0; u < 3; ++u) {
+              if (g0 + u >= KS) break;
+              const int sh = 7 * (KS - 1 - g0 - u);
+#pragma unroll
+              for (int c = 0; c < 16; ++c)
+                Wv[c] += (long long)__float2int_rn(__uint_as_float(r[u][c])) * (1ll << sh);
+            }
           }
         }
         umma::fence_before_sync();
@@ -639,17 +648,30 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
           for (int c = 0; c < 16; ++c)
             z[c] = c < cend ? pair_i64(Wv[c], eA + ecol[c] - SH) : make_float2(0.f, 0.f);
           float2 *rr = red + ((int64_t)hf * 128 + row) * rs;
-          for (int o0 = 0; o0 < no; o0 += 4) {
+          const int cs = piece == 1 ? 1 : 16;
+          // one output: out o = sum_c z[c] y[c cs]
+          auto one = [&](int o) {
+            const float2 *y = piece == 1 ? yrow(c0 >> 4) + o * 16 : yrow(o >> 4) + c0 * 16 + (o & 15);
+            float sh = 0.f, sl = 0.f;
+#pragma unroll
+            for (int c = 0; c < 16; ++c) {
+              if (c >= cend) break;
+              df_mac(sh, sl, z[c], y[c * cs]);
+            }
+            rr[o] = make_float2(sh, sl);
+          };
+          const int no4 = no & ~3;
+          for (int o = no4; o < no; ++o) one(o);
+          for (int o0 = 0; o0 < no4; o0 += 4) {
             float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
             const float2 *yp[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const int o = min(o0 + u, no - 1);
+              const int o = o0 + u;
               // piece 1: out b = o, Y[al][b][G, g = c0 + c]; piece 2: out g = o,
               // Y[al][b = c0 + c][G, g]
               yp[u] = piece == 1 ? yrow(c0 >> 4) + o * 16 : yrow(o >> 4) + c0 * 16 + (o & 15);
             }
-            const int cs = piece == 1 ? 1 : 16;
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
               if (c >= cend) break;
@@ -657,8 +679,7 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
               for (int u = 0; u < 4; ++u) df_mac(sh[u], sl[u], z[c], yp[u][c * cs]);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
-              if (o0 + u < no) rr[o0 + u] = make_float2(sh[u], sl[u]);
+            for (int u = 0; u < 4; ++u) rr[o0 + u] = make_float2(sh[u], sl[u]);
           }
         }
         __syncwarp();
