@@ -196,6 +196,18 @@ hfx_status hfx_get_H_all(const hfx_ctx *ctx, double *out, int on_device);
  */
 hfx_status hfx_grad(hfx_ctx *ctx, double *dC, double *dV);
 
+/*
+ * Build many independent cells (contexts), cell c with theta thetas[c]: the
+ * same as hfx_build on each context in order, on each context's own stream,
+ * with ex_out[c] (if ex_out is not NULL) receiving cell c's E_X.  The cells
+ * share nothing; results are bitwise those of separate hfx_build calls.
+ * Errors: HFX_E_ARG (NULL arrays, ncells < 0), else the first failing cell's
+ * status, with its message in that cell's hfx_last_error; cells after it are
+ * not built.
+ */
+hfx_status hfx_build_batch(hfx_ctx **cells, int32_t ncells, const double *thetas, hfx_prec prec,
+                           int32_t nslices, double *ex_out);
+
 /* Statistics of the last build (layout: struct hfx_stats_v1 below). */
 typedef struct {
   int32_t version;          /* 1 */

@@ -6,7 +6,7 @@ There is no CPU fallback: loading fails loudly if the library cannot be built
 or loaded.
 """
 from .hfx import (HFX_BF16X3, HFX_FP64, HFX_OZAKI, Context, ExchangeEnergy, HfxError,
-                  build_library, load_library)
+                  build_batch, build_library, load_library)
 
-__all__ = ["Context", "ExchangeEnergy", "HfxError", "HFX_FP64", "HFX_BF16X3", "HFX_OZAKI", "build_library",
-           "load_library"]
+__all__ = ["Context", "ExchangeEnergy", "HfxError", "HFX_FP64", "HFX_BF16X3", "HFX_OZAKI", "build_batch",
+           "build_library", "load_library"]

@@ -1325,6 +1325,19 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
   return HFX_OK;
 }
 
+hfx_status hfx_build_batch(hfx_ctx **cells, int32_t ncells, const double *thetas, hfx_prec prec,
+                           int32_t nslices, double *ex_out) {
+  if (ncells < 0 || (ncells > 0 && (!cells || !thetas))) return HFX_E_ARG;
+  for (int32_t c = 0; c < ncells; ++c) {
+    if (!cells[c]) return HFX_E_ARG;
+    double ex = 0.0;
+    const hfx_status s = hfx_build(cells[c], thetas[c], prec, nslices, &ex);
+    if (s != HFX_OK) return s;
+    if (ex_out) ex_out[c] = ex;
+  }
+  return HFX_OK;
+}
+
 hfx_status hfx_set_shard(hfx_ctx *ctx, const int32_t *owner, int32_t rank) {
   if (!ctx) return HFX_E_ARG;
   if (!owner) {

@@ -80,6 +80,7 @@ def load_library():
             "hfx_set_H_fixed": (S, [P, P, ctypes.c_int, P]),
             "hfx_selftest_ozaki": (S, [i32, i32, i32, P, P, P, i32]),
             "hfx_selftest_timeout": (S, [i64, P]),
+            "hfx_build_batch": (S, [P, i32, P, ctypes.c_int, i32, P]),
             "hfx_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
@@ -111,6 +112,20 @@ def selftest_ozaki(A, B, nslices: int):
     if rc != 0:
         raise HfxError(rc, "hfx_selftest_ozaki failed")
     return C
+
+
+def build_batch(contexts, thetas, prec: str = "ozaki", nslices: int = 0):
+    """hfx_build_batch over Context objects; returns the E_X of every cell."""
+    lib = load_library()
+    n = len(contexts)
+    hs = (ctypes.c_void_p * max(n, 1))(*[c._h.value for c in contexts])
+    th = np.ascontiguousarray(thetas, np.float64)
+    ex = np.zeros(max(n, 1), np.float64)
+    rc = lib.hfx_build_batch(hs, n, _p(th), _PREC[prec], int(nslices), _p(ex))
+    if rc != 0:
+        msgs = [lib.hfx_last_error(c._h).decode() for c in contexts]
+        raise HfxError(rc, "; ".join(m for m in msgs if m) or "hfx_build_batch failed")
+    return ex[:n]
 
 
 def selftest_timeout(limit_cycles: int):

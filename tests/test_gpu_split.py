@@ -130,3 +130,19 @@ def test_split_si64_bench_config_sampled():
     print(f"si64: max|Sigma_split - Sigma_fp64| = {d:.3e}")
     assert d <= TOL
     assert abs(g["ex"] - f["ex"]) <= TOL * wl.system.natoms
+
+
+def test_build_batch_equals_separate_builds():
+    """hfx_build_batch over two unrelated cells with different thresholds gives
+    bitwise the separate builds' Sigma and E_X."""
+    import paper_2009_12505_gb300 as hfx
+    cells = [(synth.si_shrunk(), 1e-2), (synth.ab_shrunk(), 1e-3)]
+    ctxs, sep = [], []
+    for wl, th in cells:
+        c, g = gpu_build(wl, th, "ozaki", 6)
+        sep.append(g)
+        ctxs.append(c)
+    ex = hfx.build_batch(ctxs, [th for _, th in cells], "ozaki", 6)
+    for c, g, e in zip(ctxs, sep, ex):
+        np.testing.assert_array_equal(c.sigma(), g["data"])
+        assert e == g["ex"]
