@@ -1145,8 +1145,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         for (size_t q = 0; q < nw; ++q) {
           const WorkItem &it = ctx->items[w0 + q];
           const int64_t ntv = (ctx->nabf[it.a] + 63) / 64;
-          const int64_t mty = ((int64_t)ctx->nao[it.b] * ctx->aotot[it.b] + 127) / 128;
-          ycand[q + 1] = ycand[q] + mty * ntv;
+          (void)ntv;
           const bool has = it.dab >= 0 && !(ctx->sym && it.role == 2);
           const int64_t ntp = (ctx->aotot[it.b] + 63) / 64, mt4 = (ctx->aotot[it.a] + 127) / 128;
           prow[q + 1] = prow[q] + (has ? ntp * 64 : 0);
@@ -1157,11 +1156,25 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
             v4max += mt4 * ntp * ((ctx->kt4[it.a] + 19) / 20);
           }
         }
+        // Y candidates with the items grouped by atom B (stable), so that Y jobs
+        // running side by side share C_B digit tiles in L2
+        std::vector<int64_t> yperm(nw);
+        for (size_t q = 0; q < nw; ++q) yperm[q] = (int64_t)q;
+        std::stable_sort(yperm.begin(), yperm.end(), [&](int64_t x, int64_t y) {
+          return ctx->items[w0 + x].b < ctx->items[w0 + y].b;
+        });
+        for (size_t k = 0; k < nw; ++k) {
+          const WorkItem &it = ctx->items[w0 + yperm[k]];
+          const int64_t ntv = (ctx->nabf[it.a] + 63) / 64;
+          const int64_t mty = ((int64_t)ctx->nao[it.b] * ctx->aotot[it.b] + 127) / 128;
+          ycand[k + 1] = ycand[k] + mty * ntv;
+        }
         std::vector<int64_t> wm;
         wm.insert(wm.end(), prow.begin(), prow.end());
         wm.insert(wm.end(), psb.begin(), psb.end());
         wm.insert(wm.end(), ycand.begin(), ycand.end());
         wm.insert(wm.end(), v4cand.begin(), v4cand.end());
+        wm.insert(wm.end(), yperm.begin(), yperm.end());
         CK(ctx->d_wave_split.reserve(wm.size()));
         CK(cudaMemcpyAsync(ctx->d_wave_split.p, wm.data(), sizeof(int64_t) * wm.size(),
                            cudaMemcpyHostToDevice, st));
@@ -1180,6 +1193,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         SW.ps_base = ctx->d_wave_split.p + (nw + 1);
         SW.y_candpre = ctx->d_wave_split.p + (nw + 1) + nw;
         SW.v4_candpre = ctx->d_wave_split.p + 2 * (nw + 1) + nw;
+        SW.y_perm = ctx->d_wave_split.p + 3 * (nw + 1) + nw;
         SW.y2_off = ctx->d_waveoffs.p + 4 * nw;
         SW.y2_on = zjobs ? 1 : 0;
         SW.y64_mode = (zjobs && ctx->sym) ? 2 : 1;

@@ -142,8 +142,9 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
       uint32_t idesc[4];
 #pragma unroll
       for (int n = 1; n <= 4; ++n) idesc[n - 1] = umma::idesc_bf16_f32(TM, NT * n);
-      for (int j = blockIdx.x; j < njobs && !*abort_f; j += gridDim.x, ++hand) {
+      for (int j = blockIdx.x; j < njobs && !*abort_f; j += gridDim.x) {
         const Job jb = jobs[j];
+        if (jb.nk == 0) continue;  // an empty job (a skipped candidate tile)
         if (hand >= 1 &&
             !umma::mbar_wait(&ctl->tempty, (uint32_t)((hand - 1) & 1), S.err, PG_WAIT)) {
           *abort_f = 1;
@@ -177,6 +178,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         }
         if (!ok) { *abort_f = 1; break; }
         umma::mma_commit(&ctl->tfull);
+        ++hand;
       }
       umma::mma_commit(&ctl->drain);
       umma::mbar_wait(&ctl->drain, 0, S.err, PG_WAIT);
@@ -187,8 +189,55 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
     const int row = q4 * 32 + lane;
     const int c0 = hf * 32;  // this warp's 32 of the 64 columns
     long long hand = 0;
-    for (int j = blockIdx.x; j < njobs; j += gridDim.x, ++hand) {
-      const bool okw = umma::mbar_wait(&ctl->tfull, (uint32_t)(hand & 1), S.err, PG_WAIT);
+    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+      const Job jb = jobs[j];
+      if (jb.nk == 0) continue;  // no MMAs, no accumulator handoff
+      const uint32_t par = (uint32_t)(hand & 1);
+      ++hand;
+      // everything this thread needs from global memory, before the wait, so
+      // the dependent lookups overlap the job's MMAs
+      const WorkItem it = S.items[jb.w];
+      const int wl = (int)(jb.w - W.w0);
+      const __nv_bfloat16 *Ab, *Bb;
+      const int16_t *ea_p, *eb_p;
+      pg_operands<KS, JOB>(S, W, jb, it, Ab, Bb, ea_p, eb_p);
+      const int ea = ea_p[row];
+      bool valid;
+      // Y job: row (b, G, g) of Y, Y2 row, FP64 need
+      int64_t yrow = 0, y2row = -1, nrowY = 0;
+      bool need64 = false;
+      int pA = 0, nbY = 0;
+      // D_AB job: row (F, f)
+      int F = 0, nf = 0, f = 0;
+      NbrEntry ef{};
+      if (JOB == 0) {
+        nbY = S.nao[it.b];
+        const int ncol = S.ncol[it.b];
+        nrowY = (int64_t)nbY * ncol;
+        const int rowY = jb.mt * TM + row;
+        pA = S.nabf[it.a];
+        valid = rowY < nrowY;
+        yrow = rowY;
+        need64 = W.y64_mode == 1 || (it.dab >= 0 && !(S.sym && it.role == 2));
+        if (valid && W.y2_on) {
+          const int b = rowY / ncol, col = rowY - b * ncol;
+          const int G = entry_of(S.nbr, it.gbase, it.nG, col);
+          const int g = col - S.nbr[it.gbase + G].aopre;
+          const int cb = S.kofs[it.gbase + G] / 16 + g / 16;
+          y2row = (((int64_t)cb * pA) * nbY + b) * 16 + (g & 15);
+        }
+      } else {
+        const int rF = jb.mt * TM + row;
+        valid = rF < S.ncol[it.a];
+        if (valid) {
+          F = entry_of(S.nbr, it.fbase, it.nF, rF);
+          ef = S.nbr[it.fbase + F];
+          nf = S.nao[ef.other];
+          f = rF - ef.aopre;
+        }
+      }
+
+      const bool okw = umma::mbar_wait(&ctl->tfull, par, S.err, PG_WAIT);
       if (umma::bar_any(!okw || *abort_f, PG_EPI * 32)) {
         *abort_f = 1;
         break;
@@ -209,49 +258,24 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
       umma::fence_before_sync();
       __syncwarp();
       if (lane == 0) umma::mbar_arrive(&ctl->tempty);
+      if (!valid) continue;
 
-      const Job jb = jobs[j];
-      const WorkItem it = S.items[jb.w];
-      const int wl = (int)(jb.w - W.w0);
-      const __nv_bfloat16 *Ab, *Bb;
-      const int16_t *ea_p, *eb_p;
-      pg_operands<KS, JOB>(S, W, jb, it, Ab, Bb, ea_p, eb_p);
-      const int ea = ea_p[row];
       if (JOB == 0) {
-        // Y[al][rowY] with rowY = b * ncol + col(G,g); Y2 (f32 pairs) in 16-column
+        // Y[al][b * ncol + col(G,g)] (FP64) and Y2 (f32 pairs) in 16-column
         // blocks [cb][al][b][16], cb = kofs(G) / 16 + g / 16
-        const int nb = S.nao[it.b], ncol = S.ncol[it.b];
-        const int nrow = nb * ncol;
-        const int rowY = jb.mt * TM + row;
-        const int pA = S.nabf[it.a];
-        if (rowY >= nrow) continue;
         double *Y = W.scratch + W.y_off[wl];
         float2 *Y2 = reinterpret_cast<float2 *>(W.scratch + W.y2_off[wl]);
-        const bool need64 = W.y64_mode == 1 || (it.dab >= 0 && !(S.sym && it.role == 2));
-        int64_t y2row = -1;
-        if (W.y2_on) {
-          const int b = rowY / ncol, col = rowY - b * ncol;
-          const int G = entry_of(S.nbr, it.gbase, it.nG, col);
-          const int g = col - S.nbr[it.gbase + G].aopre;
-          const int cb = S.kofs[it.gbase + G] / 16 + g / 16;
-          y2row = (((int64_t)cb * pA) * nb + b) * 16 + (g & 15);
-        }
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const int al = jb.nt * NT + c0 + i;
           if (al >= pA) break;
           const int e = ea + eb_p[c0 + i] - SH;
-          if (need64) Y[(int64_t)al * nrow + rowY] = scaled_i64(Wv[i], e);
-          if (y2row >= 0) Y2[y2row + (int64_t)al * nb * 16] = pair_i64(Wv[i], e);
+          if (need64) Y[(int64_t)al * nrowY + yrow] = scaled_i64(Wv[i], e);
+          if (y2row >= 0) Y2[y2row + (int64_t)al * nbY * 16] = pair_i64(Wv[i], e);
         }
       } else {
         // Sigma_FG blocks: rows (F,f) of atom A, columns (G,g) of atom B
-        const int ncolA = S.ncol[it.a], ncolB = S.ncol[it.b];
-        const int rF = jb.mt * TM + row;
-        if (rF >= ncolA) continue;
-        const int F = entry_of(S.nbr, it.fbase, it.nF, rF);
-        const NbrEntry ef = S.nbr[it.fbase + F];
-        const int nf = S.nao[ef.other], f = rF - ef.aopre;
+        const int ncolB = S.ncol[it.b];
         const bool mir = S.sym && it.role == 1;
         int lastG = -1;
         bool live = false;

@@ -177,9 +177,13 @@ __global__ void k_jobs_y(SplitShared S, SplitWave W) {
     const int mid = (lo + hi + 1) >> 1;
     if (W.y_candpre[mid] <= t) lo = mid; else hi = mid - 1;
   }
-  const int wl = lo;
+  // candidates are enumerated with the items grouped by atom B, and job t is
+  // candidate t (an empty job when skipped), so jobs running side by side
+  // read the same C_B tiles from L2
+  const int wl = (int)W.y_perm[lo];
+  if (t == 0) W.njobs[0] = (int)W.y_candpre[W.nw];
   const WorkItem &it = S.items[W.w0 + wl];
-  const int local = (int)(t - W.y_candpre[wl]);
+  const int local = (int)(t - W.y_candpre[lo]);
   const int ntv = (S.nabf[it.a] + NT - 1) / NT;
   const int mt = local / ntv, nt = local - mt * ntv;
   // skip tiles whose rows (b, G, g) belong only to G without a surviving term
@@ -199,10 +203,8 @@ __global__ void k_jobs_y(SplitShared S, SplitWave W) {
     for (int g = G0; g < it.nG && !any; ++g) any = S.wg[it.wg_off + g] != 0;
     for (int g = 0; g <= G1 && !any; ++g) any = S.wg[it.wg_off + g] != 0;
   }
-  if (!any) return;
-  const int j = atomicAdd(W.njobs, 1);
-  W.jobs[j] = Job{W.w0 + wl, mt, nt, 0, S.ktY[it.b]};
-  atomicAdd(W.tmacs, (unsigned long long)TM * NT * TK * S.ktY[it.b]);
+  W.jobs[t] = Job{W.w0 + wl, mt, nt, 0, any ? S.ktY[it.b] : 0};
+  if (any) atomicAdd(W.tmacs, (unsigned long long)TM * NT * TK * S.ktY[it.b]);
 }
 
 // D_AB jobs: (F-tile, G-tile) pairs holding at least one surviving block.

@@ -94,6 +94,7 @@ struct SplitWave {
   const int64_t *ps_base;          // -1 without D_AB jobs
   int16_t *ps_e;
   const int64_t *y_candpre, *v4_candpre;
+  const int64_t *y_perm;           // wave items in Y-job order (grouped by atom B), nw
   Job *jobs, *jobs4;
   int *njobs;                      // [0] Y jobs, [1] D_AB jobs, [2] Z jobs, [3] Z entries
   unsigned long long *tmacs;       // [0] Y, [1] D_AB, [2] Z: multiply-adds of the launched jobs
