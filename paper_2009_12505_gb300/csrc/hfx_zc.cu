@@ -46,10 +46,18 @@
 namespace split {
 
 constexpr int ZC_COLS = 32;                      // Z columns per job
-constexpr int ZC_EPI = 8;                        // epilogue warps
-constexpr int ZC_THREADS = (ZC_EPI + 3) * 32;    // + A/B loader, MMA issuer, Y loader
 constexpr int ZC_KMAX = 640;                     // K per job: exact f32 group sums
-constexpr int ZC_OWN = 8;                        // owned outputs per epilogue thread (2 x 32 x 32 / 256)
+
+// Epilogue geometry for EPI epilogue warps (8 or 16): 4 warps cover the 128
+// TMEM lanes, so there are EPI / 4 column groups of 32 / (EPI / 4) columns.
+template <int EPI>
+struct ZcGeo {
+  static constexpr int NQ = EPI / 4;                 // column groups
+  static constexpr int CW = ZC_COLS / NQ;            // Z columns per epilogue warp
+  static constexpr int ET = EPI * 32;                // epilogue threads
+  static constexpr int THREADS = (EPI + 3) * 32;     // + A/B loader, MMA issuer, Y loader
+  static constexpr int OWN = 2 * 32 * 32 / ET;       // owned outputs per epilogue thread
+};
 constexpr long long ZC_WAIT = 2000000000ll;      // cycles per bounded wait
 
 __host__ __device__ __forceinline__ int kb_of(int nao) { return nao <= 16 ? 16 : 32; }
@@ -330,7 +338,7 @@ struct ZcSmem {
   uint64_t full[8], empty[8], tfull[2], tempty[2], yfull[2], yempty[2], drain;
   uint32_t tslot;
   int abort_f;
-  int ecol[2][16];  // column exponents of the job, per column half
+  int ecol[ZC_COLS];  // column exponents of the job (column group q at q * CW)
 };
 
 // Launch shape of k_zc: ybytes = shared bytes per staged Y block (0: the
@@ -346,16 +354,19 @@ __device__ __forceinline__ const float2 *zc_y_global(const float2 *Y2, int cb, i
   return Y2 + (((int64_t)cb * pA + al) * nb) * 16;
 }
 
-template <int KS, int KBM, int NST>
-__global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W, ZcCfg cfg) {
+template <int KS, int KBM, int NST, int EPI>
+__global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
+    k_zc(SplitShared S, SplitWave W, ZcCfg cfg) {
+  constexpr int ZC_EPI = EPI, ZC_NQ = ZcGeo<EPI>::NQ, ZC_CW = ZcGeo<EPI>::CW,
+                ZC_ET = ZcGeo<EPI>::ET, ZC_OWN = ZcGeo<EPI>::OWN;
   constexpr int A_BYTES = KS * 128 * KBM * 2;
   constexpr int B_BYTES = KS * ZC_COLS * KBM * 2;
   constexpr int STG = A_BYTES + B_BYTES;
   constexpr int SH = 7 * (KS + 1);
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t *ybuf = smem + NST * STG;                                     // [2][2][ybytes]
-  float2 *red = reinterpret_cast<float2 *>(ybuf + 4 * cfg.ybytes);     // [2][128][rs]
-  ZcSmem *ctl = reinterpret_cast<ZcSmem *>(red + 2 * 128 * cfg.rs);
+  float2 *red = reinterpret_cast<float2 *>(ybuf + 4 * cfg.ybytes);     // [ZC_NQ][128][rs]
+  ZcSmem *ctl = reinterpret_cast<ZcSmem *>(red + ZC_NQ * 128 * cfg.rs);
   volatile int *abort_f = &ctl->abort_f;
   const bool ystage = cfg.ybytes > 0;
 
@@ -541,9 +552,9 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int q4 = warp & 3, hf = warp >> 2;
+    const int q4 = warp & 3, hf = warp >> 2;  // TMEM lane quarter, column group
     const int row = q4 * 32 + lane;
-    const int et = threadIdx.x;  // 0 .. 255
+    const int et = threadIdx.x;  // 0 .. ZC_ET - 1
     const int rs = cfg.rs;
     long long hand = 0;
     for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
@@ -554,31 +565,34 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
       const int mtz = (pA * na + 127) / 128;
       const float2 *Y2 = reinterpret_cast<const float2 *>(W.scratch + W.y2_off[wl]);
       // blocks: rows, outputs, columns
-      int Rb[2] = {16, 16}, nout[2] = {0, 0}, ncv[2] = {0, 0}, gat[2] = {0, 0}, gcb[2] = {0, 0},
-          gncb[2] = {0, 0};
+      int Rb[2] = {16, 16}, nout[2] = {0, 0}, ncv[2] = {0, 0}, gat[2] = {0, 0}, gcb[2] = {0, 0};
       for (int b = 0; b < jb.nblk; ++b) {
         const NbrEntry eg = S.nbr[it.gbase + jb.g[b]];
         const int ng = S.nao[eg.other];
         gat[b] = eg.other;
         gcb[b] = S.kofs[it.gbase + jb.g[b]] / 16;
-        gncb[b] = (ng + 15) / 16;
         ncv[b] = jb.piece[b] == 1 ? ng : nb;
         nout[b] = jb.piece[b] == 1 ? nb : ng;
         Rb[b] = ncv[b] <= 16 ? 16 : 32;
       }
-      // this warp's columns: block hb, columns [c0, c0 + 16) of it
-      int hb = -1, c0 = 0;
-      if (hf == 0) hb = 0;
-      else if (jb.nblk == 2) hb = 1;
-      else if (Rb[0] == 32) { hb = 0; c0 = 16; }
+      // block and columns [c0, c0 + ZC_CW) of column group q (two 16-column
+      // blocks: the first half of the groups each; one block: all groups below R)
+      auto group_block = [&](int q, int &cq) -> int {
+        const int jc = q * ZC_CW;
+        if (jb.nblk == 2) { cq = jc & 15; return jc >> 4; }
+        cq = jc;
+        return jc < Rb[0] ? 0 : -1;
+      };
+      int c0 = 0;
+      const int hb = group_block(hf, c0);
       const int piece = hb >= 0 ? jb.piece[hb] : 0;
-      // column exponents of this warp's 16 columns (shared by the half's warps;
+      // column exponents of this warp's columns (shared by the group's warps;
       // the previous job's last reads are behind the tile barriers)
-      const int *ecol = ctl->ecol[hf];
-      if (q4 == 0 && lane < 16) {
+      const int *ecol = ctl->ecol + hf * ZC_CW;
+      if (q4 == 0 && lane < ZC_CW) {
         const int at = hb >= 0 ? (piece == 1 ? gat[hb] : it.b) : 0;
         const int cc = c0 + lane;
-        ctl->ecol[hf][lane] = (hb >= 0 && cc < ncv[hb])
+        ctl->ecol[hf * ZC_CW + lane] = (hb >= 0 && cc < ncv[hb])
                                   ? row_exponent((long long)S.de[S.aoff[at] + cc]) : -1000;
       }
       float jh[ZC_OWN], jl[ZC_OWN];  // job sums of the owned outputs (f32 pairs)
@@ -593,7 +607,7 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
         bool okw = umma::mbar_wait(&ctl->tfull[tb], par, S.err, ZC_WAIT);
         if (okw && ystage) okw = umma::mbar_wait(&ctl->yfull[tb], par, S.err, ZC_WAIT);
         // the same decision in every epilogue warp
-        if (umma::bar_any(!okw || *abort_f, 256)) {
+        if (umma::bar_any(!okw || *abort_f, ZC_ET)) {
           *abort_f = 1;
           aborted = true;
           break;
@@ -604,26 +618,31 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
         const int al = rvalid ? rowZ / na : 0;
         const int al0 = mt * 128 / na, al1 = min(pA - 1, (mt * 128 + 127) / na);
         const int nal = al1 - al0 + 1;
-        long long Wv[16];
+        long long Wv[ZC_CW];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) Wv[c] = 0;
+        for (int c = 0; c < ZC_CW; ++c) Wv[c] = 0;
         if (hb >= 0) {
           // the digit-order groups, three loads in flight per wait
           const uint32_t ta = tbase + (uint32_t)(tb * 256) + ((uint32_t)(q4 * 32) << 16) +
-                              (uint32_t)(hf * 16);
+                              (uint32_t)(hf * ZC_CW);
 #pragma unroll
           for (int g0 = 0; g0 < KS; g0 += 3) {
-            uint32_t r[3][16];
+            uint32_t r[3][ZC_CW];
 #pragma unroll
             for (int u = 0; u < 3; ++u)
-              if (g0 + u < KS) umma::tmem_ld16_nowait(ta + (uint32_t)((g0 + u) * ZC_COLS), r[u]);
+              if (g0 + u < KS) {
+                if constexpr (ZC_CW == 8)
+                  umma::tmem_ld8_nowait(ta + (uint32_t)((g0 + u) * ZC_COLS), r[u]);
+                else
+                  umma::tmem_ld16_nowait(ta + (uint32_t)((g0 + u) * ZC_COLS), r[u]);
+              }
             umma::tmem_wait_ld();
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
               if (g0 + u >= KS) break;
               const int sh = 7 * (KS - 1 - g0 - u);
 #pragma unroll
-              for (int c = 0; c < 16; ++c)
+              for (int c = 0; c < ZC_CW; ++c)
                 Wv[c] += (long long)__float2int_rn(__uint_as_float(r[u][c])) * (1ll << sh);
             }
           }
@@ -642,38 +661,37 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
         if (hb >= 0 && rvalid) {
           const int eA = S.cz_e[S.cz_rowpre[it.a] + rowZ];
           const int no = nout[hb];
-          const int cend = min(16, ncv[hb] - c0);
-          float2 z[16];
+          const int cend = min(ZC_CW, ncv[hb] - c0);
+          float2 z[ZC_CW];
 #pragma unroll
-          for (int c = 0; c < 16; ++c)
+          for (int c = 0; c < ZC_CW; ++c)
             z[c] = c < cend ? pair_i64(Wv[c], eA + ecol[c] - SH) : make_float2(0.f, 0.f);
           float2 *rr = red + ((int64_t)hf * 128 + row) * rs;
           const int cs = piece == 1 ? 1 : 16;
-          // one output: out o = sum_c z[c] y[c cs]
-          auto one = [&](int o) {
-            const float2 *y = piece == 1 ? yrow(c0 >> 4) + o * 16 : yrow(o >> 4) + c0 * 16 + (o & 15);
+          // y of output o at column c: y[c cs].  Piece 1: out b = o,
+          // Y[al][b][G, g = c0 + c]; piece 2: out g = o, Y[al][b = c0 + c][G, g]
+          auto ybase = [&](int o) -> const float2 * {
+            return piece == 1 ? yrow(c0 >> 4) + o * 16 + (c0 & 15)
+                              : yrow(o >> 4) + c0 * 16 + (o & 15);
+          };
+          const int no4 = no & ~3;
+          for (int o = no4; o < no; ++o) {
+            const float2 *y = ybase(o);
             float sh = 0.f, sl = 0.f;
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < ZC_CW; ++c) {
               if (c >= cend) break;
               df_mac(sh, sl, z[c], y[c * cs]);
             }
             rr[o] = make_float2(sh, sl);
-          };
-          const int no4 = no & ~3;
-          for (int o = no4; o < no; ++o) one(o);
+          }
           for (int o0 = 0; o0 < no4; o0 += 4) {
             float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
             const float2 *yp[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              const int o = o0 + u;
-              // piece 1: out b = o, Y[al][b][G, g = c0 + c]; piece 2: out g = o,
-              // Y[al][b = c0 + c][G, g]
-              yp[u] = piece == 1 ? yrow(c0 >> 4) + o * 16 : yrow(o >> 4) + c0 * 16 + (o & 15);
-            }
+            for (int u = 0; u < 4; ++u) yp[u] = ybase(o0 + u);
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
+            for (int c = 0; c < ZC_CW; ++c) {
               if (c >= cend) break;
 #pragma unroll
               for (int u = 0; u < 4; ++u) df_mac(sh[u], sl[u], z[c], yp[u][c * cs]);
@@ -684,12 +702,13 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
         }
         __syncwarp();
         if (lane == 0) umma::mbar_arrive(&ctl->yempty[tb]);
-        asm volatile("bar.sync 1, 256;" ::: "memory");
-        // owners: (block, a, o) summed over the tile's rows (al, a) in order
+        asm volatile("bar.sync 1, %0;" ::"r"(ZC_ET) : "memory");
+        // owners: (block, a, o) summed over the tile's rows (al, a) and the
+        // block's column groups, in a fixed order
         const int r0 = mt * 128, rend = min(pA * na, r0 + 128);
 #pragma unroll
         for (int k = 0; k < ZC_OWN; ++k) {
-          const int idx = et + k * 256;
+          const int idx = et + k * ZC_ET;
           if (idx >= nown) break;
           const int b = idx < own0 ? 0 : 1;
           const int rem = idx - (b ? own0 : 0);
@@ -698,23 +717,22 @@ __global__ void __launch_bounds__(ZC_THREADS, 1) k_zc(SplitShared S, SplitWave W
           float h = jh[k], l = jl[k];
           for (; r < rend; r += na) {
             const int lr = r - r0;
-            if (jb.nblk == 2) {
-              df_add(h, l, red[((int64_t)b * 128 + lr) * rs + o]);
-            } else {
-              df_add(h, l, red[(int64_t)lr * rs + o]);
-              if (Rb[0] == 32) df_add(h, l, red[(128 + (int64_t)lr) * rs + o]);
+#pragma unroll
+            for (int q = 0; q < ZC_NQ; ++q) {
+              int cq;
+              if (group_block(q, cq) == b) df_add(h, l, red[((int64_t)q * 128 + lr) * rs + o]);
             }
           }
           jh[k] = h;
           jl[k] = l;
         }
-        asm volatile("bar.sync 1, 256;" ::: "memory");
+        asm volatile("bar.sync 1, %0;" ::"r"(ZC_ET) : "memory");
       }
       if (aborted) break;
       // add the finished blocks to Sigma (and mirrors)
 #pragma unroll
       for (int k = 0; k < ZC_OWN; ++k) {
-        const int idx = et + k * 256;
+        const int idx = et + k * ZC_ET;
         if (idx >= nown) break;
         const int b = idx < own0 ? 0 : 1;
         const int rem = idx - (b ? own0 : 0);
@@ -756,25 +774,29 @@ cudaError_t zc_run_t(const SplitShared &S, const SplitWave &W, const ZcPlanShape
   if (blocks <= 0) return cudaSuccess;
   constexpr size_t kMax = 227 * 1024;
   const int rs = P.nout_max <= 16 ? 16 : 32;
-  const size_t red = 2 * 128 * (size_t)rs * sizeof(float2) + sizeof(ZcSmem) + 64;
-  auto launch = [&](auto kern, int nst, int kbm, int ybytes) -> cudaError_t {
-    const size_t smem = (size_t)nst * KS * (128 + ZC_COLS) * kbm * 2 + 4 * (size_t)ybytes + red;
+  auto smem_of = [&](int nst, int kbm, int ybytes, int nq) {
+    return (size_t)nst * KS * (128 + ZC_COLS) * kbm * 2 + 4 * (size_t)ybytes +
+           (size_t)nq * 128 * rs * sizeof(float2) + sizeof(ZcSmem) + 64;
+  };
+  auto launch = [&](auto kern, int threads, int nst, int kbm, int ybytes, int nq) -> cudaError_t {
+    const size_t smem = smem_of(nst, kbm, ybytes, nq);
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<blocks, ZC_THREADS, smem, st>>>(S, W, ZcCfg{ybytes, rs});
+    kern<<<blocks, threads, smem, st>>>(S, W, ZcCfg{ybytes, rs});
     return cudaGetLastError();
   };
-  auto fits = [&](int nst, int kbm, int ybytes) {
-    return (size_t)nst * KS * (128 + ZC_COLS) * kbm * 2 + 4 * (size_t)ybytes + red <= kMax;
-  };
+  // 8 epilogue warps (2 column groups of 16).  16 warps (4 groups of 8) leave
+  // room for only two operand stages next to the staged Y and were slower.
+  constexpr int T8 = ZcGeo<8>::THREADS;
   if (P.kbmax <= 16) {
-    if (ZC_STAGE_Y && fits(3, 16, P.ybytes)) return launch(k_zc<KS, 16, 3>, 3, 16, P.ybytes);
-    if (fits(6, 16, 0)) return launch(k_zc<KS, 16, 6>, 6, 16, 0);
-    return launch(k_zc<KS, 16, 3>, 3, 16, 0);
+    if (ZC_STAGE_Y && smem_of(3, 16, P.ybytes, 2) <= kMax)
+      return launch(k_zc<KS, 16, 3, 8>, T8, 3, 16, P.ybytes, 2);
+    return launch(k_zc<KS, 16, 3, 8>, T8, 3, 16, 0, 2);
   }
-  if (ZC_STAGE_Y && fits(2, 32, P.ybytes)) return launch(k_zc<KS, 32, 2>, 2, 32, P.ybytes);
-  return launch(k_zc<KS, 32, 2>, 2, 32, 0);
+  if (ZC_STAGE_Y && smem_of(2, 32, P.ybytes, 2) <= kMax)
+    return launch(k_zc<KS, 32, 2, 8>, T8, 2, 32, P.ybytes, 2);
+  return launch(k_zc<KS, 32, 2, 8>, T8, 2, 32, 0, 2);
 }
 
 template <int KS>
