@@ -606,8 +606,9 @@ hfx_status dz_prepare_meta(hfx_ctx *ctx, int ks) {
   CK(ctx->d_dij.reserve(std::max<int64_t>(2 * nd, 1)));
   CK(ctx->d_aoff.reserve(n + 1));
   CK(ctx->d_de.reserve(std::max<int32_t>(aoff[n], 1)));
-  CK(ctx->d_dzero.reserve(1024));
-  CK(cudaMemsetAsync(ctx->d_dzero.p, 0, 1024 * sizeof(__nv_bfloat16), st));
+  // zero tile: up to 6 digits of a 32 x 32 tile
+  CK(ctx->d_dzero.reserve(6 * 32 * 32));
+  CK(cudaMemsetAsync(ctx->d_dzero.p, 0, 6 * 32 * 32 * sizeof(__nv_bfloat16), st));
   if (nd) {
     CK(cudaMemcpyAsync(ctx->d_dz_off.p, off.data(), sizeof(int64_t) * nd, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(ctx->d_dij.p, ij.data(), sizeof(int32_t) * 2 * nd, cudaMemcpyHostToDevice, st));

@@ -73,7 +73,7 @@ struct SplitShared {
   DevHash dhash;
   // D blocks as transposed digit tiles for the D_FG / D_FB products
   __nv_bfloat16 *dz;
-  const __nv_bfloat16 *dzero;      // zero tile (2 KB)
+  const __nv_bfloat16 *dzero;      // zero tile (6 digits of 32 x 32)
   const int64_t *dz_off;           // per D block
   const int32_t *dij;              // per D block: (i, j)
   unsigned long long *de;          // per (atom, ao) column maximum (bit pattern)

@@ -20,12 +20,14 @@
 //
 // Digit-stacked products.  A (C of atom A, rows (al,a), K = F blocks) and B
 // (D blocks, transposed) are split into KS balanced base-128 digits, exact in
-// bf16.  The B digits of one K step are stacked along N (digit j at rows
-// 32 j .. 32 j + 31), so one tcgen05.mma with A digit i, N = 32 (KS - i) and
-// accumulator column offset 32 i adds every product of digit order i + j
-// into TMEM columns [32 (i + j), 32 (i + j + 1)): KS MMAs per K step instead of
-// KS (KS + 1) / 2 narrow ones.  The epilogue recombines the order groups into
-// one exact int64 per element.
+// bf16.  In shared memory each column block's B digits of one K step are
+// stacked along N (digit j at rows R j .. R j + R - 1, R = 16 or 32 rows), so
+// one tcgen05.mma with A digit i, N = R (KS - i) and accumulator column offset
+// R i adds every product of digit order i + j into the block's TMEM columns
+// [R (i + j), R (i + j + 1)): KS MMAs per block and K step instead of
+// KS (KS + 1) / 2 narrow ones, and one bulk copy per block (the D tiles are
+// stored digit-major).  The epilogue recombines the order groups into one
+// exact int64 per element.
 //
 // Roles (one CTA per SM, persistent over a static round-robin job split):
 // warp 8 streams A and B tiles with 1-D bulk copies into a ring of shared
@@ -417,8 +419,9 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         R0 = ncb <= 16 ? 16 : 32;
       }
       // this lane's copy: 0 = A, 1 .. nblk KS = (block, digit)
-      const int cb = lane >= 1 ? (lane - 1) / KS : 0, cd = lane >= 1 ? (lane - 1) % KS : 0;
-      const bool has_b = lane >= 1 && lane <= jb.nblk * KS;
+      // lane 0 copies the A tile, lanes 1 .. nblk one whole B block each
+      const int cb = lane - 1;
+      const bool has_b = lane >= 1 && lane <= jb.nblk;
       const int Rl = jb.nblk == 1 ? R0 : 16;
       bool ok = true;
       for (int mt = 0; mt < mtz && ok; ++mt)
@@ -448,10 +451,11 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
             umma::bulk_g2s(st, Abase + ((int64_t)mt * ktot + en.kofs) * KS * 128, abytes,
                            &ctl->full[s]);
           } else if (has_b) {
+            // B stage block-major: block b's KS digits of Rl rows x kb at b KS 16 kb
             const int64_t dz = en.dz[cb];
-            const __nv_bfloat16 *src = dz >= 0 ? S.dz + dz + (int64_t)cd * Rl * kb : S.dzero;
-            umma::bulk_g2s(st + A_BYTES + cd * (ZC_COLS * kb * 2) + cb * 16 * kb * 2, src,
-                           (uint32_t)(Rl * kb * 2), &ctl->full[s]);
+            const __nv_bfloat16 *src = dz >= 0 ? S.dz + dz : S.dzero;
+            umma::bulk_g2s(st + A_BYTES + cb * (KS * 16 * kb * 2), src,
+                           (uint32_t)(KS * Rl * kb * 2), &ctl->full[s]);
           }
         }
     }
@@ -504,13 +508,22 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       long long step = 0, hand = 0;
-      uint32_t idesc[KS];
+      // N = R (KS - i) for a block of R rows (16 or 32), 16 KS at most 192
+      uint32_t idesc16[KS], idesc32[KS];
 #pragma unroll
-      for (int i = 0; i < KS; ++i) idesc[i] = umma::idesc_bf16_f32(128, ZC_COLS * (KS - i));
+      for (int i = 0; i < KS; ++i) {
+        idesc16[i] = umma::idesc_bf16_f32(128, 16 * (KS - i));
+        idesc32[i] = umma::idesc_bf16_f32(128, 32 * (KS - i));
+      }
       for (int j = blockIdx.x; j < njobs && !*abort_f; j += gridDim.x) {
         const ZcJob jb = W.zc_jobs[j];
         const WorkItem it = S.items[jb.w];
         const int mtz = (S.nabf[it.a] * S.nao[it.a] + 127) / 128;
+        int R0 = 16;  // rows of a lone block (two blocks have 16 each)
+        if (jb.nblk == 1) {
+          const int ncb = jb.piece[0] == 1 ? S.nao[S.nbr[it.gbase + jb.g[0]].other] : S.nao[it.b];
+          R0 = ncb <= 16 ? 16 : 32;
+        }
         for (int mt = 0; mt < mtz && !*abort_f; ++mt, ++hand) {
           const int tb = (int)(hand & 1);
           const long long use = hand >> 1;
@@ -533,14 +546,20 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
             const uint32_t a0 = umma::smem_u32(smem + s * STG);
             const uint32_t b0 = a0 + A_BYTES;
             const uint32_t sbo = (uint32_t)(kb / 8) * 128;
+            // block b (R rows): A digit i times B digits 0 .. KS - 1 - i of the block,
+            // into TMEM columns b R KS + (i + j) R + r
+            const int R = jb.nblk == 1 ? R0 : 16;
             for (int ks = 0; ks < kb / 16; ++ks)
+              for (int b = 0; b < jb.nblk; ++b)
 #pragma unroll
-              for (int i = 0; i < KS; ++i) {
-                const uint64_t ad = umma::smem_desc(a0 + i * (128 * kb * 2) + ks * 256, 128, sbo);
-                const uint64_t bd = umma::smem_desc(b0 + ks * 256, 128, sbo);
-                umma::mma_bf16(dcol + (uint32_t)(i * ZC_COLS), ad, bd, idesc[i],
-                               (q | ks | i) ? 1u : 0u);
-              }
+                for (int i = 0; i < KS; ++i) {
+                  const uint64_t ad =
+                      umma::smem_desc(a0 + i * (128 * kb * 2) + ks * 256, 128, sbo);
+                  const uint64_t bd =
+                      umma::smem_desc(b0 + b * (KS * 16 * kb * 2) + ks * 256, 128, sbo);
+                  umma::mma_bf16(dcol + (uint32_t)(b * 16 * KS + i * R), ad, bd,
+                                 R == 16 ? idesc16[i] : idesc32[i], (q | ks | i) ? 1u : 0u);
+                }
             umma::mma_commit(&ctl->empty[s]);
           }
           if (!ok) { *abort_f = 1; break; }
@@ -623,8 +642,10 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         for (int c = 0; c < ZC_CW; ++c) Wv[c] = 0;
         if (hb >= 0) {
           // the digit-order groups, three loads in flight per wait
+          // block hb's order g occupies TMEM columns hb 16 KS + g R .. + R
+          const int Rh = Rb[hb];
           const uint32_t ta = tbase + (uint32_t)(tb * 256) + ((uint32_t)(q4 * 32) << 16) +
-                              (uint32_t)(hf * ZC_CW);
+                              (uint32_t)(hb * 16 * KS + c0);
 #pragma unroll
           for (int g0 = 0; g0 < KS; g0 += 3) {
             uint32_t r[3][ZC_CW];
@@ -632,9 +653,9 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
             for (int u = 0; u < 3; ++u)
               if (g0 + u < KS) {
                 if constexpr (ZC_CW == 8)
-                  umma::tmem_ld8_nowait(ta + (uint32_t)((g0 + u) * ZC_COLS), r[u]);
+                  umma::tmem_ld8_nowait(ta + (uint32_t)((g0 + u) * Rh), r[u]);
                 else
-                  umma::tmem_ld16_nowait(ta + (uint32_t)((g0 + u) * ZC_COLS), r[u]);
+                  umma::tmem_ld16_nowait(ta + (uint32_t)((g0 + u) * Rh), r[u]);
               }
             umma::tmem_wait_ld();
 #pragma unroll
