@@ -811,6 +811,8 @@ cudaError_t zc_run_t(const SplitShared &S, const SplitWave &W, const ZcPlanShape
   // room for only two operand stages next to the staged Y and were slower.
   constexpr int T8 = ZcGeo<8>::THREADS;
   if (P.kbmax <= 16) {
+    if (ZC_STAGE_Y && smem_of(4, 16, P.ybytes, 2) <= kMax)
+      return launch(k_zc<KS, 16, 4, 8>, T8, 4, 16, P.ybytes, 2);
     if (ZC_STAGE_Y && smem_of(3, 16, P.ybytes, 2) <= kMax)
       return launch(k_zc<KS, 16, 3, 8>, T8, 3, 16, P.ybytes, 2);
     return launch(k_zc<KS, 16, 3, 8>, T8, 3, 16, 0, 2);
