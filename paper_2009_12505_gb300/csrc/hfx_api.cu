@@ -1079,7 +1079,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         const bool y64 = !(split && zjobs && ctx->sym) ||
                          (it.dab >= 0 && !(ctx->sym && it.role == 2));
         const int64_t ysz = y64 ? pad(pA * nb * ctx->aotot[it.b]) : 0;
-        const int64_t psz = it.dab >= 0 ? pad(pA * na * ctx->aotot[it.b]) : 0;
+        const int64_t psz = (it.dab >= 0 && !split) ? pad(pA * na * ctx->aotot[it.b]) : 0;
         // T3 only for the D_AG piece without mirrors; Q only for the FP64 D_FB piece
         const int64_t tsz = ctx->sym ? 0 : pad((int64_t)it.nG * pA * na * nb);
         const int64_t qsz = zjobs ? 0 : pad((int64_t)it.nF * pA * na * nb);
@@ -1141,7 +1141,8 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
       SplitWave SW{};
       if (split) {
         // per-wave split metadata
-        std::vector<int64_t> prow(nw + 1, 0), psb(nw, -1), ycand(nw + 1, 0), v4cand(nw + 1, 0);
+        std::vector<int64_t> prow(nw + 1, 0), psb(nw, -1), ycand(nw + 1, 0), v4cand(nw + 1, 0),
+            pgcand(nw + 1, 0);
         int64_t ps_elems = 0, v4max = 0;
         for (size_t q = 0; q < nw; ++q) {
           const WorkItem &it = ctx->items[w0 + q];
@@ -1150,6 +1151,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
           const bool has = it.dab >= 0 && !(ctx->sym && it.role == 2);
           const int64_t ntp = (ctx->aotot[it.b] + 63) / 64, mt4 = (ctx->aotot[it.a] + 127) / 128;
           prow[q + 1] = prow[q] + (has ? ntp * 64 : 0);
+          pgcand[q + 1] = pgcand[q] + (has ? it.nG : 0);
           v4cand[q + 1] = v4cand[q] + (has ? mt4 * ntp : 0);
           if (has) {
             psb[q] = ps_elems;
@@ -1176,6 +1178,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         wm.insert(wm.end(), ycand.begin(), ycand.end());
         wm.insert(wm.end(), v4cand.begin(), v4cand.end());
         wm.insert(wm.end(), yperm.begin(), yperm.end());
+        wm.insert(wm.end(), pgcand.begin(), pgcand.end());
         CK(ctx->d_wave_split.reserve(wm.size()));
         CK(cudaMemcpyAsync(ctx->d_wave_split.p, wm.data(), sizeof(int64_t) * wm.size(),
                            cudaMemcpyHostToDevice, st));
@@ -1195,6 +1198,8 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         SW.y_candpre = ctx->d_wave_split.p + (nw + 1) + nw;
         SW.v4_candpre = ctx->d_wave_split.p + 2 * (nw + 1) + nw;
         SW.y_perm = ctx->d_wave_split.p + 3 * (nw + 1) + nw;
+        SW.pg_candpre = ctx->d_wave_split.p + 3 * (nw + 1) + 2 * nw;
+        SW.h_pgcand = pgcand[nw];
         SW.y2_off = ctx->d_waveoffs.p + 4 * nw;
         SW.y2_on = zjobs ? 1 : 0;
         SW.y64_mode = (zjobs && ctx->sym) ? 2 : 1;
@@ -1215,6 +1220,10 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         // Y and the D_AB piece run on the tensor cores; the D_FG and D_FB pieces
         // too when the Z-job form is selected (HFX_ZJOBS=1)
         c.skip = zjobs ? (1u | 4u | 8u | 32u | 64u) : (1u | 64u);
+        // P of the D_AB piece is computed and sliced in phase 1; the D-stage is
+        // left with T3, needed only without mirror pieces
+        c.no_p = 1;
+        if (ctx->sym) c.skip |= 2u;
       }
       CK(launch_contract_fp64(c, st, ctx->kev, &nl));
       ctx->launches += nl;
@@ -1222,7 +1231,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         CK(cudaEventRecord(ctx->sev[2], st));
         CK(split_wave(SS, SW, nslices, 1, st));
         CK(cudaEventRecord(ctx->sev[3], st));
-        ctx->launches += (SW.h_prows > 0) + (SW.h_v4cand > 0) + 1;
+        ctx->launches += (SW.h_pgcand > 0) + (SW.h_v4cand > 0) + 1;
       }
       if (split && zjobs) {
         // D_FG and D_FB pieces: count jobs and entries, size the lists, plan and run

@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kThreads) k_dstage(ContractArgs A) {
   const int ncol = A.ncol[it.b];
   const double *Y = A.scratch + A.y_off[L.w - A.w0] + eg.aopre;  // Y[al][b][ncol]
   unsigned long long macs = 0;
-  if ((bits & 8u) && it.dab >= 0 && !(A.sym && it.role == 2)) {
+  if ((bits & 8u) && it.dab >= 0 && !(A.sym && it.role == 2) && !A.no_p) {
     // P_G[al][a][g] = sum_b D_AB[a][b] Y_G[al][b][g]
     const double *Dab = A.D.data + A.D.offs[it.dab];
     double *P = A.scratch + A.p_off[L.w - A.w0] + eg.aopre;  // P[al][a][ncol]

@@ -159,6 +159,7 @@ struct ContractArgs {
   unsigned *err;
   int sym;                   // inputs Hermitian: use the mirror pieces (see hfx_fp64.cu)
   unsigned skip;             // kernels not to launch: bit q = launch order q (0 = Y ... 6 = D_AB)
+  int no_p;                  // the D-stage leaves P (the D_AB piece's T) to the split path
   unsigned long long *dcacc; // adjoint: fixed-point dE/dC (2 words per C element)
   double *dv;                // adjoint: dE/dV in the V block layout
 };

@@ -95,19 +95,6 @@ struct SrcV {
   __device__ double get(int r, int beta) const { return V[(int64_t)r * pB + beta]; }
 };
 
-// P of a pair: rows (G, g), K = (alpha, a); rows of G without D_AB survivors are zero.
-struct SrcP {
-  const double *P;
-  const NbrEntry *nbr;
-  const uint8_t *wg;
-  int64_t gbase, wg_off;
-  int nG, ncol;
-  __device__ bool row_live(int r) const {
-    return (wg[wg_off + entry_of(nbr, gbase, nG, r)] & 8u) != 0;
-  }
-  __device__ double get(int r, int kappa) const { return P[(int64_t)kappa * ncol + r]; }
-};
-
 template <int KS>
 __global__ void k_slice_atoms(SplitShared S, int which /*0: CY, 1: C4*/) {
   const int64_t grow = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -149,22 +136,85 @@ __global__ void k_slice_v(SplitShared S) {
   slice_row<KS>(src, grow, r, NT, pA, pB, S.ktY[it.b], S.vs + S.vs_base[e], S.vs_e);
 }
 
+// P of the D_AB piece, computed and sliced in one pass: one CTA per (pair, G)
+// of the wave's pairs with a D_AB job.  P_G[(al,a)][g] = sum_b D_AB[a][b]
+// Y[al][b][(G,g)] in FP64 (the D-stage's order), held in shared memory for a
+// chunk of g columns, then written as the digit rows (G,g) of the B operand,
+// K = (al,a), with one exponent per row.  Rows of G without D_AB survivors
+// and the padding rows after the last G are not written: the D_AB epilogue
+// adds only surviving (F, G) blocks, and each output column depends on its
+// own B row alone, so whatever those rows hold never reaches Sigma.
+constexpr int PD_THREADS = 256;
+constexpr int PD_SMEM_DOUBLES = 3072;  // 24 KB: a few g columns at a time
+
 template <int KS>
-__global__ void k_slice_p(SplitShared S, SplitWave W) {
-  const int64_t grow = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (grow >= W.p_rowpre[W.nw]) return;
+__global__ void __launch_bounds__(PD_THREADS) k_pdig(SplitShared S, SplitWave W) {
+  extern __shared__ double Ps[];  // [gc][K]
+  __shared__ int es[32];
+  const int64_t t = blockIdx.x;
   int lo = 0, hi = W.nw - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
-    if (W.p_rowpre[mid] <= grow) lo = mid; else hi = mid - 1;
+    if (W.pg_candpre[mid] <= t) lo = mid; else hi = mid - 1;
   }
   const int wl = lo;
-  if (W.ps_base[wl] < 0) return;  // no D_AB job for this pair
+  if (W.ps_base[wl] < 0) return;
   const WorkItem &it = S.items[W.w0 + wl];
-  const int r = (int)(grow - W.p_rowpre[wl]);
-  const int pA = S.nabf[it.a], na = S.nao[it.a], ncol = S.ncol[it.b];
-  SrcP src{W.scratch + W.p_off[wl], S.nbr, S.wg, it.gbase, it.wg_off, it.nG, ncol};
-  slice_row<KS>(src, grow, r, NT, ncol, pA * na, S.kt4[it.a], W.ps + W.ps_base[wl], W.ps_e);
+  const int G = (int)(t - W.pg_candpre[wl]);
+  const NbrEntry eg = S.nbr[it.gbase + G];
+  const int pA = S.nabf[it.a], na = S.nao[it.a], nb = S.nao[it.b], ng = S.nao[eg.other];
+  const int K = pA * na, ncol = S.ncol[it.b], ktiles = S.kt4[it.a], KT = ktiles * TK;
+  if (!(S.wg[it.wg_off + G] & 8u)) return;  // no D_AB survivor for this G
+  const bool live = true;
+  __nv_bfloat16 *out = W.ps + W.ps_base[wl];
+  int16_t *eout = W.ps_e + W.p_rowpre[wl];
+  const double *Y = W.scratch + W.y_off[wl];
+  const double *Dab = S.Dd + S.Do[it.dab];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  auto put = [&](int r, int c, const int (&d)[KS]) {
+    const int rt = r / NT, rr = r - rt * NT, kt = c / TK, cc = c - kt * TK;
+    __nv_bfloat16 *base = out + ((int64_t)(rt * ktiles + kt) * KS) * NT * TK;
+#pragma unroll
+    for (int sd = 0; sd < KS; ++sd)
+      base[(int64_t)sd * NT * TK + tile_off(rr, cc)] = __int2bfloat16_rn(d[sd]);
+  };
+  const int gc = max(1, min(32, PD_SMEM_DOUBLES / K));
+  for (int g0 = 0; g0 < ng; g0 += gc) {
+    const int gn = min(gc, ng - g0);
+    if (live)
+      for (int idx = threadIdx.x; idx < gn * K; idx += PD_THREADS) {
+        const int gi = idx / K, kap = idx - gi * K, al = kap / na, a = kap - al * na;
+        const double *y = Y + (int64_t)al * nb * ncol + eg.aopre + g0 + gi;
+        const double *d = Dab + a * nb;
+        double sum = 0.0;
+        for (int b = 0; b < nb; ++b) sum = fma(d[b], y[(int64_t)b * ncol], sum);
+        Ps[gi * K + kap] = sum;
+      }
+    __syncthreads();
+    // one exponent per row (G, g0 + gi) over its K values
+    for (int gi = warp; gi < gn; gi += PD_THREADS / 32) {
+      long long mbits = 0;
+      if (live)
+        for (int c = lane; c < K; c += 32)
+          mbits = max(mbits, __double_as_longlong(Ps[gi * K + c]) & 0x7FFFFFFFFFFFFFFFll);
+      for (int o = 16; o; o >>= 1) mbits = max(mbits, __shfl_xor_sync(0xffffffffu, mbits, o));
+      const int e = row_exponent(mbits);
+      if (lane == 0) {
+        es[gi] = e;
+        eout[eg.aopre + g0 + gi] = (int16_t)max(-30000, e);
+      }
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < gn * KT; idx += PD_THREADS) {
+      const int gi = idx / KT, c = idx - gi * KT;
+      const int e = es[gi];
+      const double x = (live && c < K && e > -1000) ? Ps[gi * K + c] : 0.0;
+      int d[KS];
+      to_digits<KS>(x, e, d);
+      put(eg.aopre + g0 + gi, c, d);
+    }
+    __syncthreads();
+  }
 }
 
 // ------------------------------------------------------------------- jobs
@@ -265,9 +315,14 @@ cudaError_t wave_t(const SplitShared &S, const SplitWave &W, int phase, cudaStre
     if (e != cudaSuccess) return e;
     return split_pgemm(S, W, KS, 0, W.h_ycand, st);
   }
-  // phase 1: slice P, build D_AB jobs, run them
-  if (W.h_prows > 0)
-    k_slice_p<KS><<<(unsigned)((W.h_prows * 32 + 255) / 256), 256, 0, st>>>(S, W);
+  // phase 1: P digits, D_AB jobs, D_AB products
+  if (W.h_pgcand > 0) {
+    const int smem = PD_SMEM_DOUBLES * (int)sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_pdig<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         smem);
+    if (e != cudaSuccess) return e;
+    k_pdig<KS><<<(unsigned)W.h_pgcand, PD_THREADS, smem, st>>>(S, W);
+  }
   if (W.h_v4cand > 0)
     k_jobs_v4<<<(unsigned)((W.h_v4cand + 255) / 256), 256, 0, st>>>(S, W);
   cudaError_t e = cudaGetLastError();

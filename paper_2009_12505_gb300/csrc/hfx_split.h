@@ -95,6 +95,8 @@ struct SplitWave {
   int16_t *ps_e;
   const int64_t *y_candpre, *v4_candpre;
   const int64_t *y_perm;           // wave items in Y-job order (grouped by atom B), nw
+  const int64_t *pg_candpre;       // per item: nG if it has D_AB jobs else 0, nw + 1
+  int64_t h_pgcand;
   Job *jobs, *jobs4;
   int *njobs;                      // [0] Y jobs, [1] D_AB jobs, [2] Z jobs, [3] Z entries
   unsigned long long *tmacs;       // [0] Y, [1] D_AB, [2] Z: multiply-adds of the launched jobs
