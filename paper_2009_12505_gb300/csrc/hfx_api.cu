@@ -143,6 +143,8 @@ struct hfx_ctx {
   DevBuf<int16_t> d_cy_e, d_c4_e, d_vs_e, d_ps_e, d_cz_e;
   DevBuf<int64_t> d_cz_meta;      // cz_base, cz_rowpre
   DevBuf<int32_t> d_kofs, d_ktotZ;
+  DevBuf<int16_t> d_colG;          // per (atom, column): index of its neighbour entry
+  DevBuf<int64_t> d_coloff;        // per atom: first column in d_colG
   std::vector<int32_t> ktotZ_h;  // per atom: sum of 16 ceil(nao / 16) over its neighbours
   int64_t h_cz_rows = 0;
   // D digit tiles for the D_FG / D_FB products
@@ -540,6 +542,25 @@ hfx_status split_prepare(hfx_ctx *ctx, int ks) {
   CK(cudaMemcpyAsync(ctx->d_ktotZ.p, ktotZ.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, st));
   ctx->ktotZ_h = ktotZ;
   CK(cudaStreamSynchronize(st));
+  // column (G, g) of an atom's concatenated neighbour blocks -> local index of G
+  {
+    std::vector<int64_t> coloff(n + 1, 0);
+    for (int x = 0; x < n; ++x) coloff[x + 1] = coloff[x] + ctx->aotot[x];
+    std::vector<int16_t> colG(std::max<int64_t>(coloff[n], 1));
+    for (int x = 0; x < n; ++x)
+      for (int64_t q = ctx->nc_start[x]; q < ctx->nc_start[x + 1]; ++q) {
+        const NbrEntry &e = ctx->nbr[q];
+        for (int g = 0; g < ctx->nao[e.other]; ++g)
+          colG[coloff[x] + e.aopre + g] = (int16_t)(q - ctx->nc_start[x]);
+      }
+    CK(ctx->d_colG.reserve(colG.size()));
+    CK(ctx->d_coloff.reserve(n + 1));
+    CK(cudaMemcpyAsync(ctx->d_colG.p, colG.data(), sizeof(int16_t) * colG.size(),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(ctx->d_coloff.p, coloff.data(), sizeof(int64_t) * (n + 1),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
   ctx->h_cy_rows = cy_row[n];
   ctx->h_c4_rows = c4_row[n];
   ctx->h_v_rows = v_row[nv];
@@ -684,6 +705,8 @@ SplitShared split_shared(hfx_ctx *ctx) {
   S.de = ctx->d_de.p;
   S.aoff = ctx->d_aoff.p;
   S.h_nd = ctx->dz_nd > 0 ? ctx->dz_nd : 0;
+  S.colG = ctx->d_colG.p;
+  S.coloff = ctx->d_coloff.p;
   S.nsm = ctx->nsm;
   return S;
 }

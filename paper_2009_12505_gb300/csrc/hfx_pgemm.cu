@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         need64 = W.y64_mode == 1 || (it.dab >= 0 && !(S.sym && it.role == 2));
         if (valid && (W.y2_on || W.y64_mode == 2)) {
           const int b = rowY / ncol, col = rowY - b * ncol;
-          const int G = entry_of(S.nbr, it.gbase, it.nG, col);
+          const int G = S.colG[S.coloff[it.b] + col];
           const int g = col - S.nbr[it.gbase + G].aopre;
           // only rows of G with survivors are read: the f32 pairs by the D_FG /
           // D_FB products, FP64 Y (when kept for the D_AB piece alone) by P
@@ -236,7 +236,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         const int rF = jb.mt * TM + row;
         valid = rF < S.ncol[it.a];
         if (valid) {
-          F = entry_of(S.nbr, it.fbase, it.nF, rF);
+          F = S.colG[S.coloff[it.a] + rF];
           ef = S.nbr[it.fbase + F];
           nf = S.nao[ef.other];
           f = rF - ef.aopre;
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
           const int cG = jb.nt * NT + c0 + i;
           if (cG >= ncolB) break;
           if (cG >= gpre + ng || lastG < 0) {
-            const int G = entry_of(S.nbr, it.gbase, it.nG, cG);
+            const int G = S.colG[S.coloff[it.b] + cG];
             const NbrEntry eg = S.nbr[it.gbase + G];
             lastG = G;
             ng = S.nao[eg.other];

@@ -80,6 +80,8 @@ struct SplitShared {
   const int32_t *aoff;             // per atom: first (atom, ao) index
   int64_t h_nd;                    // D blocks
   int32_t nsm;                     // SMs of the device (persistent grids)
+  const int16_t *colG;             // per (atom, column): local index of its neighbour entry
+  const int64_t *coloff;           // per atom: first column in colG
   int64_t h_cy_rows, h_c4_rows, h_v_rows, h_cz_rows;  // host copies of the row totals
 };
 
