@@ -1097,17 +1097,16 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         const int64_t pA = ctx->nabf[it.a], na = ctx->nao[it.a], nb = ctx->nao[it.b];
         // every region starts on a 256-byte boundary (bulk copies read Y2)
         auto pad = [](int64_t x) { return (x + 31) / 32 * 32; };
-        // FP64 Y: with the tensor D_FG / D_FB products and mirror pieces only the
-        // D-stage of items whose D_AB piece runs here reads it
-        const bool y64 = !(split && zjobs && ctx->sym) ||
-                         (it.dab >= 0 && !(ctx->sym && it.role == 2));
+        // FP64 Y: not read at all with the tensor D_FG / D_FB products and mirror
+        // pieces (P of the D_AB piece is built from the f32 pairs)
+        const bool y64 = !(split && zjobs && ctx->sym);
         const int64_t ysz = y64 ? pad(pA * nb * ctx->aotot[it.b]) : 0;
         const int64_t psz = (it.dab >= 0 && !split) ? pad(pA * na * ctx->aotot[it.b]) : 0;
         // T3 only for the D_AG piece without mirrors; Q only for the FP64 D_FB piece
         const int64_t tsz = ctx->sym ? 0 : pad((int64_t)it.nG * pA * na * nb);
         const int64_t qsz = zjobs ? 0 : pad((int64_t)it.nF * pA * na * nb);
-        // Y as f32 pairs in 16-column blocks (D_FG / D_FB products)
-        const int64_t pssz = (split && zjobs) ? pad(pA * nb * ctx->ktotZ_h[it.b]) : 0;
+        // Y as f32 pairs in 16-column blocks (D_FG / D_FB products and P)
+        const int64_t pssz = split ? pad(pA * nb * ctx->ktotZ_h[it.b]) : 0;
         const size_t need = (size_t)(ysz + psz + tsz + qsz + pssz);
         if (w1 > w0 && used + need > budget) break;
         yo.push_back((int64_t)used);
@@ -1224,7 +1223,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         SW.pg_candpre = ctx->d_wave_split.p + 3 * (nw + 1) + 2 * nw;
         SW.h_pgcand = pgcand[nw];
         SW.y2_off = ctx->d_waveoffs.p + 4 * nw;
-        SW.y2_on = zjobs ? 1 : 0;
+        SW.y2_on = 1;
         SW.y64_mode = (zjobs && ctx->sym) ? 2 : 1;
         SW.ps = ctx->d_ps.p;
         SW.ps_e = ctx->d_ps_e.p;

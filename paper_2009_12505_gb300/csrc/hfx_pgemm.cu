@@ -218,19 +218,18 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         pA = S.nabf[it.a];
         valid = rowY < nrowY;
         yrow = rowY;
-        need64 = W.y64_mode == 1 || (it.dab >= 0 && !(S.sym && it.role == 2));
-        if (valid && (W.y2_on || W.y64_mode == 2)) {
+        need64 = W.y64_mode == 1;
+        if (valid && W.y2_on) {
           const int b = rowY / ncol, col = rowY - b * ncol;
           const int G = S.colG[S.coloff[it.b] + col];
           const int g = col - S.nbr[it.gbase + G].aopre;
           // only rows of G with survivors are read: the f32 pairs by the D_FG /
-          // D_FB products, FP64 Y (when kept for the D_AB piece alone) by P
+          // D_FB products and by P of the D_AB piece
           const unsigned bits = S.wg[it.wg_off + G];
-          if (W.y2_on && (bits & 3u)) {
+          if (bits & 11u) {
             const int cb = S.kofs[it.gbase + G] / 16 + g / 16;
             y2row = (((int64_t)cb * pA) * nbY + b) * 16 + (g & 15);
           }
-          if (W.y64_mode == 2 && !(bits & 8u)) need64 = false;
         }
       } else {
         const int rF = jb.mt * TM + row;

@@ -137,20 +137,24 @@ __global__ void k_slice_v(SplitShared S) {
 }
 
 // P of the D_AB piece, computed and sliced in one pass: one CTA per (pair, G)
-// of the wave's pairs with a D_AB job.  P_G[(al,a)][g] = sum_b D_AB[a][b]
-// Y[al][b][(G,g)] in FP64 (the D-stage's order), held in shared memory for a
-// chunk of g columns, then written as the digit rows (G,g) of the B operand,
-// K = (al,a), with one exponent per row.  Rows of G without D_AB survivors
+// of the wave's pairs with a D_AB job and D_AB survivors for G.
+//   P_G[(al,a)][g] = sum_b D_AB[a][b] Y[al][b][(G,g)]
+// in double-float arithmetic from the f32 pairs of Y, held in shared memory
+// for a chunk of g columns, then written as the digit rows (G,g) of the B
+// operand, K = (al,a), with one exponent per row.  A digit expansion only has
+// to be within one unit of the scaled value, so the integer is formed from
+// the two halves of the pair separately.  Rows of G without D_AB survivors
 // and the padding rows after the last G are not written: the D_AB epilogue
 // adds only surviving (F, G) blocks, and each output column depends on its
 // own B row alone, so whatever those rows hold never reaches Sigma.
 constexpr int PD_THREADS = 256;
-constexpr int PD_SMEM_DOUBLES = 3072;  // 24 KB: a few g columns at a time
+constexpr int PD_SMEM_PAIRS = 3072;  // 24 KB: a few g columns at a time
 
 template <int KS>
 __global__ void __launch_bounds__(PD_THREADS) k_pdig(SplitShared S, SplitWave W) {
-  extern __shared__ double Ps[];  // [gc][K]
+  extern __shared__ float2 Ps[];  // [gc][K]
   __shared__ int es[32];
+  __shared__ float2 Dp[32 * 32];  // D_AB as f32 pairs
   const int64_t t = blockIdx.x;
   int lo = 0, hi = W.nw - 1;
   while (lo < hi) {
@@ -161,16 +165,22 @@ __global__ void __launch_bounds__(PD_THREADS) k_pdig(SplitShared S, SplitWave W)
   if (W.ps_base[wl] < 0) return;
   const WorkItem &it = S.items[W.w0 + wl];
   const int G = (int)(t - W.pg_candpre[wl]);
+  if (!(S.wg[it.wg_off + G] & 8u)) return;  // no D_AB survivor for this G
   const NbrEntry eg = S.nbr[it.gbase + G];
   const int pA = S.nabf[it.a], na = S.nao[it.a], nb = S.nao[it.b], ng = S.nao[eg.other];
-  const int K = pA * na, ncol = S.ncol[it.b], ktiles = S.kt4[it.a], KT = ktiles * TK;
-  if (!(S.wg[it.wg_off + G] & 8u)) return;  // no D_AB survivor for this G
-  const bool live = true;
+  const int K = pA * na, ktiles = S.kt4[it.a], KT = ktiles * TK;
+  const int cbG = S.kofs[it.gbase + G] / 16;
   __nv_bfloat16 *out = W.ps + W.ps_base[wl];
   int16_t *eout = W.ps_e + W.p_rowpre[wl];
-  const double *Y = W.scratch + W.y_off[wl];
+  const float2 *Y2 = reinterpret_cast<const float2 *>(W.scratch + W.y2_off[wl]);
   const double *Dab = S.Dd + S.Do[it.dab];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = threadIdx.x; i < na * nb; i += PD_THREADS) {
+    const double d = Dab[i];
+    const float h = __double2float_rn(d);
+    Dp[i] = make_float2(h, __double2float_rn(d - (double)h));
+  }
+  __syncthreads();
   auto put = [&](int r, int c, const int (&d)[KS]) {
     const int rt = r / NT, rr = r - rt * NT, kt = c / TK, cc = c - kt * TK;
     __nv_bfloat16 *base = out + ((int64_t)(rt * ktiles + kt) * KS) * NT * TK;
@@ -178,27 +188,26 @@ __global__ void __launch_bounds__(PD_THREADS) k_pdig(SplitShared S, SplitWave W)
     for (int sd = 0; sd < KS; ++sd)
       base[(int64_t)sd * NT * TK + tile_off(rr, cc)] = __int2bfloat16_rn(d[sd]);
   };
-  const int gc = max(1, min(32, PD_SMEM_DOUBLES / K));
+  const int gc = max(1, min(32, PD_SMEM_PAIRS / K));
   for (int g0 = 0; g0 < ng; g0 += gc) {
     const int gn = min(gc, ng - g0);
-    if (live)
-      for (int idx = threadIdx.x; idx < gn * K; idx += PD_THREADS) {
-        const int gi = idx / K, kap = idx - gi * K, al = kap / na, a = kap - al * na;
-        const double *y = Y + (int64_t)al * nb * ncol + eg.aopre + g0 + gi;
-        const double *d = Dab + a * nb;
-        double sum = 0.0;
-        for (int b = 0; b < nb; ++b) sum = fma(d[b], y[(int64_t)b * ncol], sum);
-        Ps[gi * K + kap] = sum;
-      }
+    for (int idx = threadIdx.x; idx < gn * K; idx += PD_THREADS) {
+      const int gi = idx / K, kap = idx - gi * K, al = kap / na, a = kap - al * na;
+      const int g = g0 + gi;
+      // Y2 layout [cb][al][b][16]
+      const float2 *y = Y2 + (((int64_t)(cbG + (g >> 4)) * pA + al) * nb) * 16 + (g & 15);
+      const float2 *d = Dp + a * nb;
+      float sh = 0.f, sl = 0.f;
+      for (int b = 0; b < nb; ++b) df_mac(sh, sl, d[b], y[b * 16]);
+      Ps[gi * K + kap] = make_float2(sh, sl);
+    }
     __syncthreads();
     // one exponent per row (G, g0 + gi) over its K values
     for (int gi = warp; gi < gn; gi += PD_THREADS / 32) {
-      long long mbits = 0;
-      if (live)
-        for (int c = lane; c < K; c += 32)
-          mbits = max(mbits, __double_as_longlong(Ps[gi * K + c]) & 0x7FFFFFFFFFFFFFFFll);
-      for (int o = 16; o; o >>= 1) mbits = max(mbits, __shfl_xor_sync(0xffffffffu, mbits, o));
-      const int e = row_exponent(mbits);
+      float m = 0.f;
+      for (int c = lane; c < K; c += 32) m = fmaxf(m, fabsf(Ps[gi * K + c].x));
+      for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      const int e = row_exponent(__double_as_longlong((double)m));
       if (lane == 0) {
         es[gi] = e;
         eout[eg.aopre + g0 + gi] = (int16_t)max(-30000, e);
@@ -208,9 +217,17 @@ __global__ void __launch_bounds__(PD_THREADS) k_pdig(SplitShared S, SplitWave W)
     for (int idx = threadIdx.x; idx < gn * KT; idx += PD_THREADS) {
       const int gi = idx / KT, c = idx - gi * KT;
       const int e = es[gi];
-      const double x = (live && c < K && e > -1000) ? Ps[gi * K + c] : 0.0;
+      long long X = 0;
+      if (c < K && e > -200) {  // below 2^-200 the row is dropped
+        // scale by 2^(7 KS - e) (|value| < 2^(e - 1)) in two exact steps
+        const int sft = 7 * KS - e, s1 = sft / 2, s2 = sft - s1;
+        const float f1 = __int_as_float((s1 + 127) << 23), f2 = __int_as_float((s2 + 127) << 23);
+        const float2 v = Ps[gi * K + c];
+        X = __float2ll_rn(__fmul_rn(__fmul_rn(v.x, f1), f2)) +
+            __float2ll_rn(__fmul_rn(__fmul_rn(v.y, f1), f2));
+      }
       int d[KS];
-      to_digits<KS>(x, e, d);
+      to_digits_i64<KS>(X, d);
       put(eg.aopre + g0 + gi, c, d);
     }
     __syncthreads();
@@ -317,7 +334,7 @@ cudaError_t wave_t(const SplitShared &S, const SplitWave &W, int phase, cudaStre
   }
   // phase 1: P digits, D_AB jobs, D_AB products
   if (W.h_pgcand > 0) {
-    const int smem = PD_SMEM_DOUBLES * (int)sizeof(double);
+    const int smem = PD_SMEM_PAIRS * (int)sizeof(float2);
     cudaError_t e = cudaFuncSetAttribute(k_pdig<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem);
     if (e != cudaSuccess) return e;

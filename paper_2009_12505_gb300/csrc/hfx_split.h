@@ -104,11 +104,10 @@ struct SplitWave {
   unsigned long long *tmacs;       // [0] Y, [1] D_AB, [2] Z: multiply-adds of the launched jobs
   int64_t h_ycand, h_v4cand, h_prows, h_v4jobs_max;
   // Y as (hi, lo) f32 pairs in 16-column blocks, [cb][al][b][16], for the
-  // D_FG / D_FB product epilogues; written only when y2_on (the region exists)
+  // D_FG / D_FB product epilogues and P; written only when y2_on (the region exists)
   const int64_t *y2_off;
   int32_t y2_on;
-  // FP64 Y: 1 = every item; 2 = only items whose D_AB piece runs here (the
-  // D-stage is then its only reader)
+  // FP64 Y: 1 = every item (read by the FP64 kernels); 2 = none
   int32_t y64_mode;
   // D_FG and D_FB products: job list and F entries
   ZcJob *zc_jobs;

@@ -36,6 +36,19 @@ __device__ __forceinline__ void to_digits(double x, int e, int (&d)[KS]) {
   d[0] = (int)X;
 }
 
+// k balanced base-128 digits of an integer X with |X| <= 2^(7 KS - 1):
+// X = sum_s d_s 2^(7 (KS - 1 - s)), |d_s| <= 64.
+template <int KS>
+__device__ __forceinline__ void to_digits_i64(long long X, int (&d)[KS]) {
+#pragma unroll
+  for (int s = KS - 1; s > 0; --s) {
+    const int dd = (int)(((X + 64) & 127) - 64);
+    d[s] = dd;
+    X = (X - dd) >> 7;
+  }
+  d[0] = (int)X;
+}
+
 // W * 2^e as a double using integer operations only (round to nearest).
 __device__ __forceinline__ double scaled_i64(long long W, int e) {
   if (W == 0) return 0.0;
