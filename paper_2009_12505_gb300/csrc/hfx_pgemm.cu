@@ -2,8 +2,10 @@
 // of Algorithm 3 as exact split-precision tcgen05 products, in one persistent
 // kernel per wave.
 //
-// A job is a 128-row x 64-column output tile over up to 20 K tiles of 32 (so
-// every digit-order group sum stays an exact f32 integer):
+// A job is a 128-row x 64-column output tile over all its K tiles of 32.
+// The MMAs hand the accumulator to the epilogue after every 20 K tiles (so
+// every digit-order group sum stays an exact f32 integer), and the epilogue
+// adds the chunks' recombined sums in int64 before it writes the tile once:
 //   Y job:    rows (b, G, g) of C_B transposed, columns al of V_AB, K = beta;
 //   D_AB job: rows (F, f) of C_A, columns (G, g) of P, K = (al, a).
 // Both operands are stored as KS balanced base-128 bf16 digits, one exponent
@@ -145,14 +147,17 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
       for (int j = blockIdx.x; j < njobs && !*abort_f; j += gridDim.x) {
         const Job jb = jobs[j];
         if (jb.nk == 0) continue;  // an empty job (a skipped candidate tile)
+        bool ok = true;
+        // K chunks of at most KT_CHUNK tiles, one accumulator handoff each
+        for (int k0 = 0; k0 < jb.nk && ok; k0 += KT_CHUNK) {
         if (hand >= 1 &&
             !umma::mbar_wait(&ctl->tempty, (uint32_t)((hand - 1) & 1), S.err, PG_WAIT)) {
-          *abort_f = 1;
+          ok = false;
           break;
         }
         umma::fence_after_sync();
-        bool ok = true;
-        for (int kt = 0; kt < jb.nk; ++kt, ++step) {
+        const int k1 = min(jb.nk, k0 + KT_CHUNK);
+        for (int kt = k0; kt < k1; ++kt, ++step) {
           const int s = (int)(step % PG_NST);
           if (!umma::mbar_wait(&ctl->full[s], (uint32_t)((step / PG_NST) & 1), S.err, PG_WAIT)) {
             ok = false;
@@ -170,15 +175,17 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
                 const uint64_t ad = umma::smem_desc(a0 + i * TM * TK * 2 + ks * 256, 128, 512);
                 const uint64_t bd =
                     umma::smem_desc(b0 + 4 * c * NT * TK * 2 + ks * 256, 128, 512);
-                // the two MMAs of digit 0 write every column of the first step
+                // the two MMAs of digit 0 write every column of a chunk's first step
                 umma::mma_bf16(tbase + (uint32_t)((i + 4 * c) * NT), ad, bd, idesc[n - 1],
-                               (kt | ks | i) ? 1u : 0u);
+                               ((kt - k0) | ks | i) ? 1u : 0u);
               }
           umma::mma_commit(&ctl->empty[s]);
         }
-        if (!ok) { *abort_f = 1; break; }
+        if (!ok) break;
         umma::mma_commit(&ctl->tfull);
         ++hand;
+        }
+        if (!ok) { *abort_f = 1; break; }
       }
       umma::mma_commit(&ctl->drain);
       umma::mbar_wait(&ctl->drain, 0, S.err, PG_WAIT);
@@ -192,8 +199,6 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
     for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
       const Job jb = jobs[j];
       if (jb.nk == 0) continue;  // no MMAs, no accumulator handoff
-      const uint32_t par = (uint32_t)(hand & 1);
-      ++hand;
       // everything this thread needs from global memory, before the wait, so
       // the dependent lookups overlap the job's MMAs
       const WorkItem it = S.items[jb.w];
@@ -242,27 +247,35 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         }
       }
 
-      const bool okw = umma::mbar_wait(&ctl->tfull, par, S.err, PG_WAIT);
-      if (umma::bar_any(!okw || *abort_f, PG_EPI * 32)) {
-        *abort_f = 1;
-        break;
-      }
-      umma::fence_after_sync();
+      // one accumulator handoff per K chunk; the chunks' exact sums add in int64
       long long Wv[32];
 #pragma unroll
       for (int i = 0; i < 32; ++i) Wv[i] = 0;
+      bool aborted = false;
+      for (int k0 = 0; k0 < jb.nk; k0 += KT_CHUNK) {
+        const uint32_t par = (uint32_t)(hand & 1);
+        ++hand;
+        const bool okw = umma::mbar_wait(&ctl->tfull, par, S.err, PG_WAIT);
+        if (umma::bar_any(!okw || *abort_f, PG_EPI * 32)) {
+          *abort_f = 1;
+          aborted = true;
+          break;
+        }
+        umma::fence_after_sync();
 #pragma unroll
-      for (int g = 0; g < KS; ++g) {
-        float v[32];
-        umma::tmem_ld32(tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(g * NT + c0), v);
-        const long long sc = 1ll << (7 * (KS - 1 - g));
+        for (int g = 0; g < KS; ++g) {
+          float v[32];
+          umma::tmem_ld32(tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(g * NT + c0), v);
+          const long long sc = 1ll << (7 * (KS - 1 - g));
 #pragma unroll
-        for (int i = 0; i < 32; ++i) Wv[i] += (long long)__float2int_rn(v[i]) * sc;
+          for (int i = 0; i < 32; ++i) Wv[i] += (long long)__float2int_rn(v[i]) * sc;
+        }
+        // the accumulator is free for the next chunk's or job's MMAs
+        umma::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&ctl->tempty);
       }
-      // the accumulator is free for the next job's MMAs
-      umma::fence_before_sync();
-      __syncwarp();
-      if (lane == 0) umma::mbar_arrive(&ctl->tempty);
+      if (aborted) break;
       if (!valid) continue;
 
       if (JOB == 0) {

@@ -307,11 +307,11 @@ __global__ void k_jobs_v4(SplitShared S, SplitWave W) {
   }
   if (!any) return;
   const int kt = S.kt4[it.a];
-  for (int k0 = 0; k0 < kt; k0 += KT_CHUNK) {
-    const int j = atomicAdd(W.njobs + 1, 1);
-    W.jobs4[j] = Job{W.w0 + wl, mt, nt, k0, min(KT_CHUNK, kt - k0)};
-    atomicAdd(W.tmacs + 1, (unsigned long long)TM * NT * TK * min(KT_CHUNK, kt - k0));
-  }
+  // one job over the whole K; the product hands the accumulator to the
+  // epilogue after every KT_CHUNK tiles (exact group sums)
+  const int j = atomicAdd(W.njobs + 1, 1);
+  W.jobs4[j] = Job{W.w0 + wl, mt, nt, 0, kt};
+  atomicAdd(W.tmacs + 1, (unsigned long long)TM * NT * TK * kt);
 }
 
 template <int KS>
