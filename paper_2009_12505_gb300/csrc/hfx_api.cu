@@ -618,10 +618,10 @@ hfx_status dz_prepare_meta(hfx_ctx *ctx, int ks) {
     naomax = std::max(naomax, ctx->nao[x]);
     naomin = std::min(naomin, ctx->nao[x]);
   }
-  // staged Y rows per tile: al rows spanned by 128 (al, a) rows, all b, the
-  // 16-column blocks of one G
+  // staged Y rows per tile: al rows spanned by 128 (al, a) rows, all b (plus
+  // 2 pairs of padding per al), the 16-column blocks of one G
   ctx->zc_shape = ZcPlanShape{kbmax, naomax,
-                              (127 / naomin + 2) * naomax * 16 * 8 * ((naomax + 15) / 16)};
+                              (127 / naomin + 2) * (naomax * 16 + 2) * 8 * ((naomax + 15) / 16)};
   CK(ctx->d_dz.reserve(std::max<int64_t>(off[nd], 1)));
   CK(ctx->d_dz_off.reserve(std::max<int64_t>(nd, 1)));
   CK(ctx->d_dij.reserve(std::max<int64_t>(2 * nd, 1)));

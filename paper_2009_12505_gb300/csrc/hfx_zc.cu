@@ -61,6 +61,9 @@ struct ZcGeo {
   static constexpr int OWN = 2 * 32 * 32 / ET;       // owned outputs per epilogue thread
 };
 constexpr long long ZC_WAIT = 2000000000ll;      // cycles per bounded wait
+// Staged Y rows of one al are padded by ZC_YPAD pairs, so the rows of the
+// few al a warp touches fall in different shared-memory banks.
+constexpr int ZC_YPAD = 2;
 
 __host__ __device__ __forceinline__ int kb_of(int nao) { return nao <= 16 ? 16 : 32; }
 
@@ -467,41 +470,52 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
     }
   } else if (warp == ZC_EPI + 2) {
     // ------------------------------------------------------------ Y loader
-    if (lane == 0 && ystage) {
+    if (ystage) {
       long long hand = 0;
-      for (int j = blockIdx.x; j < njobs && !*abort_f; j += gridDim.x) {
+      for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+        if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
         const ZcJob jb = W.zc_jobs[j];
         const WorkItem it = S.items[jb.w];
         const int wl = (int)(jb.w - W.w0);
         const int pA = S.nabf[it.a], na = S.nao[it.a], nb = S.nao[it.b];
         const int mtz = (pA * na + 127) / 128;
         const float2 *Y2 = reinterpret_cast<const float2 *>(W.scratch + W.y2_off[wl]);
-        for (int mt = 0; mt < mtz && !*abort_f; ++mt, ++hand) {
+        int ncbg[2] = {0, 0}, cbs[2] = {0, 0};
+        for (int b = 0; b < jb.nblk; ++b) {
+          const NbrEntry eg = S.nbr[it.gbase + jb.g[b]];
+          ncbg[b] = (S.nao[eg.other] + 15) / 16;
+          cbs[b] = S.kofs[it.gbase + jb.g[b]] / 16;
+        }
+        bool ok = true;
+        for (int mt = 0; mt < mtz; ++mt, ++hand) {
           const int tb = (int)(hand & 1);
           const long long use = hand >> 1;
-          if (use >= 1 &&
-              !umma::mbar_wait(&ctl->yempty[tb], (uint32_t)((use - 1) & 1), S.err, ZC_WAIT)) {
-            *abort_f = 1;
+          bool w = true;
+          if (lane == 0) {
+            if (use >= 1)
+              w = umma::mbar_wait(&ctl->yempty[tb], (uint32_t)((use - 1) & 1), S.err, ZC_WAIT);
+            w = w && !*abort_f;
+          }
+          if (!__shfl_sync(0xffffffffu, (int)w, 0)) {
+            if (lane == 0) *abort_f = 1;
+            ok = false;
             break;
           }
           const int al0 = mt * 128 / na, al1 = min(pA - 1, (mt * 128 + 127) / na);
           const int nal = al1 - al0 + 1;
-          uint32_t bytes = 0;
-          for (int b = 0; b < jb.nblk; ++b) {
-            const NbrEntry eg = S.nbr[it.gbase + jb.g[b]];
-            bytes += (uint32_t)(((S.nao[eg.other] + 15) / 16) * nal * nb * 16 * 8);
-          }
-          umma::mbar_arrive_expect_tx(&ctl->yfull[tb], bytes);
-          for (int b = 0; b < jb.nblk; ++b) {
-            const NbrEntry eg = S.nbr[it.gbase + jb.g[b]];
-            const int ncbg = (S.nao[eg.other] + 15) / 16, cb = S.kofs[it.gbase + jb.g[b]] / 16;
-            const uint32_t part = (uint32_t)(nal * nb * 16 * 8);
-            uint8_t *dst = ybuf + (tb * 2 + b) * cfg.ybytes;
-            for (int k = 0; k < ncbg; ++k)
-              umma::bulk_g2s(dst + k * part, zc_y_global(Y2, cb + k, pA, nb, al0), part,
-                             &ctl->yfull[tb]);
+          const uint32_t run = (uint32_t)(nb * 16 * 8);  // one al's [b][16] pairs
+          const int n0 = ncbg[0] * nal, ncopy = n0 + (jb.nblk > 1 ? ncbg[1] * nal : 0);
+          if (lane == 0) umma::mbar_arrive_expect_tx(&ctl->yfull[tb], (uint32_t)ncopy * run);
+          __syncwarp();
+          for (int q = lane; q < ncopy; q += 32) {
+            const int b = q < n0 ? 0 : 1;
+            const int r = q - (b ? n0 : 0), k = r / nal, al = al0 + r - k * nal;
+            uint8_t *dst = ybuf + (tb * 2 + b) * cfg.ybytes +
+                           ((int64_t)(k * nal + (al - al0)) * (nb * 16 + ZC_YPAD)) * 8;
+            umma::bulk_g2s(dst, zc_y_global(Y2, cbs[b] + k, pA, nb, al), run, &ctl->yfull[tb]);
           }
         }
+        if (!ok) break;
       }
     }
   } else if (warp == ZC_EPI + 1) {
@@ -617,12 +631,15 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
       float jh[ZC_OWN], jl[ZC_OWN];  // job sums of the owned outputs (f32 pairs)
 #pragma unroll
       for (int k = 0; k < ZC_OWN; ++k) { jh[k] = 0.f; jl[k] = 0.f; }
+      const int64_t czrow0 = S.cz_rowpre[it.a];
       const int own0 = jb.nblk > 0 ? na * nout[0] : 0;
       const int nown = own0 + (jb.nblk > 1 ? na * nout[1] : 0);
       bool aborted = false;
       for (int mt = 0; mt < mtz; ++mt, ++hand) {
         const int tb = (int)(hand & 1);
         const uint32_t par = (uint32_t)((hand >> 1) & 1);
+        // this row's exponent, read before the wait so its latency is hidden
+        const int eA = (mt * 128 + row < pA * na) ? S.cz_e[czrow0 + mt * 128 + row] : 0;
         bool okw = umma::mbar_wait(&ctl->tfull[tb], par, S.err, ZC_WAIT);
         if (okw && ystage) okw = umma::mbar_wait(&ctl->yfull[tb], par, S.err, ZC_WAIT);
         // the same decision in every epilogue warp
@@ -675,12 +692,11 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         auto yrow = [&](int k) -> const float2 * {
           if (ystage)
             return reinterpret_cast<const float2 *>(ybuf + (tb * 2 + hb) * cfg.ybytes) +
-                   ((int64_t)k * nal + (al - al0)) * nb * 16;
+                   ((int64_t)k * nal + (al - al0)) * (nb * 16 + ZC_YPAD);
           return zc_y_global(Y2, gcb[hb] + k, pA, nb, al);
         };
         // Z (f32 pairs) and the contraction with Y, four outputs at a time
         if (hb >= 0 && rvalid) {
-          const int eA = S.cz_e[S.cz_rowpre[it.a] + rowZ];
           const int no = nout[hb];
           const int cend = min(ZC_CW, ncv[hb] - c0);
           float2 z[ZC_CW];
