@@ -53,6 +53,25 @@ def workload_desc(wl) -> str:
             f"60 ABF per atom, C,D <= 16 bohr, V <= 20 bohr, theta = {THETA:g}, seed {wl.seed}")
 
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_zc<6,16,4,8> launch on the
+# 8-atom cell (30.64 GB + 1.28 GB) over its issued bf16 tensor flops (14.99 TFLOP),
+# captured from hfx_zc.cu with this sha256 prefix (see profiles/k_zc_split_si8.md)
+ZC_BYTES_PER_TENSOR_FLOP = (30.642044e9 + 1.275507e9) / 14.988985761792e12
+ZC_CAPTURED_SHA = "3094786fe5f16abd"
+
+
+def zc_traffic(tensor_flops_per_launch):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2009_12505_gb300", "csrc", "hfx_zc.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    if sha != ZC_CAPTURED_SHA:
+        return None
+    return ZC_BYTES_PER_TENSOR_FLOP * tensor_flops_per_launch
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -294,6 +313,7 @@ def run_gpu(args):
 
     # roofline of the kernel with the most device time
     top = max(kms, key=kms.get)
+    nwaves = max(1, int(st["n_waves"]))
     achieved = kfl[top] / (kms[top] / 1e3) / 1e12
     pk, src = peaks()
     tfl = st.get("kernel_tensor_flops", {}).get(top, 0.0)
@@ -323,7 +343,11 @@ def run_gpu(args):
                                "per build / its device time",
                 "tensor_issued": {"achieved": issued, "peak": bf16, "frac": issued / bf16,
                                   "unit": "TFLOP/s"},
-                "traffic": None}
+                "traffic": zc_traffic(tfl / nwaves) if top == "v1_DFG" else None,
+                "traffic_note": ("DRAM bytes per launch (one launch per wave): bytes per issued "
+                                 "tensor flop from one ncu capture of this kernel on the 8-atom "
+                                 "cell, times this launch's issued flops; null once the kernel "
+                                 "source differs from the captured one") if top == "v1_DFG" else None}
     roof["kernel_ms_per_step"] = {k: v / args.steps for k, v in kms.items()}
 
     cpu = None
@@ -341,8 +365,8 @@ def run_gpu(args):
                            "arithmetic": ("Y, D_FG, D_FB and D_AB products: exact products of "
                                           "7-bit bf16 digits on tcgen05 (f32 group sums, int64 "
                                           "recombination); Y contraction of the D_FG / D_FB "
-                                          "pieces in double-float; D-stage FP64; Sigma in "
-                                          "128-bit fixed point")
+                                          "pieces and P of the D_AB piece in double-float; "
+                                          "Sigma in 128-bit fixed point")
                            if prec == "ozaki" else "FP64 CUDA cores; Sigma in 128-bit fixed point",
                            "l2": f"inputs {sum(getattr(wl, k).data.nbytes for k in 'CVD') / 1e9:.2f} GB per cell (L2 is 129 MB)",
                            "parallelism": f"{world} independent cells" if world > 1 else "1 cell"},
