@@ -343,12 +343,13 @@ struct ZcSmem {
   uint64_t full[8], empty[8], tfull[2], tempty[2], yfull[2], yempty[2], drain;
   uint32_t tslot;
   int abort_f;
+  int stkb[8];  // K of the entry in each operand stage (16 or 32)
   int ecol[ZC_COLS];  // column exponents of the job (column group q at q * CW)
 };
 
 // Launch shape of k_zc: ybytes = shared bytes per staged Y block (0: the
-// epilogue reads Y from global memory), rs = row stride of the reduction
-// buffer (outputs per block, 16 or 32).
+// epilogue reads Y from global memory), rs = outputs per block held in the
+// reduction buffer (16 or 32; the buffer is [column group][output][row]).
 struct ZcCfg {
   int ybytes, rs;
 };
@@ -359,7 +360,66 @@ __device__ __forceinline__ const float2 *zc_y_global(const float2 *Y2, int cb, i
   return Y2 + (((int64_t)cb * pA + al) * nb) * 16;
 }
 
-template <int KS, int KBM, int NST, int EPI>
+// One operand stage's MMAs (K = KB): for each K step of 16 and block b, A
+// digit i times the block's B digits 0 .. KS - 1 - i stacked along N
+// (N = R (KS - i)) into TMEM columns b 16 KS + i R ..  Descriptors are the
+// stage's two base descriptors plus constant offsets (the 14-bit start field
+// cannot carry: shared addresses stay below 2^18).
+template <int KS, int KB>
+__device__ __forceinline__ void zc_stage_mmas(uint32_t a0, uint32_t b0, uint32_t dcol, int nblk,
+                                              int R, const uint32_t (&id16)[KS],
+                                              const uint32_t (&id32)[KS], bool first) {
+  constexpr uint32_t SBO = KB / 8 * 128;
+  const uint64_t adesc = umma::smem_desc(a0, 128, SBO);
+  const uint64_t bdesc = umma::smem_desc(b0, 128, SBO);
+#pragma unroll
+  for (int ks = 0; ks < KB / 16; ++ks)
+    for (int b = 0; b < nblk; ++b) {
+      const uint64_t bd = bdesc + (uint64_t)((b * (KS * 16 * KB * 2) + ks * 256) >> 4);
+#pragma unroll
+      for (int i = 0; i < KS; ++i) {
+        const uint64_t ad = adesc + (uint64_t)((i * (128 * KB * 2) + ks * 256) >> 4);
+        umma::mma_bf16(dcol + (uint32_t)(b * 16 * KS + i * R), ad, bd,
+                       R == 16 ? id16[i] : id32[i], (!first || ks || i) ? 1u : 0u);
+      }
+    }
+}
+
+// One row's contraction with Y in double-float: out[o] = sum_{c < cend} z[c]
+// yb[o so + c sc] for o < no, four outputs at a time; out[o] is stored at
+// outp[o 128] (the reduction buffer is output-major, so a warp's 32 rows
+// store to consecutive addresses).
+template <int CW>
+__device__ __forceinline__ void zc_contract(const float2 (&z)[CW], int cend,
+                                            const float2 *__restrict__ yb, int so, int sc, int no,
+                                            float2 *__restrict__ outp) {
+  const int no4 = no & ~3;
+  for (int o0 = 0; o0 < no4; o0 += 4) {
+    float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+    const float2 *y0 = yb + o0 * so;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+      if (c >= cend) break;
+      const float2 *yc = y0 + c * sc;
+      const float2 v[4] = {yc[0], yc[so], yc[2 * so], yc[3 * so]};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) df_mac(sh[u], sl[u], z[c], v[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) outp[(o0 + u) * 128] = make_float2(sh[u], sl[u]);
+  }
+  for (int o = no4; o < no; ++o) {
+    float sh = 0.f, sl = 0.f;
+#pragma unroll
+    for (int c = 0; c < CW; ++c) {
+      if (c >= cend) break;
+      df_mac(sh, sl, z[c], yb[o * so + c * sc]);
+    }
+    outp[o * 128] = make_float2(sh, sl);
+  }
+}
+
+template <int KS, int KBM, int NST, int EPI, bool YST>
 __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
     k_zc(SplitShared S, SplitWave W, ZcCfg cfg) {
   constexpr int ZC_EPI = EPI, ZC_NQ = ZcGeo<EPI>::NQ, ZC_CW = ZcGeo<EPI>::CW,
@@ -370,10 +430,9 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
   constexpr int SH = 7 * (KS + 1);
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t *ybuf = smem + NST * STG;                                     // [2][2][ybytes]
-  float2 *red = reinterpret_cast<float2 *>(ybuf + 4 * cfg.ybytes);     // [ZC_NQ][128][rs]
+  float2 *red = reinterpret_cast<float2 *>(ybuf + 4 * cfg.ybytes);     // [ZC_NQ][rs][128]
   ZcSmem *ctl = reinterpret_cast<ZcSmem *>(red + ZC_NQ * 128 * cfg.rs);
   volatile int *abort_f = &ctl->abort_f;
-  const bool ystage = cfg.ybytes > 0;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int njobs = W.njobs[2];
@@ -404,8 +463,10 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
 
   if (warp == ZC_EPI) {
     // ------------------------------------------------------------ A / B loader
-    // the whole warp walks the steps; lane 0 waits and arms the stage, then
-    // lane 0 copies the A tile and lanes 1 .. nblk KS one B digit tile each
+    // the whole warp walks the steps.  Lane l holds entry q0 + l of the job
+    // (fetched 32 at a time, off the per-stage path); lane 0 waits and arms
+    // the stage, then lane 0 copies the A tile and lanes 1 .. nblk one whole
+    // B block each
     long long step = 0;
     for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
       // one decision for the whole warp
@@ -421,44 +482,56 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         const int ncb = jb.piece[0] == 1 ? S.nao[S.nbr[it.gbase + jb.g[0]].other] : S.nao[it.b];
         R0 = ncb <= 16 ? 16 : 32;
       }
-      // this lane's copy: 0 = A, 1 .. nblk KS = (block, digit)
-      // lane 0 copies the A tile, lanes 1 .. nblk one whole B block each
       const int cb = lane - 1;
       const bool has_b = lane >= 1 && lane <= jb.nblk;
       const int Rl = jb.nblk == 1 ? R0 : 16;
+      ZcEnt mine = {0, 0, {-1, -1}};
+      int held = -1;  // q0 of the entries the lanes hold
       bool ok = true;
       for (int mt = 0; mt < mtz && ok; ++mt)
-        for (int q = 0; q < jb.nent; ++q, ++step) {
-          const ZcEnt en = W.zc_ents[jb.ent + q];
-          const int s = (int)(step % NST);
-          bool w = true;
-          if (lane == 0) {
-            if (step >= NST)
-              w = umma::mbar_wait(&ctl->empty[s], (uint32_t)((step / NST - 1) & 1), S.err,
-                                  ZC_WAIT);
-            w = w && !*abort_f;
+        for (int q0 = 0; q0 < jb.nent && ok; q0 += 32) {
+          if (held != q0) {
+            if (q0 + lane < jb.nent) mine = W.zc_ents[jb.ent + q0 + lane];
+            held = q0;
           }
-          w = __shfl_sync(0xffffffffu, (int)w, 0) != 0;
-          if (!w) {
-            if (lane == 0) *abort_f = 1;
-            ok = false;
-            break;
-          }
-          uint8_t *st = smem + s * STG;
-          const int kb = en.kb;
-          const uint32_t abytes = (uint32_t)(KS * 128 * kb * 2);
-          const uint32_t bbytes = (uint32_t)(KS * kb * 2) * (uint32_t)(jb.nblk * Rl);
-          if (lane == 0) umma::mbar_arrive_expect_tx(&ctl->full[s], abytes + bbytes);
-          __syncwarp();
-          if (lane == 0) {
-            umma::bulk_g2s(st, Abase + ((int64_t)mt * ktot + en.kofs) * KS * 128, abytes,
-                           &ctl->full[s]);
-          } else if (has_b) {
-            // B stage block-major: block b's KS digits of Rl rows x kb at b KS 16 kb
-            const int64_t dz = en.dz[cb];
-            const __nv_bfloat16 *src = dz >= 0 ? S.dz + dz : S.dzero;
-            umma::bulk_g2s(st + A_BYTES + cb * (KS * 16 * kb * 2), src,
-                           (uint32_t)(KS * Rl * kb * 2), &ctl->full[s]);
+          const int nq = min(32, jb.nent - q0);
+          for (int qq = 0; qq < nq; ++qq, ++step) {
+            const int kofs = __shfl_sync(0xffffffffu, mine.kofs, qq);
+            const int kb = __shfl_sync(0xffffffffu, mine.kb, qq);
+            const long long d0 = __shfl_sync(0xffffffffu, (long long)mine.dz[0], qq);
+            const long long d1 = __shfl_sync(0xffffffffu, (long long)mine.dz[1], qq);
+            const int s = (int)(step % NST);
+            bool w = true;
+            if (lane == 0) {
+              if (step >= NST)
+                w = umma::mbar_wait(&ctl->empty[s], (uint32_t)((step / NST - 1) & 1), S.err,
+                                    ZC_WAIT);
+              w = w && !*abort_f;
+            }
+            w = __shfl_sync(0xffffffffu, (int)w, 0) != 0;
+            if (!w) {
+              if (lane == 0) *abort_f = 1;
+              ok = false;
+              break;
+            }
+            uint8_t *st = smem + s * STG;
+            const uint32_t abytes = (uint32_t)(KS * 128 * kb * 2);
+            const uint32_t bbytes = (uint32_t)(KS * kb * 2) * (uint32_t)(jb.nblk * Rl);
+            if (lane == 0) {
+              ctl->stkb[s] = kb;  // read by the MMA issuer after the stage lands
+              umma::mbar_arrive_expect_tx(&ctl->full[s], abytes + bbytes);
+            }
+            __syncwarp();
+            if (lane == 0) {
+              umma::bulk_g2s(st, Abase + ((int64_t)mt * ktot + kofs) * KS * 128, abytes,
+                             &ctl->full[s]);
+            } else if (has_b) {
+              // B stage block-major: block b's KS digits of Rl rows x kb at b KS 16 kb
+              const int64_t dz = cb == 0 ? d0 : d1;
+              const __nv_bfloat16 *src = dz >= 0 ? S.dz + dz : S.dzero;
+              umma::bulk_g2s(st + A_BYTES + cb * (KS * 16 * kb * 2), src,
+                             (uint32_t)(KS * Rl * kb * 2), &ctl->full[s]);
+            }
           }
         }
     }
@@ -470,7 +543,7 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
     }
   } else if (warp == ZC_EPI + 2) {
     // ------------------------------------------------------------ Y loader
-    if (ystage) {
+    if constexpr (YST) {
       long long hand = 0;
       for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
         if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
@@ -529,6 +602,7 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         idesc16[i] = umma::idesc_bf16_f32(128, 16 * (KS - i));
         idesc32[i] = umma::idesc_bf16_f32(128, 32 * (KS - i));
       }
+      const uint32_t sbase = umma::smem_u32(smem);
       for (int j = blockIdx.x; j < njobs && !*abort_f; j += gridDim.x) {
         const ZcJob jb = W.zc_jobs[j];
         const WorkItem it = S.items[jb.w];
@@ -538,6 +612,7 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
           const int ncb = jb.piece[0] == 1 ? S.nao[S.nbr[it.gbase + jb.g[0]].other] : S.nao[it.b];
           R0 = ncb <= 16 ? 16 : 32;
         }
+        const int R = jb.nblk == 1 ? R0 : 16;
         for (int mt = 0; mt < mtz && !*abort_f; ++mt, ++hand) {
           const int tb = (int)(hand & 1);
           const long long use = hand >> 1;
@@ -550,30 +625,17 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
           const uint32_t dcol = tbase + (uint32_t)(tb * 256);
           bool ok = true;
           for (int q = 0; q < jb.nent; ++q, ++step) {
-            const int kb = W.zc_ents[jb.ent + q].kb;
             const int s = (int)(step % NST);
             if (!umma::mbar_wait(&ctl->full[s], (uint32_t)((step / NST) & 1), S.err, ZC_WAIT)) {
               ok = false;
               break;
             }
             umma::fence_after_sync();
-            const uint32_t a0 = umma::smem_u32(smem + s * STG);
-            const uint32_t b0 = a0 + A_BYTES;
-            const uint32_t sbo = (uint32_t)(kb / 8) * 128;
-            // block b (R rows): A digit i times B digits 0 .. KS - 1 - i of the block,
-            // into TMEM columns b R KS + (i + j) R + r
-            const int R = jb.nblk == 1 ? R0 : 16;
-            for (int ks = 0; ks < kb / 16; ++ks)
-              for (int b = 0; b < jb.nblk; ++b)
-#pragma unroll
-                for (int i = 0; i < KS; ++i) {
-                  const uint64_t ad =
-                      umma::smem_desc(a0 + i * (128 * kb * 2) + ks * 256, 128, sbo);
-                  const uint64_t bd =
-                      umma::smem_desc(b0 + b * (KS * 16 * kb * 2) + ks * 256, 128, sbo);
-                  umma::mma_bf16(dcol + (uint32_t)(b * 16 * KS + i * R), ad, bd,
-                                 R == 16 ? idesc16[i] : idesc32[i], (q | ks | i) ? 1u : 0u);
-                }
+            const uint32_t a0 = sbase + (uint32_t)(s * STG);
+            if (KBM == 16 || ctl->stkb[s] == 16)
+              zc_stage_mmas<KS, 16>(a0, a0 + A_BYTES, dcol, jb.nblk, R, idesc16, idesc32, q == 0);
+            else
+              zc_stage_mmas<KS, 32>(a0, a0 + A_BYTES, dcol, jb.nblk, R, idesc16, idesc32, q == 0);
             umma::mma_commit(&ctl->empty[s]);
           }
           if (!ok) { *abort_f = 1; break; }
@@ -597,16 +659,22 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
       const int pA = S.nabf[it.a], na = S.nao[it.a], nb = S.nao[it.b];
       const int mtz = (pA * na + 127) / 128;
       const float2 *Y2 = reinterpret_cast<const float2 *>(W.scratch + W.y2_off[wl]);
-      // blocks: rows, outputs, columns
-      int Rb[2] = {16, 16}, nout[2] = {0, 0}, ncv[2] = {0, 0}, gat[2] = {0, 0}, gcb[2] = {0, 0};
-      for (int b = 0; b < jb.nblk; ++b) {
-        const NbrEntry eg = S.nbr[it.gbase + jb.g[b]];
-        const int ng = S.nao[eg.other];
-        gat[b] = eg.other;
-        gcb[b] = S.kofs[it.gbase + jb.g[b]] / 16;
-        ncv[b] = jb.piece[b] == 1 ? ng : nb;
-        nout[b] = jb.piece[b] == 1 ? nb : ng;
-        Rb[b] = ncv[b] <= 16 ? 16 : 32;
+      // blocks 0 and 1: Z columns, outputs, TMEM rows per order, 16-column
+      // block of G's Y columns (scalars: no dynamically indexed arrays)
+      int ncv0 = 0, ncv1 = 0, nout0 = 0, nout1 = 0, R0b = 16, gcb0 = 0, gcb1 = 0;
+      const int pc0 = jb.piece[0], pc1 = jb.piece[1];
+      if (jb.nblk > 0) {
+        const int G = S.nbr[it.gbase + jb.g[0]].other, ng = S.nao[G];
+        gcb0 = S.kofs[it.gbase + jb.g[0]] / 16;
+        ncv0 = pc0 == 1 ? ng : nb;
+        nout0 = pc0 == 1 ? nb : ng;
+        R0b = ncv0 <= 16 ? 16 : 32;
+      }
+      if (jb.nblk > 1) {
+        const int G = S.nbr[it.gbase + jb.g[1]].other, ng = S.nao[G];
+        gcb1 = S.kofs[it.gbase + jb.g[1]] / 16;
+        ncv1 = pc1 == 1 ? ng : nb;
+        nout1 = pc1 == 1 ? nb : ng;
       }
       // block and columns [c0, c0 + ZC_CW) of column group q (two 16-column
       // blocks: the first half of the groups each; one block: all groups below R)
@@ -614,26 +682,40 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         const int jc = q * ZC_CW;
         if (jb.nblk == 2) { cq = jc & 15; return jc >> 4; }
         cq = jc;
-        return jc < Rb[0] ? 0 : -1;
+        return jc < R0b ? 0 : -1;
       };
       int c0 = 0;
       const int hb = group_block(hf, c0);
-      const int piece = hb >= 0 ? jb.piece[hb] : 0;
+      const bool h1 = hb == 1;
+      const int piece = hb >= 0 ? (h1 ? pc1 : pc0) : 0;
+      const int Rh = h1 ? 16 : R0b;
+      const int noh = h1 ? nout1 : nout0, ncvh = h1 ? ncv1 : ncv0, gcbh = h1 ? gcb1 : gcb0;
+      // column groups feeding block 0 and block 1 (bit q)
+      unsigned qm0 = 0, qm1 = 0;
+#pragma unroll
+      for (int q = 0; q < ZC_NQ; ++q) {
+        int cq;
+        const int bq = group_block(q, cq);
+        qm0 |= (bq == 0 ? 1u : 0u) << q;
+        qm1 |= (bq == 1 ? 1u : 0u) << q;
+      }
       // column exponents of this warp's columns (shared by the group's warps;
       // the previous job's last reads are behind the tile barriers)
       const int *ecol = ctl->ecol + hf * ZC_CW;
       if (q4 == 0 && lane < ZC_CW) {
-        const int at = hb >= 0 ? (piece == 1 ? gat[hb] : it.b) : 0;
+        const int at = hb >= 0 ? (piece == 1 ? S.nbr[it.gbase + (h1 ? jb.g[1] : jb.g[0])].other
+                                             : it.b)
+                               : 0;
         const int cc = c0 + lane;
-        ctl->ecol[hf * ZC_CW + lane] = (hb >= 0 && cc < ncv[hb])
+        ctl->ecol[hf * ZC_CW + lane] = (hb >= 0 && cc < ncvh)
                                   ? row_exponent((long long)S.de[S.aoff[at] + cc]) : -1000;
       }
       float jh[ZC_OWN], jl[ZC_OWN];  // job sums of the owned outputs (f32 pairs)
 #pragma unroll
       for (int k = 0; k < ZC_OWN; ++k) { jh[k] = 0.f; jl[k] = 0.f; }
       const int64_t czrow0 = S.cz_rowpre[it.a];
-      const int own0 = jb.nblk > 0 ? na * nout[0] : 0;
-      const int nown = own0 + (jb.nblk > 1 ? na * nout[1] : 0);
+      const int own0 = na * nout0;
+      const int nown = own0 + na * nout1;
       bool aborted = false;
       for (int mt = 0; mt < mtz; ++mt, ++hand) {
         const int tb = (int)(hand & 1);
@@ -641,7 +723,9 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         // this row's exponent, read before the wait so its latency is hidden
         const int eA = (mt * 128 + row < pA * na) ? S.cz_e[czrow0 + mt * 128 + row] : 0;
         bool okw = umma::mbar_wait(&ctl->tfull[tb], par, S.err, ZC_WAIT);
-        if (okw && ystage) okw = umma::mbar_wait(&ctl->yfull[tb], par, S.err, ZC_WAIT);
+        if constexpr (YST) {
+          if (okw) okw = umma::mbar_wait(&ctl->yfull[tb], par, S.err, ZC_WAIT);
+        }
         // the same decision in every epilogue warp
         if (umma::bar_any(!okw || *abort_f, ZC_ET)) {
           *abort_f = 1;
@@ -660,7 +744,6 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         if (hb >= 0) {
           // the digit-order groups, three loads in flight per wait
           // block hb's order g occupies TMEM columns hb 16 KS + g R .. + R
-          const int Rh = Rb[hb];
           const uint32_t ta = tbase + (uint32_t)(tb * 256) + ((uint32_t)(q4 * 32) << 16) +
                               (uint32_t)(hb * 16 * KS + c0);
 #pragma unroll
@@ -690,75 +773,62 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         if (lane == 0) umma::mbar_arrive(&ctl->tempty[tb]);
         // Y rows of this thread's al in 16-column block k of G: [b][16] pairs
         auto yrow = [&](int k) -> const float2 * {
-          if (ystage)
+          if constexpr (YST)
             return reinterpret_cast<const float2 *>(ybuf + (tb * 2 + hb) * cfg.ybytes) +
                    ((int64_t)k * nal + (al - al0)) * (nb * 16 + ZC_YPAD);
-          return zc_y_global(Y2, gcb[hb] + k, pA, nb, al);
+          else
+            return zc_y_global(Y2, gcbh + k, pA, nb, al);
         };
-        // Z (f32 pairs) and the contraction with Y, four outputs at a time
+        // Z (f32 pairs) and the contraction with Y
         if (hb >= 0 && rvalid) {
-          const int no = nout[hb];
-          const int cend = min(ZC_CW, ncv[hb] - c0);
+          const int cend = min(ZC_CW, ncvh - c0);
           float2 z[ZC_CW];
 #pragma unroll
           for (int c = 0; c < ZC_CW; ++c)
             z[c] = c < cend ? pair_i64(Wv[c], eA + ecol[c] - SH) : make_float2(0.f, 0.f);
-          float2 *rr = red + ((int64_t)hf * 128 + row) * rs;
-          const int cs = piece == 1 ? 1 : 16;
-          // y of output o at column c: y[c cs].  Piece 1: out b = o,
-          // Y[al][b][G, g = c0 + c]; piece 2: out g = o, Y[al][b = c0 + c][G, g]
-          auto ybase = [&](int o) -> const float2 * {
-            return piece == 1 ? yrow(c0 >> 4) + o * 16 + (c0 & 15)
-                              : yrow(o >> 4) + c0 * 16 + (o & 15);
-          };
-          const int no4 = no & ~3;
-          for (int o = no4; o < no; ++o) {
-            const float2 *y = ybase(o);
-            float sh = 0.f, sl = 0.f;
-#pragma unroll
-            for (int c = 0; c < ZC_CW; ++c) {
-              if (c >= cend) break;
-              df_mac(sh, sl, z[c], y[c * cs]);
-            }
-            rr[o] = make_float2(sh, sl);
-          }
-          for (int o0 = 0; o0 < no4; o0 += 4) {
-            float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
-            const float2 *yp[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) yp[u] = ybase(o0 + u);
-#pragma unroll
-            for (int c = 0; c < ZC_CW; ++c) {
-              if (c >= cend) break;
-#pragma unroll
-              for (int u = 0; u < 4; ++u) df_mac(sh[u], sl[u], z[c], yp[u][c * cs]);
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) rr[o0 + u] = make_float2(sh[u], sl[u]);
+          float2 *rr = red + (int64_t)hf * rs * 128 + row;
+          if (piece == 1) {
+            // out b: Y[al][b][G, g = c0 + c]
+            zc_contract<ZC_CW>(z, cend, yrow(c0 >> 4) + (c0 & 15), 16, 1, noh, rr);
+          } else {
+            // out g: Y[al][b = c0 + c][G, g], one 16-column block of g at a time
+            for (int k = 0; 16 * k < noh; ++k)
+              zc_contract<ZC_CW>(z, cend, yrow(k) + c0 * 16, 1, 16, min(16, noh - 16 * k),
+                                 rr + 16 * k * 128);
           }
         }
         __syncwarp();
-        if (lane == 0) umma::mbar_arrive(&ctl->yempty[tb]);
+        if constexpr (YST) {
+          if (lane == 0) umma::mbar_arrive(&ctl->yempty[tb]);
+        }
         asm volatile("bar.sync 1, %0;" ::"r"(ZC_ET) : "memory");
         // owners: (block, a, o) summed over the tile's rows (al, a) and the
         // block's column groups, in a fixed order
         const int r0 = mt * 128, rend = min(pA * na, r0 + 128);
+        const int ph = r0 % na;
 #pragma unroll
         for (int k = 0; k < ZC_OWN; ++k) {
           const int idx = et + k * ZC_ET;
           if (idx >= nown) break;
-          const int b = idx < own0 ? 0 : 1;
-          const int rem = idx - (b ? own0 : 0);
-          const int a = rem / nout[b], o = rem - a * nout[b];
-          int r = r0 + ((a - r0 % na) % na + na) % na;
+          const bool b1 = idx >= own0;
+          const int rem = idx - (b1 ? own0 : 0);
+          const int o = rem / na, a = rem - o * na;  // consecutive owners: consecutive a
+          const unsigned qm = b1 ? qm1 : qm0;
+          int d = a - ph;
+          if (d < 0) d += na;
           float h = jh[k], l = jl[k];
-          for (; r < rend; r += na) {
-            const int lr = r - r0;
 #pragma unroll
-            for (int q = 0; q < ZC_NQ; ++q) {
-              int cq;
-              if (group_block(q, cq) == b) df_add(h, l, red[((int64_t)q * 128 + lr) * rs + o]);
+          for (int q = 0; q < ZC_NQ; ++q) {
+            if (!((qm >> q) & 1u)) continue;
+            const float2 *rq = red + ((int64_t)q * rs + o) * 128;
+            int lr = d;
+            // two rows per step: both loads in flight before the adds
+            for (; lr + na < rend - r0; lr += 2 * na) {
+              const float2 v0 = rq[lr], v1 = rq[lr + na];
+              df_add(h, l, v0);
+              df_add(h, l, v1);
             }
+            if (lr < rend - r0) df_add(h, l, rq[lr]);
           }
           jh[k] = h;
           jl[k] = l;
@@ -771,14 +841,16 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
       for (int k = 0; k < ZC_OWN; ++k) {
         const int idx = et + k * ZC_ET;
         if (idx >= nown) break;
-        const int b = idx < own0 ? 0 : 1;
-        const int rem = idx - (b ? own0 : 0);
-        const int a = rem / nout[b], o = rem - a * nout[b];
-        const NbrEntry eg = S.nbr[it.gbase + jb.g[b]];
+        const bool b1 = idx >= own0;
+        const int nob = b1 ? nout1 : nout0;
+        const int rem = idx - (b1 ? own0 : 0);
+        const int o = rem / na, a = rem - o * na;
+        const int pcb = b1 ? pc1 : pc0;
+        const NbrEntry eg = S.nbr[it.gbase + (b1 ? jb.g[1] : jb.g[0])];
         const int nG0 = it.n[0] + eg.n[0], nG1 = it.n[1] + eg.n[1], nG2 = it.n[2] + eg.n[2];
         int64_t t0, t1 = -1;
-        const bool mir = S.sym && (jb.piece[b] == 2 || it.role == 1);
-        if (jb.piece[b] == 1) {
+        const bool mir = S.sym && (pcb == 2 || it.role == 1);
+        if (pcb == 1) {
           t0 = dh_find(S.shash, hk_pack(it.a, it.b, it.n[0], it.n[1], it.n[2]));
           if (mir) t1 = dh_find(S.shash, hk_pack(it.b, it.a, -it.n[0], -it.n[1], -it.n[2]));
         } else {
@@ -790,7 +862,7 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
           continue;
         }
         const float2 v = make_float2(jh[k], jl[k]);
-        fx_add_df(S.acc + 2 * (t0 + (int64_t)a * nout[b] + o), v, true);
+        fx_add_df(S.acc + 2 * (t0 + (int64_t)a * nob + o), v, true);
         if (t1 >= 0) fx_add_df(S.acc + 2 * (t1 + (int64_t)o * na + a), v, true);
       }
     }
@@ -828,14 +900,14 @@ cudaError_t zc_run_t(const SplitShared &S, const SplitWave &W, const ZcPlanShape
   constexpr int T8 = ZcGeo<8>::THREADS;
   if (P.kbmax <= 16) {
     if (ZC_STAGE_Y && smem_of(4, 16, P.ybytes, 2) <= kMax)
-      return launch(k_zc<KS, 16, 4, 8>, T8, 4, 16, P.ybytes, 2);
+      return launch(k_zc<KS, 16, 4, 8, true>, T8, 4, 16, P.ybytes, 2);
     if (ZC_STAGE_Y && smem_of(3, 16, P.ybytes, 2) <= kMax)
-      return launch(k_zc<KS, 16, 3, 8>, T8, 3, 16, P.ybytes, 2);
-    return launch(k_zc<KS, 16, 3, 8>, T8, 3, 16, 0, 2);
+      return launch(k_zc<KS, 16, 3, 8, true>, T8, 3, 16, P.ybytes, 2);
+    return launch(k_zc<KS, 16, 3, 8, false>, T8, 3, 16, 0, 2);
   }
   if (ZC_STAGE_Y && smem_of(2, 32, P.ybytes, 2) <= kMax)
-    return launch(k_zc<KS, 32, 2, 8>, T8, 2, 32, P.ybytes, 2);
-  return launch(k_zc<KS, 32, 2, 8>, T8, 2, 32, 0, 2);
+    return launch(k_zc<KS, 32, 2, 8, true>, T8, 2, 32, P.ybytes, 2);
+  return launch(k_zc<KS, 32, 2, 8, false>, T8, 2, 32, 0, 2);
 }
 
 template <int KS>
