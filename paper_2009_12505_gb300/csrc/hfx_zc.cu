@@ -419,6 +419,55 @@ __device__ __forceinline__ void zc_contract(const float2 (&z)[CW], int cend,
   }
 }
 
+// The same contraction with packed f32x2 arithmetic: lane 0 sums the even
+// columns, lane 1 the odd ones, and the two double-float sums are added at the
+// end.  zh / nzh / nzl hold column pairs (2j, 2j + 1) of the high words, their
+// negatives and the negated low words, zero from column cend on (an odd last
+// pair repeats its column's Y, times zero).  Y words are loaded one by one
+// into the two lanes.  P1: so = 16, sc = 1; otherwise so = 1, sc = 16.
+template <int NP, bool P1>
+__device__ __forceinline__ void zc_contract2(const uint64_t (&zh)[NP], const uint64_t (&nzh)[NP],
+                                             const uint64_t (&nzl)[NP], int cend,
+                                             const float2 *__restrict__ yb, int no,
+                                             float2 *__restrict__ outp) {
+  const float *yf = reinterpret_cast<const float *>(yb);
+  constexpr int SO = P1 ? 32 : 2, SC = P1 ? 2 : 32;  // float words per output, column
+  const int npair = (cend + 1) >> 1;
+  auto put = [&](int o, uint64_t h2, uint64_t l2) {
+    const float2 h = f2_un(h2), l = f2_un(l2);
+    float sh = h.x, sl = l.x;
+    df_add(sh, sl, make_float2(h.y, l.y));
+    outp[o * 128] = make_float2(sh, sl);
+  };
+  const int no4 = no & ~3;
+  for (int o0 = 0; o0 < no4; o0 += 4) {
+    uint64_t sh[4] = {0, 0, 0, 0}, sl[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      if (j >= npair) break;
+      const int d1 = 2 * j + 1 < cend ? SC : 0;  // the pair's second column
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float *y = yf + (o0 + u) * SO + 2 * j * SC;
+        df_mac2(sh[u], sl[u], zh[j], nzh[j], nzl[j], f2_pk(y[0], y[d1]), f2_pk(y[1], y[d1 + 1]));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) put(o0 + u, sh[u], sl[u]);
+  }
+  for (int o = no4; o < no; ++o) {
+    uint64_t sh = 0, sl = 0;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      if (j >= npair) break;
+      const int d1 = 2 * j + 1 < cend ? SC : 0;
+      const float *y = yf + o * SO + 2 * j * SC;
+      df_mac2(sh, sl, zh[j], nzh[j], nzl[j], f2_pk(y[0], y[d1]), f2_pk(y[1], y[d1 + 1]));
+    }
+    put(o, sh, sl);
+  }
+}
+
 template <int KS, int KBM, int NST, int EPI, bool YST>
 __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
     k_zc(SplitShared S, SplitWave W, ZcCfg cfg) {
@@ -772,6 +821,7 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         __syncwarp();
         if (lane == 0) umma::mbar_arrive(&ctl->tempty[tb]);
         // Y rows of this thread's al in 16-column block k of G: [b][16] pairs
+        // Y rows of this thread's al in 16-column block k of G: [b][16] pairs
         auto yrow = [&](int k) -> const float2 * {
           if constexpr (YST)
             return reinterpret_cast<const float2 *>(ybuf + (tb * 2 + hb) * cfg.ybytes) +
@@ -782,19 +832,43 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         // Z (f32 pairs) and the contraction with Y
         if (hb >= 0 && rvalid) {
           const int cend = min(ZC_CW, ncvh - c0);
-          float2 z[ZC_CW];
-#pragma unroll
-          for (int c = 0; c < ZC_CW; ++c)
-            z[c] = c < cend ? pair_i64(Wv[c], eA + ecol[c] - SH) : make_float2(0.f, 0.f);
           float2 *rr = red + (int64_t)hf * rs * 128 + row;
-          if (piece == 1) {
-            // out b: Y[al][b][G, g = c0 + c]
-            zc_contract<ZC_CW>(z, cend, yrow(c0 >> 4) + (c0 & 15), 16, 1, noh, rr);
+          if constexpr (YST) {
+            // Z as column pairs for the packed contraction
+            constexpr int NP = ZC_CW / 2;
+            uint64_t zh[NP], nzh[NP], nzl[NP];
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+              const float2 z0 = 2 * j < cend ? pair_i64(Wv[2 * j], eA + ecol[2 * j] - SH)
+                                             : make_float2(0.f, 0.f);
+              const float2 z1 = 2 * j + 1 < cend
+                                    ? pair_i64(Wv[2 * j + 1], eA + ecol[2 * j + 1] - SH)
+                                    : make_float2(0.f, 0.f);
+              zh[j] = f2_pk(z0.x, z1.x);
+              nzh[j] = f2_pk(-z0.x, -z1.x);
+              nzl[j] = f2_pk(-z0.y, -z1.y);
+            }
+            if (piece == 1) {
+              // out b: Y[al][b][G, g = c0 + c]
+              zc_contract2<NP, true>(zh, nzh, nzl, cend, yrow(c0 >> 4) + (c0 & 15), noh, rr);
+            } else {
+              // out g: Y[al][b = c0 + c][G, g], one 16-column block of g at a time
+              for (int k = 0; 16 * k < noh; ++k)
+                zc_contract2<NP, false>(zh, nzh, nzl, cend, yrow(k) + c0 * 16,
+                                        min(16, noh - 16 * k), rr + 16 * k * 128);
+            }
           } else {
-            // out g: Y[al][b = c0 + c][G, g], one 16-column block of g at a time
-            for (int k = 0; 16 * k < noh; ++k)
-              zc_contract<ZC_CW>(z, cend, yrow(k) + c0 * 16, 1, 16, min(16, noh - 16 * k),
-                                 rr + 16 * k * 128);
+            float2 z[ZC_CW];
+#pragma unroll
+            for (int c = 0; c < ZC_CW; ++c)
+              z[c] = c < cend ? pair_i64(Wv[c], eA + ecol[c] - SH) : make_float2(0.f, 0.f);
+            if (piece == 1) {
+              zc_contract<ZC_CW>(z, cend, yrow(c0 >> 4) + (c0 & 15), 16, 1, noh, rr);
+            } else {
+              for (int k = 0; 16 * k < noh; ++k)
+                zc_contract<ZC_CW>(z, cend, yrow(k) + c0 * 16, 1, 16, min(16, noh - 16 * k),
+                                   rr + 16 * k * 128);
+            }
           }
         }
         __syncwarp();

@@ -174,4 +174,54 @@ __device__ __forceinline__ void df_mac(float &sh, float &sl, float2 a, float2 b)
   sl = __fadd_rn(sl, __fadd_rn(err, e));
 }
 
+// Two f32 lanes in one 64-bit register pair, with the packed f32x2
+// arithmetic of sm_100 and later: each lane is rounded to nearest exactly as
+// the scalar operation, so error-free transformations carry over lane-wise.
+__device__ __forceinline__ uint64_t f2_pk(float x, float y) {
+  uint64_t d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(x), "f"(y));
+  return d;
+}
+__device__ __forceinline__ float2 f2_un(uint64_t v) {
+  float2 r;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(v));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_add(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// df_mac in both lanes: (sh, sl) += (ah, al) (bh, bl), given na = -ah and
+// nl = -al.  The product's error term is carried negated
+// (ne = p - ah bh - ah bl - al bh), which gives the same roundings as df_mac.
+__device__ __forceinline__ void df_mac2(uint64_t &sh, uint64_t &sl, uint64_t ah, uint64_t na,
+                                        uint64_t nl, uint64_t bh, uint64_t bl) {
+  const uint64_t p = f2_mul(ah, bh);
+  uint64_t ne = f2_fma(na, bh, p);
+  ne = f2_fma(na, bl, ne);
+  ne = f2_fma(nl, bh, ne);
+  const uint64_t s = f2_add(sh, p);
+  const uint64_t bb = f2_sub(s, sh);
+  const uint64_t err = f2_add(f2_sub(sh, f2_sub(s, bb)), f2_sub(p, bb));
+  sh = s;
+  sl = f2_add(sl, f2_sub(err, ne));
+}
+
 }  // namespace split
