@@ -821,7 +821,6 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         __syncwarp();
         if (lane == 0) umma::mbar_arrive(&ctl->tempty[tb]);
         // Y rows of this thread's al in 16-column block k of G: [b][16] pairs
-        // Y rows of this thread's al in 16-column block k of G: [b][16] pairs
         auto yrow = [&](int k) -> const float2 * {
           if constexpr (YST)
             return reinterpret_cast<const float2 *>(ybuf + (tb * 2 + hb) * cfg.ybytes) +
