@@ -247,10 +247,15 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         }
       }
 
-      // one accumulator handoff per K chunk; the chunks' exact sums add in int64
-      long long Wv[32];
+      // one accumulator handoff per K chunk.  D_AB: the chunks' exact sums add
+      // in int64.  Y: the order groups (exact f32 integers times powers of two)
+      // add in double-float, columns (2p, 2p + 1) in the two f32x2 lanes.
+      long long Wv[JOB == 1 ? 32 : 1];
+      uint64_t ds[JOB == 0 ? 16 : 1], dr[JOB == 0 ? 16 : 1];
 #pragma unroll
-      for (int i = 0; i < 32; ++i) Wv[i] = 0;
+      for (int i = 0; i < (JOB == 1 ? 32 : 1); ++i) Wv[i] = 0;
+#pragma unroll
+      for (int p = 0; p < (JOB == 0 ? 16 : 1); ++p) ds[p] = dr[p] = 0;
       bool aborted = false;
       for (int k0 = 0; k0 < jb.nk; k0 += KT_CHUNK) {
         const uint32_t par = (uint32_t)(hand & 1);
@@ -266,9 +271,17 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         for (int g = 0; g < KS; ++g) {
           float v[32];
           umma::tmem_ld32(tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(g * NT + c0), v);
-          const long long sc = 1ll << (7 * (KS - 1 - g));
+          if constexpr (JOB == 0) {
+            const float cg = __int_as_float((7 * (KS - 1 - g) + 127) << 23);
+            const uint64_t c2 = f2_pk(cg, cg);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) Wv[i] += (long long)__float2int_rn(v[i]) * sc;
+            for (int p = 0; p < 16; ++p)
+              df_acc2(ds[p], dr[p], f2_mul(f2_pk(v[2 * p], v[2 * p + 1]), c2));
+          } else {
+            const long long sc = 1ll << (7 * (KS - 1 - g));
+#pragma unroll
+            for (int i = 0; i < 32; ++i) Wv[i] += (long long)__float2int_rn(v[i]) * sc;
+          }
         }
         // the accumulator is free for the next chunk's or job's MMAs
         umma::fence_before_sync();
@@ -278,18 +291,25 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
       if (aborted) break;
       if (!valid) continue;
 
-      if (JOB == 0) {
+      if constexpr (JOB == 0) {
         // Y[al][b * ncol + col(G,g)] (FP64) and Y2 (f32 pairs) in 16-column
         // blocks [cb][al][b][16], cb = kofs(G) / 16 + g / 16
         double *Y = W.scratch + W.y_off[wl];
         float2 *Y2 = reinterpret_cast<float2 *>(W.scratch + W.y2_off[wl]);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int al = jb.nt * NT + c0 + i;
+        for (int p = 0; p < 16; ++p) {
+          const int al = jb.nt * NT + c0 + 2 * p;
           if (al >= pA) break;
-          const int e = ea + eb_p[c0 + i] - SH;
-          if (need64) Y[(int64_t)al * nrowY + yrow] = scaled_i64(Wv[i], e);
-          if (y2row >= 0) Y2[y2row + (int64_t)al * nbY * 16] = pair_i64(Wv[i], e);
+          float2 o[2];
+          df_fin2(ds[p], dr[p], ea + eb_p[c0 + 2 * p] - SH, ea + eb_p[c0 + 2 * p + 1] - SH, o[0],
+                  o[1]);
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            if (al + u >= pA) break;
+            if (need64)
+              Y[(int64_t)(al + u) * nrowY + yrow] = (double)o[u].x + (double)o[u].y;
+            if (y2row >= 0) Y2[y2row + (int64_t)(al + u) * nbY * 16] = o[u];
+          }
         }
       } else {
         // Sigma_FG blocks: rows (F,f) of atom A, columns (G,g) of atom B

@@ -787,9 +787,12 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         const int al = rvalid ? rowZ / na : 0;
         const int al0 = mt * 128 / na, al1 = min(pA - 1, (mt * 128 + 127) / na);
         const int nal = al1 - al0 + 1;
-        long long Wv[ZC_CW];
+        // the order groups (exact f32 integers) summed in double-float, columns
+        // (2j, 2j + 1) in the two f32x2 lanes
+        constexpr int NP = ZC_CW / 2;
+        uint64_t ds[NP], dr[NP];
 #pragma unroll
-        for (int c = 0; c < ZC_CW; ++c) Wv[c] = 0;
+        for (int j = 0; j < NP; ++j) ds[j] = dr[j] = 0;
         if (hb >= 0) {
           // the digit-order groups, three loads in flight per wait
           // block hb's order g occupies TMEM columns hb 16 KS + g R .. + R
@@ -810,10 +813,13 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
 #pragma unroll
             for (int u = 0; u < 3; ++u) {
               if (g0 + u >= KS) break;
-              const int sh = 7 * (KS - 1 - g0 - u);
+              const float cg = __int_as_float((7 * (KS - 1 - g0 - u) + 127) << 23);
+              const uint64_t c2 = f2_pk(cg, cg);
 #pragma unroll
-              for (int c = 0; c < ZC_CW; ++c)
-                Wv[c] += (long long)__float2int_rn(__uint_as_float(r[u][c])) * (1ll << sh);
+              for (int j = 0; j < NP; ++j)
+                df_acc2(ds[j], dr[j],
+                        f2_mul(f2_pk(__uint_as_float(r[u][2 * j]), __uint_as_float(r[u][2 * j + 1])),
+                               c2));
             }
           }
         }
@@ -832,20 +838,23 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         if (hb >= 0 && rvalid) {
           const int cend = min(ZC_CW, ncvh - c0);
           float2 *rr = red + (int64_t)hf * rs * 128 + row;
+          // Z = (order-group sum) 2^(eA + ecol - SH) as f32 pairs; zero from cend on
+          float2 zp[NP][2];
+#pragma unroll
+          for (int j = 0; j < NP; ++j) {
+            df_fin2(ds[j], dr[j], eA + ecol[2 * j] - SH, eA + ecol[2 * j + 1] - SH, zp[j][0],
+                    zp[j][1]);
+            if (2 * j >= cend) zp[j][0] = make_float2(0.f, 0.f);
+            if (2 * j + 1 >= cend) zp[j][1] = make_float2(0.f, 0.f);
+          }
           if constexpr (YST) {
             // Z as column pairs for the packed contraction
-            constexpr int NP = ZC_CW / 2;
             uint64_t zh[NP], nzh[NP], nzl[NP];
 #pragma unroll
             for (int j = 0; j < NP; ++j) {
-              const float2 z0 = 2 * j < cend ? pair_i64(Wv[2 * j], eA + ecol[2 * j] - SH)
-                                             : make_float2(0.f, 0.f);
-              const float2 z1 = 2 * j + 1 < cend
-                                    ? pair_i64(Wv[2 * j + 1], eA + ecol[2 * j + 1] - SH)
-                                    : make_float2(0.f, 0.f);
-              zh[j] = f2_pk(z0.x, z1.x);
-              nzh[j] = f2_pk(-z0.x, -z1.x);
-              nzl[j] = f2_pk(-z0.y, -z1.y);
+              zh[j] = f2_pk(zp[j][0].x, zp[j][1].x);
+              nzh[j] = f2_pk(-zp[j][0].x, -zp[j][1].x);
+              nzl[j] = f2_pk(-zp[j][0].y, -zp[j][1].y);
             }
             if (piece == 1) {
               // out b: Y[al][b][G, g = c0 + c]
@@ -859,8 +868,7 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
           } else {
             float2 z[ZC_CW];
 #pragma unroll
-            for (int c = 0; c < ZC_CW; ++c)
-              z[c] = c < cend ? pair_i64(Wv[c], eA + ecol[c] - SH) : make_float2(0.f, 0.f);
+            for (int c = 0; c < ZC_CW; ++c) z[c] = zp[c >> 1][c & 1];
             if (piece == 1) {
               zc_contract<ZC_CW>(z, cend, yrow(c0 >> 4) + (c0 & 15), 16, 1, noh, rr);
             } else {

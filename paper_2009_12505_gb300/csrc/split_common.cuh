@@ -224,4 +224,33 @@ __device__ __forceinline__ void df_mac2(uint64_t &sh, uint64_t &sl, uint64_t ah,
   sl = f2_add(sl, f2_sub(err, ne));
 }
 
+// Lane-wise double-float accumulation (s, r) += t: the sum s + t is split
+// exactly (TwoSum), its error added to r.
+__device__ __forceinline__ void df_acc2(uint64_t &s, uint64_t &r, uint64_t t) {
+  const uint64_t s1 = f2_add(s, t);
+  const uint64_t bb = f2_sub(s1, s);
+  const uint64_t err = f2_add(f2_sub(s, f2_sub(s1, bb)), f2_sub(t, bb));
+  s = s1;
+  r = f2_add(r, err);
+}
+
+// (s, r) of lanes 0 and 1 renormalised (TwoSum) and scaled by 2^e0, 2^e1 in
+// two exact steps each; exponents below -250 are taken as -250 (|s| < 2^64,
+// so those values fall below the f32 range anyway).  Requires e <= 100.
+__device__ __forceinline__ void df_fin2(uint64_t s, uint64_t r, int e0, int e1, float2 &o0,
+                                        float2 &o1) {
+  uint64_t h = 0, l = 0;
+  df_acc2(h, l, s);
+  df_acc2(h, l, r);
+  e0 = max(e0, -250);
+  e1 = max(e1, -250);
+  const int a0 = e0 / 2, a1 = e1 / 2;
+  const uint64_t f1 = f2_pk(__int_as_float((a0 + 127) << 23), __int_as_float((a1 + 127) << 23));
+  const uint64_t f2 =
+      f2_pk(__int_as_float((e0 - a0 + 127) << 23), __int_as_float((e1 - a1 + 127) << 23));
+  const float2 H = f2_un(f2_mul(f2_mul(h, f1), f2)), L = f2_un(f2_mul(f2_mul(l, f1), f2));
+  o0 = make_float2(H.x, L.x);
+  o1 = make_float2(H.y, L.y);
+}
+
 }  // namespace split
