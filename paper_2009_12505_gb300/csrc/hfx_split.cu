@@ -181,13 +181,6 @@ __global__ void __launch_bounds__(PD_THREADS) k_pdig(SplitShared S, SplitWave W)
     Dp[i] = make_float2(h, __double2float_rn(d - (double)h));
   }
   __syncthreads();
-  auto put = [&](int r, int c, const int (&d)[KS]) {
-    const int rt = r / NT, rr = r - rt * NT, kt = c / TK, cc = c - kt * TK;
-    __nv_bfloat16 *base = out + ((int64_t)(rt * ktiles + kt) * KS) * NT * TK;
-#pragma unroll
-    for (int sd = 0; sd < KS; ++sd)
-      base[(int64_t)sd * NT * TK + tile_off(rr, cc)] = __int2bfloat16_rn(d[sd]);
-  };
   const int gc = max(1, min(32, PD_SMEM_PAIRS / K));
   for (int g0 = 0; g0 < ng; g0 += gc) {
     const int gn = min(gc, ng - g0);
@@ -214,21 +207,41 @@ __global__ void __launch_bounds__(PD_THREADS) k_pdig(SplitShared S, SplitWave W)
       }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < gn * KT; idx += PD_THREADS) {
-      const int gi = idx / KT, c = idx - gi * KT;
+    // eight consecutive K of one row per thread: each digit plane gets one
+    // 16-byte store (the eight are adjacent in the core-matrix tile)
+    const int KT8 = KT / 8;
+    for (int idx = threadIdx.x; idx < gn * KT8; idx += PD_THREADS) {
+      const int gi = idx / KT8, c8 = (idx - gi * KT8) * 8;
       const int e = es[gi];
-      long long X = 0;
-      if (c < K && e > -200) {  // below 2^-200 the row is dropped
-        // scale by 2^(7 KS - e) (|value| < 2^(e - 1)) in two exact steps
-        const int sft = 7 * KS - e, s1 = sft / 2, s2 = sft - s1;
-        const float f1 = __int_as_float((s1 + 127) << 23), f2 = __int_as_float((s2 + 127) << 23);
-        const float2 v = Ps[gi * K + c];
-        X = __float2ll_rn(__fmul_rn(__fmul_rn(v.x, f1), f2)) +
-            __float2ll_rn(__fmul_rn(__fmul_rn(v.y, f1), f2));
+      // scale by 2^(7 KS - e) (|value| < 2^(e - 1)) in two exact steps
+      const int sft = 7 * KS - e, s1 = sft / 2, s2 = sft - s1;
+      const float f1 = __int_as_float((s1 + 127) << 23), f2 = __int_as_float((s2 + 127) << 23);
+      uint32_t pk[KS][4];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int c = c8 + k;
+        long long X = 0;
+        if (c < K && e > -200) {  // below 2^-200 the row is dropped
+          const float2 v = Ps[gi * K + c];
+          X = __float2ll_rn(__fmul_rn(__fmul_rn(v.x, f1), f2)) +
+              __float2ll_rn(__fmul_rn(__fmul_rn(v.y, f1), f2));
+        }
+        int d[KS];
+        to_digits_i64<KS>(X, d);
+#pragma unroll
+        for (int sd = 0; sd < KS; ++sd) {
+          const uint32_t b = __bfloat16_as_ushort(__int2bfloat16_rn(d[sd]));
+          if (k & 1) pk[sd][k >> 1] |= b << 16;
+          else pk[sd][k >> 1] = b;
+        }
       }
-      int d[KS];
-      to_digits_i64<KS>(X, d);
-      put(eg.aopre + g0 + gi, c, d);
+      const int r = eg.aopre + g0 + gi;
+      const int rt = r / NT, rr = r - rt * NT, kt = c8 / TK, cc = c8 - kt * TK;
+      __nv_bfloat16 *base = out + ((int64_t)(rt * ktiles + kt) * KS) * NT * TK + tile_off(rr, cc);
+#pragma unroll
+      for (int sd = 0; sd < KS; ++sd)
+        *reinterpret_cast<uint4 *>(base + (int64_t)sd * NT * TK) =
+            make_uint4(pk[sd][0], pk[sd][1], pk[sd][2], pk[sd][3]);
     }
     __syncthreads();
   }
