@@ -708,6 +708,17 @@ SplitShared split_shared(hfx_ctx *ctx) {
   S.colG = ctx->d_colG.p;
   S.coloff = ctx->d_coloff.p;
   S.nsm = ctx->nsm;
+  {
+    // P of the D_AB piece: at least one g column of P (K = nabf nao of A) and
+    // of the staged Y (nabf(A) nao(B) rows) at a time
+    int64_t kmax = 0, pmax = 0, nmax = 0;
+    for (int x = 0; x < ctx->natoms; ++x) {
+      kmax = std::max<int64_t>(kmax, (int64_t)ctx->nabf[x] * ctx->nao[x]);
+      pmax = std::max<int64_t>(pmax, ctx->nabf[x]);
+      nmax = std::max<int64_t>(nmax, ctx->nao[x]);
+    }
+    S.pd_pairs = (int32_t)std::max<int64_t>(6400, kmax + pmax * nmax);
+  }
   return S;
 }
 

@@ -148,11 +148,10 @@ __global__ void k_slice_v(SplitShared S) {
 // adds only surviving (F, G) blocks, and each output column depends on its
 // own B row alone, so whatever those rows hold never reaches Sigma.
 constexpr int PD_THREADS = 256;
-constexpr int PD_SMEM_PAIRS = 3072;  // 24 KB: a few g columns at a time
 
 template <int KS>
 __global__ void __launch_bounds__(PD_THREADS) k_pdig(SplitShared S, SplitWave W) {
-  extern __shared__ float2 Ps[];  // [gc][K]
+  extern __shared__ float2 Ps[];  // [gc][K], then the staged Y [al][b][gc]
   __shared__ int es[32];
   __shared__ float2 Dp[32 * 32];  // D_AB as f32 pairs
   const int64_t t = blockIdx.x;
@@ -181,17 +180,34 @@ __global__ void __launch_bounds__(PD_THREADS) k_pdig(SplitShared S, SplitWave W)
     Dp[i] = make_float2(h, __double2float_rn(d - (double)h));
   }
   __syncthreads();
-  const int gc = max(1, min(32, PD_SMEM_PAIRS / K));
+  // g columns per pass: 4 (one 32-byte sector of each Y2 row), else fewer
+  const int nrow = pA * nb;
+  const int cap = S.pd_pairs;  // >= K + nrow for every pair (sized on the host)
+  const int gc = 4 * (K + nrow) <= cap ? 4 : 2 * (K + nrow) <= cap ? 2 : 1;
+  float2 *Ys = Ps + gc * K;
   for (int g0 = 0; g0 < ng; g0 += gc) {
     const int gn = min(gc, ng - g0);
+    // stage Y[al][b][g0 .. g0 + gc) (Y2 layout [cb][al][b][16]; g0 is a multiple
+    // of gc, so the gc pairs stay inside one 16-column block and one sector)
+    const float2 *yb = Y2 + ((int64_t)(cbG + (g0 >> 4)) * pA * nb) * 16 + (g0 & 15);
+    for (int r = threadIdx.x; r < nrow; r += PD_THREADS) {
+      const float2 *src = yb + (int64_t)r * 16;
+      if (gc == 4) {
+        const float4 u0 = reinterpret_cast<const float4 *>(src)[0];
+        const float4 u1 = reinterpret_cast<const float4 *>(src)[1];
+        reinterpret_cast<float4 *>(Ys + r * 4)[0] = u0;
+        reinterpret_cast<float4 *>(Ys + r * 4)[1] = u1;
+      } else {
+        for (int k = 0; k < gc; ++k) Ys[r * gc + k] = src[k];
+      }
+    }
+    __syncthreads();
     for (int idx = threadIdx.x; idx < gn * K; idx += PD_THREADS) {
       const int gi = idx / K, kap = idx - gi * K, al = kap / na, a = kap - al * na;
-      const int g = g0 + gi;
-      // Y2 layout [cb][al][b][16]
-      const float2 *y = Y2 + (((int64_t)(cbG + (g >> 4)) * pA + al) * nb) * 16 + (g & 15);
+      const float2 *y = Ys + al * nb * gc + gi;
       const float2 *d = Dp + a * nb;
       float sh = 0.f, sl = 0.f;
-      for (int b = 0; b < nb; ++b) df_mac(sh, sl, d[b], y[b * 16]);
+      for (int b = 0; b < nb; ++b) df_mac(sh, sl, d[b], y[b * gc]);
       Ps[gi * K + kap] = make_float2(sh, sl);
     }
     __syncthreads();
@@ -347,7 +363,9 @@ cudaError_t wave_t(const SplitShared &S, const SplitWave &W, int phase, cudaStre
   }
   // phase 1: P digits, D_AB jobs, D_AB products
   if (W.h_pgcand > 0) {
-    const int smem = PD_SMEM_PAIRS * (int)sizeof(float2);
+    // P and the staged Y of up to 4 g columns (50 KB for 13 NAO / 60 ABF)
+    const int smem = S.pd_pairs * (int)sizeof(float2);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(k_pdig<KS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          smem);
     if (e != cudaSuccess) return e;

@@ -80,6 +80,7 @@ struct SplitShared {
   const int32_t *aoff;             // per atom: first (atom, ao) index
   int64_t h_nd;                    // D blocks
   int32_t nsm;                     // SMs of the device (persistent grids)
+  int32_t pd_pairs;                // f32 pairs of k_pdig's dynamic shared memory
   const int16_t *colG;             // per (atom, column): local index of its neighbour entry
   const int64_t *coloff;           // per atom: first column in colG
   int64_t h_cy_rows, h_c4_rows, h_v_rows, h_cz_rows;  // host copies of the row totals
