@@ -207,6 +207,17 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
       const int16_t *ea_p, *eb_p;
       pg_operands<KS, JOB>(S, W, jb, it, Ab, Bb, ea_p, eb_p);
       const int ea = ea_p[row];
+      // Y: the column exponents too (pairs of int16), before the wait
+      uint32_t ebp[JOB == 0 ? 16 : 1];
+      if constexpr (JOB == 0) {
+        const int ncl = S.nabf[it.a] - (jb.nt * NT + c0);  // valid columns of this warp
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+          const uint32_t e0 = 2 * p < ncl ? (uint16_t)eb_p[c0 + 2 * p] : 0u;
+          const uint32_t e1 = 2 * p + 1 < ncl ? (uint16_t)eb_p[c0 + 2 * p + 1] : 0u;
+          ebp[p] = e0 | (e1 << 16);
+        }
+      }
       bool valid;
       // Y job: row (b, G, g) of Y, Y2 row, FP64 need
       int64_t yrow = 0, y2row = -1, nrowY = 0;
@@ -301,8 +312,8 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
           const int al = jb.nt * NT + c0 + 2 * p;
           if (al >= pA) break;
           float2 o[2];
-          df_fin2(ds[p], dr[p], ea + eb_p[c0 + 2 * p] - SH, ea + eb_p[c0 + 2 * p + 1] - SH, o[0],
-                  o[1]);
+          df_fin2(ds[p], dr[p], ea + (int)(int16_t)(ebp[p] & 0xFFFFu) - SH,
+                  ea + (int)(int16_t)(ebp[p] >> 16) - SH, o[0], o[1]);
 #pragma unroll
           for (int u = 0; u < 2; ++u) {
             if (al + u >= pA) break;
