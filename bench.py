@@ -53,11 +53,11 @@ def workload_desc(wl) -> str:
             f"60 ABF per atom, C,D <= 16 bohr, V <= 20 bohr, theta = {THETA:g}, seed {wl.seed}")
 
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one k_zc<6,16,4,8> launch on the
-# 8-atom cell (30.64 GB + 1.28 GB) over its issued bf16 tensor flops (14.99 TFLOP),
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_zc<6,16,4,8,1> launch on the
+# 8-atom cell (30.71 GB + 0.52 GB) over its issued bf16 tensor flops (14.99 TFLOP),
 # captured from hfx_zc.cu with this sha256 prefix (see profiles/k_zc_split_si8.md)
-ZC_BYTES_PER_TENSOR_FLOP = (30.642044e9 + 1.275507e9) / 14.988985761792e12
-ZC_CAPTURED_SHA = "3094786fe5f16abd"
+ZC_BYTES_PER_TENSOR_FLOP = (30.712555e9 + 0.524244e9) / 14.988985761792e12
+ZC_CAPTURED_SHA = "df35d929b4ed74d7"
 
 
 def zc_traffic(tensor_flops_per_launch):
