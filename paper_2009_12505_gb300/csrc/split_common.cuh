@@ -49,25 +49,6 @@ __device__ __forceinline__ void to_digits_i64(long long X, int (&d)[KS]) {
   d[0] = (int)X;
 }
 
-// W * 2^e as a double using integer operations only (round to nearest).
-__device__ __forceinline__ double scaled_i64(long long W, int e) {
-  if (W == 0) return 0.0;
-  const unsigned long long sgn = W < 0 ? 0x8000000000000000ull : 0ull;
-  unsigned long long m = W < 0 ? (unsigned long long)(-W) : (unsigned long long)W;
-  const int nbits = 64 - __clzll(m);
-  int ex = nbits - 1 + e;
-  if (nbits > 53) {
-    const int sh = nbits - 53;
-    m = (m + (1ull << (sh - 1))) >> sh;
-    if (m >> 53) { m >>= 1; ++ex; }
-  } else {
-    m <<= (53 - nbits);
-  }
-  if (ex < -1000) return 0.0;
-  return __longlong_as_double(sgn | ((unsigned long long)(ex + 1023) << 52) |
-                              (m & ((1ull << 52) - 1)));
-}
-
 // Add W * 2^e to a fixed-point Sigma element (hi: 2^-32 units, lo: 2^-64
 // units) with integer arithmetic; |W 2^e| < 2^31.
 __device__ __forceinline__ void fx_add_scaled(unsigned long long *hi_lo, long long W, int e) {
@@ -101,30 +82,6 @@ __device__ __forceinline__ int entry_of(const NbrEntry *nbr, int64_t base, int n
 
 
 namespace split {
-
-// (hi, lo) f32 pair of W * 2^e with integer conversions only; hi + lo carries
-// about 48 significant bits.  Requires e <= 100.
-__device__ __forceinline__ float2 pair_i64(long long W, int e) {
-  // |W 2^e| < 2^(63 + e): below 2^-126 it is dropped
-  if (W == 0 || e < -189) return make_float2(0.f, 0.f);
-  // W = a 2^48 + b 2^24 + c with b, c in [0, 2^24): each part exact in f32,
-  // so only 32-bit conversions are needed
-  const float fa = __fmul_rn(__int2float_rn((int)(W >> 48)), 281474976710656.f);
-  const float fb = __fmul_rn(__int2float_rn((int)((W >> 24) & 0xFFFFFF)), 16777216.f);
-  const float fc = __int2float_rn((int)(W & 0xFFFFFF));
-  // (s, t) = fa + fb exactly, then t + fc and a final renormalisation
-  const float s = __fadd_rn(fa, fb);
-  const float bb = __fsub_rn(s, fa);
-  const float t = __fadd_rn(__fsub_rn(fa, __fsub_rn(s, bb)), __fsub_rn(fb, bb));
-  const float l0 = __fadd_rn(t, fc);
-  const float h = __fadd_rn(s, l0);
-  const float hb = __fsub_rn(h, s);
-  const float l = __fadd_rn(__fsub_rn(s, __fsub_rn(h, hb)), __fsub_rn(l0, hb));
-  // multiply by 2^e in two steps so neither factor leaves the normal range
-  const int e1 = e / 2, e2 = e - e1;
-  const float s1 = __int_as_float((e1 + 127) << 23), s2 = __int_as_float((e2 + 127) << 23);
-  return make_float2(__fmul_rn(__fmul_rn(h, s1), s2), __fmul_rn(__fmul_rn(l, s1), s2));
-}
 
 // (sh, sl) += (bh, bl): error-free sum of the high parts, low parts added.
 __device__ __forceinline__ void df_add(float &sh, float &sl, float2 b) {
