@@ -57,7 +57,7 @@ def workload_desc(wl) -> str:
 # 8-atom cell (30.71 GB + 0.52 GB) over its issued bf16 tensor flops (14.99 TFLOP),
 # captured from hfx_zc.cu with this sha256 prefix (see profiles/k_zc_split_si8.md)
 ZC_BYTES_PER_TENSOR_FLOP = (30.712555e9 + 0.524244e9) / 14.988985761792e12
-ZC_CAPTURED_SHA = "df35d929b4ed74d7"
+ZC_CAPTURED_SHA = "1cef9b93b0076611"
 
 
 def zc_traffic(tensor_flops_per_launch):

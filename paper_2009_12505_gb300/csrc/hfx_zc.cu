@@ -26,8 +26,8 @@
 // R i adds every product of digit order i + j into the block's TMEM columns
 // [R (i + j), R (i + j + 1)): KS MMAs per block and K step instead of
 // KS (KS + 1) / 2 narrow ones, and one bulk copy per block (the D tiles are
-// stored digit-major).  The epilogue recombines the order groups into one
-// exact int64 per element.
+// stored digit-major).  The epilogue adds the order groups (exact f32
+// integers times powers of two) in packed double-float arithmetic.
 //
 // Roles (one CTA per SM, persistent over a static round-robin job split):
 // warp 8 streams A and B tiles with 1-D bulk copies into a ring of shared
@@ -35,8 +35,9 @@
 // copies the Y rows of each tile (f32 pairs, laid out [16-column block][al]
 // [b][16] so a tile's rows are contiguous) into one of two shared buffers;
 // warps 0-7 read an accumulator (warp w: TMEM lanes 32 (w % 4).., columns
-// 16 (w / 4)..), turn Z into f32 pairs, contract with Y in double-float
-// arithmetic, reduce over al through shared memory in a fixed order and add
+// 16 (w / 4)..), turn Z into f32 pairs, contract with Y in packed (f32x2)
+// double-float arithmetic, reduce over al through shared memory in a fixed
+// order and add
 // each finished block to the fixed-point Sigma (and its mirror for Hermitian
 // inputs) once per job.  Every wait is bounded; on expiry the kernel records
 // HFX_DEV_ERR_TIMEOUT, drains its copies and MMAs, frees TMEM and returns.
