@@ -5,7 +5,8 @@
 // A job is a 128-row x 64-column output tile over all its K tiles of 32.
 // The MMAs hand the accumulator to the epilogue after every 20 K tiles (so
 // every digit-order group sum stays an exact f32 integer), and the epilogue
-// adds the chunks' recombined sums in int64 before it writes the tile once:
+// adds up the chunks before it writes the tile once: in int64 for D_AB, in
+// packed double-float for Y (whose result is an f32 pair anyway):
 //   Y job:    rows (b, G, g) of C_B transposed, columns al of V_AB, K = beta;
 //   D_AB job: rows (F, f) of C_A, columns (G, g) of P, K = (al, a).
 // Both operands are stored as KS balanced base-128 bf16 digits, one exponent
@@ -17,9 +18,9 @@
 // copies each K tile's A and B digits (lanes 0 and 1, 1-D bulk copies) into a
 // ring of shared stages; warp 9 issues the MMAs into the TMEM accumulator;
 // warps 0-7 (TMEM lanes 32 (w % 4).., columns 32 (w / 4)..) drain the
-// accumulator into exact int64 sums, release it to the next job's MMAs, and
-// then write Y (FP64 and f32 pairs) or add the surviving Sigma_FG blocks to
-// the fixed-point Sigma.  Every wait is bounded: on expiry the kernel records
+// accumulator into those sums, release it to the next job's MMAs, and then
+// write Y (f32 pairs, and FP64 where read) or add the surviving Sigma_FG
+// blocks to the fixed-point Sigma.  Every wait is bounded: on expiry the kernel records
 // HFX_DEV_ERR_TIMEOUT, drains its copies and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 
