@@ -363,10 +363,11 @@ def run_gpu(args):
                 "config": {"workload": workload_desc(wl), "theta": THETA, "prec": prec,
                            "nslices": nsl if prec == "ozaki" else None,
                            "arithmetic": ("Y, D_FG, D_FB and D_AB products: exact products of "
-                                          "7-bit bf16 digits on tcgen05 (f32 group sums, int64 "
-                                          "recombination); Y contraction of the D_FG / D_FB "
-                                          "pieces and P of the D_AB piece in double-float; "
-                                          "Sigma in 128-bit fixed point")
+                                          "7-bit bf16 digits on tcgen05 (exact f32 group sums "
+                                          "per digit order, added in int64 for D_AB and in "
+                                          "double-float for Y, D_FG and D_FB); Y contraction "
+                                          "of the D_FG / D_FB pieces and P of the D_AB piece "
+                                          "in double-float; Sigma in 128-bit fixed point")
                            if prec == "ozaki" else "FP64 CUDA cores; Sigma in 128-bit fixed point",
                            "l2": f"inputs {sum(getattr(wl, k).data.nbytes for k in 'CVD') / 1e9:.2f} GB per cell (L2 is 129 MB)",
                            "parallelism": f"{world} independent cells" if world > 1 else "1 cell"},
