@@ -44,8 +44,11 @@
  *                 bits; does not meet 1e-8 Ha, kept for comparison);
  *   HFX_OZAKI  -- the same with nslices digits (4..6) and every digit product
  *                 of order <= nslices - 1: each order's f32 tensor-core sum is
- *                 exact, the orders are recombined in int64 (6 digits: about
- *                 41 significant bits per operand row).
+ *                 exact; the orders are added in int64 where a product goes
+ *                 straight to Sigma, and in double-float (f32 pairs, rounding
+ *                 below the digit truncation) where it feeds a further
+ *                 contraction (6 digits: about 41 significant bits per operand
+ *                 row).
  * Sigma is accumulated in 128-bit fixed point (integer adds, 2^-64 Ha
  * resolution) and converted to FP64 once, and E_X is summed from it in a
  * fixed order, so results are bitwise reproducible run to run in every mode.
