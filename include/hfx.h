@@ -139,8 +139,8 @@ hfx_status hfx_clear(hfx_ctx *ctx, char which);
  *   nslices  digits per operand: HFX_OZAKI 4..6 (0 = 6), HFX_BF16X3 0 or 2,
  *            HFX_FP64 ignored
  *   ex_out   receives E_X in Ha (host pointer), may be NULL
- * Errors: HFX_E_STATE (no C, V or D set), HFX_E_ARG, HFX_E_NOMEM, HFX_E_CUDA,
- *         HFX_E_TIMEOUT.
+ * Errors: HFX_E_STATE (no C, V or D set), HFX_E_ARG (also: a split mode with
+ *         an atom of more than 32 NAOs), HFX_E_NOMEM, HFX_E_CUDA, HFX_E_TIMEOUT.
  */
 hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices, double *ex_out);
 
