@@ -45,6 +45,91 @@ def test_atom_costs_follow_pair_weights():
     np.testing.assert_allclose(cost, ref)
 
 
+def _blobs():
+    rng = np.random.default_rng(3)
+    centres = np.array([[0.0, 0.0, 0.0], [12.0, 0.0, 0.0], [0.0, 12.0, 0.0], [0.0, 0.0, 12.0]])
+    return np.concatenate([rng.normal(c, 0.5, (15, 3)) for c in centres])
+
+
+def test_kmeans_recovers_separated_clusters():
+    pts = _blobs()
+    labels, _ = sharding.kmeans(pts, 4)
+    groups = [set(labels[15 * b:15 * (b + 1)].tolist()) for b in range(4)]
+    assert all(len(g) == 1 for g in groups)            # each blob in one category
+    assert len(set.union(*groups)) == 4                # four different categories
+    np.testing.assert_array_equal(labels, sharding.kmeans(pts, 4)[0])
+
+
+def test_kmeans_stops_at_a_fixed_point():
+    """Algorithm 7's loop ends when no atom changes category: then every atom
+    is nearest its own centre and every centre is its atoms' mean."""
+    rng = np.random.default_rng(5)
+    pts = rng.uniform(0, 20, (80, 3))
+    labels, centres = sharding.kmeans(pts, 6)
+    d = ((pts[:, None, :] - centres[None, :, :]) ** 2).sum(-1)
+    np.testing.assert_array_equal(labels, np.argmin(d, axis=1))
+    for j in range(6):
+        np.testing.assert_allclose(centres[j], pts[labels == j].mean(0))
+
+
+def _chain(natoms=48):
+    s = synth.custom("chain", 1.0, 100000, [[3 * i, 0, 0] for i in range(natoms)], 4, 6)
+    ck = np.array([(i, j, *n) for i, j, n, _ in s.pairs_within(7.0)])
+    vk = np.array([(i, j, *n) for i, j, n, _ in s.pairs_within(9.0)])
+    return s, ck, vk
+
+
+def test_sigma_fg_footprint_matches_brute_force():
+    s, ck, vk = _chain(12)
+    owner = np.arange(12) % 3
+    nbr = {a: [(int(f), tuple(int(x) for x in k[2:])) for f, k in zip(ck[ck[:, 0] == a][:, 1],
+                                                                 ck[ck[:, 0] == a])]
+           for a in range(12)}
+    for r in range(3):
+        seen = set()
+        for A, B, *nB in vk.tolist():
+            if owner[A] != r:
+                continue
+            for F, nF in nbr[A]:
+                for G, nG in nbr[B]:
+                    seen.add((F, G) + tuple(nB[c] + nG[c] - nF[c] for c in range(3)))
+        assert sharding.sigma_fg_footprint(owner, ck, vk, 3)[r] == len(seen)
+
+
+def test_kmeans_distribution_needs_fewer_sigma_blocks():
+    """Sec. III.D / IV: clustering each rank's central atoms shrinks the union
+    of the F and G neighbourhoods, so a rank touches fewer Sigma_FG blocks than
+    under machine scheduling or an equal-count random distribution."""
+    s, ck, vk = _chain()
+    costs = sharding.atom_costs(s.natoms, ck, vk)
+    for R in (2, 4, 8):
+        km = sharding.kmeans_owner(s.positions, R)
+        rnd = np.random.default_rng(R).permutation(np.arange(s.natoms) % R)
+        lp = sharding.lpt(costs, R)
+        f = lambda o: sharding.sigma_fg_footprint(o, ck, vk, R).max()
+        assert f(km) < f(rnd) and f(km) < f(lp)
+
+
+def test_machine_scheduling_balances_an_inhomogeneous_cell():
+    """Sec. IV: on an inhomogeneous system, Delta t_max / Delta t_av under
+    machine scheduling stays near 1 while a random equal-count distribution
+    drifts upward with the number of ranks."""
+    rng = np.random.default_rng(7)
+    dense = rng.integers(0, 8, (40, 3))           # a compact cluster
+    sparse = rng.integers(0, 60, (40, 3)) + 20    # scattered atoms
+    grid = np.unique(np.concatenate([dense, sparse]), axis=0)
+    s = synth.custom("mixed", 1.0, 100000, grid, 4, 6)
+    ck = np.array([(i, j, *n) for i, j, n, _ in s.pairs_within(6.0)])
+    vk = np.array([(i, j, *n) for i, j, n, _ in s.pairs_within(8.0)])
+    costs = sharding.atom_costs(s.natoms, ck, vk)
+    for R in (2, 4, 8):
+        lp = sharding.load_ratio(sharding.lpt(costs, R), costs, R)
+        rnd = max(sharding.load_ratio(np.random.default_rng(t).permutation(
+            np.arange(s.natoms) % R), costs, R) for t in range(5))
+        assert lp <= 1.1     # the paper reports below 1.2 at 32 processes
+        assert lp < rnd
+
+
 def test_fx_roundtrip_matches_library_encoding():
     x = np.array([0.0, 1.5, -2.25, 65.98757923056736, -1e-9, 3.0e-17])
     np.testing.assert_allclose(sharding.fx_decode(sharding.fx_encode(x)), x, rtol=0, atol=2**-63)
@@ -61,7 +146,7 @@ def _words_for_atoms(wl, theta, atoms, keyindex, offs, nelem):
     return acc
 
 
-def _worker(rank, world, port, q):
+def _worker(rank, world, port, q, scheme="lpt"):
     import torch.distributed as dist
     os.environ["MASTER_ADDR"] = "127.0.0.1"
     os.environ["MASTER_PORT"] = str(port)
@@ -73,7 +158,11 @@ def _worker(rank, world, port, q):
         keys = sorted(sig)
         keyindex = {k: i for i, k in enumerate(keys)}
         offs = np.concatenate([[0], np.cumsum([sig[k].size for k in keys])])
-        owner = sharding.lpt(sharding.atom_costs(wl.system.natoms, wl.C.keys, wl.V.keys), world)
+        if scheme == "kmeans":
+            owner = sharding.kmeans_owner(wl.system.positions, world)
+        else:
+            owner = sharding.lpt(sharding.atom_costs(wl.system.natoms, wl.C.keys, wl.V.keys),
+                                 world)
         mine = {a for a in range(wl.system.natoms) if owner[a] == rank}
         words = _words_for_atoms(wl, theta, mine, keyindex, offs, int(offs[-1]))
         total = sharding.all_reduce_words(words)
@@ -91,14 +180,15 @@ def _tiny3():
     return synth.make_workload(s, 3.2, 4.2, 3.0, seed=6)
 
 
-def test_gloo_world2_exchange_bitwise():
+@pytest.mark.parametrize("scheme", ["lpt", "kmeans"])
+def test_gloo_world2_exchange_bitwise(scheme):
     import torch.multiprocessing as mp
     with socket.socket() as sk:
         sk.bind(("127.0.0.1", 0))
         port = sk.getsockname()[1]
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q, scheme)) for r in range(2)]
     for p in procs:
         p.start()
     for p in procs:
