@@ -306,6 +306,41 @@ hfx_status hfx_selftest_timeout(int64_t limit_cycles, int64_t *waited_cycles);
 /* Message for the last failing call on ctx (never NULL; "" when none). */
 const char *hfx_last_error(const hfx_ctx *ctx);
 
+/*
+ * Real-space density-matrix blocks from Kohn-Sham eigenvectors (Sec. II,
+ * Eq. DM_realspace), in FP64 on the GPU.  For each requested key (K, L, n):
+ *   D_{Kk,Ll}(n) = (1/nk) sum_q sum_b occ[q][b] c_q[Kk][b] conj(c_q[Ll][b])
+ *                  exp(2 pi i kfrac_q . n),
+ * the real part (D is real for time-reversal-symmetric inputs).
+ *   nk        number of k points, >= 1
+ *   kfrac     nk x 3 k points in fractional reciprocal coordinates (host)
+ *   nbands    bands per k point, >= 1
+ *   coef      nk x nbasis x nbands complex eigenvector coefficients as (re, im)
+ *             pairs, row (Kk) = basis index sum_{x<K} nao(x) + k (host)
+ *   occ       nk x nbands occupation numbers (host)
+ *   nkeys, keys  nkeys x 5 block keys (K, L, n1, n2, n3), |n| <= 127 (host)
+ *   out       the blocks [nao(K)][nao(L)] row-major, packed in key order (host)
+ *   max_imag  (nullable) receives the largest |imaginary part| dropped
+ * The result can be passed to hfx_set_many('D', ...).  Ownership: inputs are
+ * read during the call.  Errors: HFX_E_ARG (sizes, keys, non-finite input),
+ * HFX_E_NOMEM, HFX_E_CUDA.
+ */
+hfx_status hfx_density_from_eigvecs(hfx_ctx *ctx, int32_t nk, const double *kfrac,
+                                    int32_t nbands, const double *coef, const double *occ,
+                                    int64_t nkeys, const int32_t *keys, double *out,
+                                    double *max_imag);
+
+/*
+ * The last build's exchange matrix at k points (Eq. Ham_rs2kspace), FP64 on
+ * the GPU:
+ *   Sigma_{Ii,Jj}(k) = sum over the Sigma keys (I, J, n) of
+ *                      exp(2 pi i kfrac . n) Sigma(I, J, n)_{ij}.
+ *   nk, kfrac  as in hfx_density_from_eigvecs (host)
+ *   out        nk x nbasis x nbasis complex as (re, im) pairs, row-major (host)
+ * Errors: HFX_E_ARG, HFX_E_STATE (no build), HFX_E_NOMEM, HFX_E_CUDA.
+ */
+hfx_status hfx_sigma_k(hfx_ctx *ctx, int32_t nk, const double *kfrac, double *out);
+
 /* Free the context and all device memory it owns.  NULL is allowed. */
 void hfx_destroy(hfx_ctx *ctx);
 

@@ -1587,3 +1587,114 @@ hfx_status hfx_stats(const hfx_ctx *ctx, void *stats) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------- steps next to the build
+
+namespace {
+bool finite_all(const double *x, int64_t n) {
+  for (int64_t i = 0; i < n; ++i)
+    if (!std::isfinite(x[i])) return false;
+  return true;
+}
+}  // namespace
+
+hfx_status hfx_density_from_eigvecs(hfx_ctx *ctx, int32_t nk, const double *kfrac,
+                                    int32_t nbands, const double *coef, const double *occ,
+                                    int64_t nkeys, const int32_t *keys, double *out,
+                                    double *max_imag) {
+  if (!ctx) return HFX_E_ARG;
+  if (nk < 1 || nbands < 1 || nkeys < 0 || !kfrac || !coef || !occ || (nkeys > 0 && (!keys || !out)))
+    return fail(ctx, HFX_E_ARG, "density: bad sizes or null pointers");
+  const int natoms = ctx->natoms;
+  std::vector<int32_t> aoff(natoms + 1, 0);
+  for (int x = 0; x < natoms; ++x) aoff[x + 1] = aoff[x] + ctx->nao[x];
+  const int64_t nb = aoff[natoms];
+  std::vector<int64_t> doff(nkeys + 1, 0);
+  for (int64_t e = 0; e < nkeys; ++e) {
+    const int32_t *k = keys + 5 * e;
+    if (k[0] < 0 || k[0] >= natoms || k[1] < 0 || k[1] >= natoms)
+      return fail(ctx, HFX_E_ARG, "density: key atom out of range");
+    for (int c = 2; c < 5; ++c)
+      if (k[c] < -127 || k[c] > 127) return fail(ctx, HFX_E_ARG, "density: |n| > 127");
+    doff[e + 1] = doff[e] + (int64_t)ctx->nao[k[0]] * ctx->nao[k[1]];
+  }
+  const int64_t ncoef = (int64_t)nk * nb * nbands * 2, nocc = (int64_t)nk * nbands;
+  if (!finite_all(kfrac, 3 * (int64_t)nk) || !finite_all(coef, ncoef) || !finite_all(occ, nocc))
+    return fail(ctx, HFX_E_ARG, "density: non-finite input");
+  if (nkeys == 0) {
+    if (max_imag) *max_imag = 0.0;
+    return HFX_OK;
+  }
+  cudaStream_t st = ctx->stream;
+  DevBuf<double> dk, dc, dq, dout;
+  DevBuf<int32_t> dkeys, daoff, dnao;
+  DevBuf<int64_t> ddoff;
+  DevBuf<unsigned long long> dmax;
+  CK(dk.reserve(3 * nk));
+  CK(dc.reserve(ncoef));
+  CK(dq.reserve(nocc));
+  CK(dout.reserve(doff[nkeys]));
+  CK(dkeys.reserve(5 * nkeys));
+  CK(daoff.reserve(natoms + 1));
+  CK(dnao.reserve(natoms));
+  CK(ddoff.reserve(nkeys + 1));
+  CK(dmax.reserve(1));
+  CK(cudaMemcpyAsync(dk.p, kfrac, sizeof(double) * 3 * nk, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dc.p, coef, sizeof(double) * ncoef, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dq.p, occ, sizeof(double) * nocc, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(dkeys.p, keys, sizeof(int32_t) * 5 * nkeys, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(daoff.p, aoff.data(), sizeof(int32_t) * (natoms + 1), cudaMemcpyHostToDevice,
+                     st));
+  CK(cudaMemcpyAsync(dnao.p, ctx->nao.data(), sizeof(int32_t) * natoms, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ddoff.p, doff.data(), sizeof(int64_t) * (nkeys + 1), cudaMemcpyHostToDevice,
+                     st));
+  CK(cudaMemsetAsync(dmax.p, 0, sizeof(unsigned long long), st));
+  CK(launch_density(nk, dk.p, (int)nb, nbands, dc.p, dq.p, nkeys, dkeys.p, daoff.p, dnao.p,
+                    ddoff.p, dout.p, dmax.p, st));
+  unsigned long long mbits = 0;
+  CK(cudaMemcpyAsync(out, dout.p, sizeof(double) * doff[nkeys], cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&mbits, dmax.p, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (max_imag) std::memcpy(max_imag, &mbits, sizeof(double));
+  return HFX_OK;
+}
+
+hfx_status hfx_sigma_k(hfx_ctx *ctx, int32_t nk, const double *kfrac, double *out) {
+  if (!ctx) return HFX_E_ARG;
+  if (nk < 1 || !kfrac || !out) return fail(ctx, HFX_E_ARG, "sigma_k: bad sizes or null pointers");
+  if (!ctx->results_valid) return fail(ctx, HFX_E_STATE, "sigma_k: no build");
+  if (!finite_all(kfrac, 3 * (int64_t)nk)) return fail(ctx, HFX_E_ARG, "sigma_k: non-finite k");
+  const int natoms = ctx->natoms;
+  if ((int64_t)nk * natoms * natoms > 2147483647ll)
+    return fail(ctx, HFX_E_ARG, "sigma_k: too many k points for this cell");
+  std::vector<int32_t> aoff(natoms + 1, 0);
+  for (int x = 0; x < natoms; ++x) aoff[x + 1] = aoff[x] + ctx->nao[x];
+  const int64_t nb = aoff[natoms], nkeys = (int64_t)ctx->sig_keys.size();
+  const int64_t nout = (int64_t)nk * nb * nb * 2;
+  cudaStream_t st = ctx->stream;
+  DevBuf<double> dk, dout;
+  DevBuf<int32_t> daoff, dnao;
+  DevBuf<uint64_t> dkeys;
+  DevBuf<int64_t> doffs;
+  CK(dk.reserve(3 * nk));
+  CK(dout.reserve(nout));
+  CK(daoff.reserve(natoms + 1));
+  CK(dnao.reserve(natoms));
+  CK(dkeys.reserve(nkeys));
+  CK(doffs.reserve(nkeys + 1));
+  CK(cudaMemcpyAsync(dk.p, kfrac, sizeof(double) * 3 * nk, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(daoff.p, aoff.data(), sizeof(int32_t) * (natoms + 1), cudaMemcpyHostToDevice,
+                     st));
+  CK(cudaMemcpyAsync(dnao.p, ctx->nao.data(), sizeof(int32_t) * natoms, cudaMemcpyHostToDevice, st));
+  if (nkeys > 0) {
+    CK(cudaMemcpyAsync(dkeys.p, ctx->sig_keys.data(), sizeof(uint64_t) * nkeys,
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(doffs.p, ctx->sig_offs.data(), sizeof(int64_t) * (nkeys + 1),
+                       cudaMemcpyHostToDevice, st));
+  }
+  CK(launch_sigma_k(nk, dk.p, natoms, daoff.p, dnao.p, nkeys, dkeys.p, doffs.p, ctx->d_sigma.p,
+                    nb, dout.p, st));
+  CK(cudaMemcpyAsync(out, dout.p, sizeof(double) * nout, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return HFX_OK;
+}

@@ -187,3 +187,12 @@ cudaError_t launch_check_mirror(const double *data, const int64_t *offs, const i
                                 cudaStream_t st);
 cudaError_t launch_gather(const double *const *src, const int64_t *dst_off, const int64_t *len,
                           int64_t nblk, double *dst, cudaStream_t st);
+// Density-matrix blocks from eigenvectors and Sigma at k points (hfx_fourier.cu).
+cudaError_t launch_density(int nk, const double *kfrac, int nb, int nbands, const double *coef,
+                           const double *occ, int64_t nkeys, const int32_t *keys,
+                           const int32_t *aoff, const int32_t *nao, const int64_t *doff,
+                           double *out, unsigned long long *maxim, cudaStream_t st);
+cudaError_t launch_sigma_k(int nk, const double *kfrac, int natoms, const int32_t *aoff,
+                           const int32_t *nao, int64_t nkeys, const uint64_t *skeys,
+                           const int64_t *soffs, const double *sigma, int64_t nb, double *out,
+                           cudaStream_t st);

@@ -81,6 +81,8 @@ def load_library():
             "hfx_selftest_ozaki": (S, [i32, i32, i32, P, P, P, i32]),
             "hfx_selftest_timeout": (S, [i64, P]),
             "hfx_build_batch": (S, [P, i32, P, ctypes.c_int, i32, P]),
+            "hfx_density_from_eigvecs": (S, [P, i32, P, i32, P, P, i64, P, P, P]),
+            "hfx_sigma_k": (S, [P, i32, P, P]),
             "hfx_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
@@ -319,6 +321,36 @@ class Context:
         dV = np.zeros(nV, np.float64)
         self._check(self._lib.hfx_grad(self._h, _p(dC), _p(dV)))
         return dC, dV
+
+    def density_from_eigvecs(self, kfrac, coef, occ, keys):
+        """Real-space density-matrix blocks for keys (n, 5) from eigenvectors
+        coef (nk, nbasis, nbands) complex and occupations occ (nk, nbands) at
+        fractional k points kfrac (nk, 3).  Returns (packed blocks in key
+        order, largest |imaginary part| dropped)."""
+        kf = np.ascontiguousarray(np.asarray(kfrac, np.float64).reshape(-1, 3))
+        c = np.asarray(coef, np.complex128)
+        nk, nbasis, nbands = c.shape
+        cc = np.ascontiguousarray(np.stack([c.real, c.imag], axis=-1))
+        f = np.ascontiguousarray(np.asarray(occ, np.float64).reshape(nk, nbands))
+        k = np.ascontiguousarray(np.asarray(keys, np.int32).reshape(-1, 5))
+        nat = len(self.nao)
+        ok = (k[:, 0] >= 0) & (k[:, 0] < nat) & (k[:, 1] >= 0) & (k[:, 1] < nat)
+        # keys with atoms out of range are rejected by the library (HFX_E_ARG)
+        size = int(sum(int(self.nao[a]) * int(self.nao[b]) for a, b in k[ok][:, :2].tolist()))
+        out = np.zeros(max(size, 1), np.float64)
+        mi = ctypes.c_double(0.0)
+        self._check(self._lib.hfx_density_from_eigvecs(self._h, nk, _p(kf), nbands, _p(cc), _p(f),
+                                                        k.shape[0], _p(k), _p(out),
+                                                        ctypes.byref(mi)))
+        return out[:size], mi.value
+
+    def sigma_k(self, kfrac) -> np.ndarray:
+        """The last build's Sigma at fractional k points: complex (nk, nb, nb)."""
+        kf = np.ascontiguousarray(np.asarray(kfrac, np.float64).reshape(-1, 3))
+        nb = int(np.sum(self.nao))
+        out = np.zeros((kf.shape[0], nb, nb, 2), np.float64)
+        self._check(self._lib.hfx_sigma_k(self._h, kf.shape[0], _p(kf), _p(out)))
+        return out[..., 0] + 1j * out[..., 1]
 
     def stats(self) -> dict:
         s = Stats()
