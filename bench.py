@@ -37,20 +37,32 @@ THETA = 1e-6
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
-WORKLOADS = {"si64": ("2x2x2", 2), "si8": ("1x1x1", 1), "si512": ("4x4x4", 4)}
+# name: (supercell, cells per edge, seed, generator options).  The last two are
+# the second workload: full-range Coulomb V out to 50 bohr, and a metallic D
+# (polynomial decay) out to 24 bohr.
+WORKLOADS = {"si64": ("2x2x2", 2, 2, {}), "si8": ("1x1x1", 1, 1, {}),
+             "si512": ("4x4x4", 4, 3, {}),
+             "si8_fullrange": ("1x1x1", 1, 5, {"cut_V": 50.0, "mu": 0.0}),
+             "si8_metal": ("1x1x1", 1, 6, {"cut_D": 24.0, "d_decay": "power"})}
 
 
 def workload(name: str, rank: int):
     import synth
-    cells, ncell = WORKLOADS[name]
-    seed = {"si8": 1, "si64": 2, "si512": 3}[name] + 1000 * rank
-    return synth.make_workload(synth.si_diamond(ncell), seed=seed, name=name)
+    cells, ncell, seed, opts = WORKLOADS[name]
+    return synth.make_workload(synth.si_diamond(ncell), seed=seed + 1000 * rank, name=name,
+                               **opts)
 
 
 def workload_desc(wl) -> str:
-    cells = WORKLOADS[wl.name][0]
+    cells, _, _, opts = WORKLOADS[wl.name]
+    kind = ""
+    if opts.get("mu") == 0.0:
+        kind += ", full-range Coulomb V"
+    if opts.get("d_decay") == "power":
+        kind += ", metallic D (polynomial decay)"
     return (f"{wl.name}: Si-like diamond {cells} supercell, {wl.system.natoms} atoms, 13 NAO / "
-            f"60 ABF per atom, C,D <= 16 bohr, V <= 20 bohr, theta = {THETA:g}, seed {wl.seed}")
+            f"60 ABF per atom, C <= {wl.cut_C:g} bohr, D <= {wl.cut_D:g} bohr, "
+            f"V <= {wl.cut_V:g} bohr{kind}, theta = {THETA:g}, seed {wl.seed}")
 
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_zc<6,16,4,8,1> launch on the

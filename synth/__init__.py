@@ -208,9 +208,20 @@ def gen_V(system: System, cut: float, seed: int, mu: float = 0.11) -> dict:
     return out
 
 
-def gen_D(system: System, cut: float, seed: int) -> dict:
-    """D(k, l, n) within ``cut``: N(0, 0.1) exp(-d/3); on-site (X + X^T)/sqrt2 with
-    X ~ N(0, 0.1^2); D(l, k, -n) = D(k, l, n)^T."""
+def d_envelope(d: float, decay: str = "exp") -> float:
+    """Off-site magnitude of D at distance d: exponential for an insulator
+    (exp(-d/3)), polynomial for a metal ((1 + d/3)^-2; Sec. III.B: an
+    insulator's D decays exponentially, a metal's only polynomially)."""
+    if decay == "exp":
+        return math.exp(-d / 3.0)
+    if decay == "power":
+        return (1.0 + d / 3.0) ** -2
+    raise ValueError(f"unknown D decay {decay!r}")
+
+
+def gen_D(system: System, cut: float, seed: int, decay: str = "exp") -> dict:
+    """D(k, l, n) within ``cut``: N(0, 0.1) times d_envelope(d, decay); on-site
+    (X + X^T)/sqrt2 with X ~ N(0, 0.1^2); D(l, k, -n) = D(k, l, n)^T."""
     out = {}
     for i, j, n, d in system.pairs_within(cut):
         if not _canonical(i, j, n):
@@ -221,7 +232,7 @@ def gen_D(system: System, cut: float, seed: int) -> dict:
             x = 0.1 * g.standard_normal((ka, ka))
             blk = (x + x.T) / math.sqrt(2.0)
         else:
-            blk = 0.1 * g.standard_normal((ka, kb)) * math.exp(-d / 3.0)
+            blk = 0.1 * g.standard_normal((ka, kb)) * d_envelope(d, decay)
         out[(i, j) + tuple(n)] = blk
         out[(j, i) + tuple(-c for c in n)] = blk.T.copy()
     return out
@@ -241,11 +252,13 @@ class Workload:
 
 
 def make_workload(system: System, cut_C=16.0, cut_V=20.0, cut_D=16.0, seed=1,
-                  name=None) -> Workload:
+                  name=None, mu=0.11, d_decay="exp") -> Workload:
+    """mu: range separation of V (erfc(mu d) / d; 0 is the full-range
+    Coulomb of Hartree-Fock); d_decay: "exp" (insulator) or "power" (metal)."""
     return Workload(name or system.name, system,
                     pack(gen_C(system, cut_C, seed)),
-                    pack(gen_V(system, cut_V, seed)),
-                    pack(gen_D(system, cut_D, seed)),
+                    pack(gen_V(system, cut_V, seed, mu=mu)),
+                    pack(gen_D(system, cut_D, seed, decay=d_decay)),
                     cut_C, cut_V, cut_D, seed)
 
 
@@ -266,6 +279,18 @@ def si512(seed=3):
 
 def ab216(seed=4):
     return make_workload(two_element_rocksalt(3, seed=seed), seed=seed, name="ab216")
+
+
+# The second workload (denser tasks for the same kernels): full-range Coulomb V
+# out to R_Q = 50 bohr, as Hartree-Fock or long-range-corrected functionals
+# need (Sec. IV), and a metallic D kept out to 24 bohr with polynomial decay.
+def si8_fullrange(seed=5):
+    return make_workload(si_diamond(1), cut_V=50.0, mu=0.0, seed=seed, name="si8_fullrange")
+
+
+def si8_metal(seed=6):
+    return make_workload(si_diamond(1), cut_D=24.0, d_decay="power", seed=seed,
+                         name="si8_metal")
 
 
 def si_shrunk(ncell=1, cut_C=8.0, cut_V=10.0, cut_D=8.0, seed=11, nao=13, nabf=60):
