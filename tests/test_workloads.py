@@ -1,4 +1,4 @@
-"""The second workload's generators (survey: full-range or metallic cells):
+"""The second workload's generators, full-range or metallic cells:
 full-range Coulomb V (mu = 0, R_Q up to 50 bohr) and a metallic D whose
 off-site magnitude decays polynomially (Sec. III.B).  Checked on CPU: the
 envelopes are exactly the stated ones on the same random draws, the tasks
