@@ -57,7 +57,7 @@ def kmeans(positions, k: int, max_iter: int = 200):
     then repeatedly the atom farthest from every chosen centre, ties to the
     lowest index); distances are plain Euclidean in the cell, without periodic
     images, as the algorithm is stated; a category left empty takes the atom
-    farthest from its own centre."""
+    farthest from its own centre among categories holding more than one."""
     x = np.asarray(positions, np.float64).reshape(-1, 3)
     n = x.shape[0]
     k = max(1, min(int(k), n))
@@ -72,11 +72,16 @@ def kmeans(positions, k: int, max_iter: int = 200):
     for _ in range(max_iter):
         dist = ((x[:, None, :] - centres[None, :, :]) ** 2).sum(-1)
         new = np.argmin(dist, axis=1)
+        counts = np.bincount(new, minlength=k)
+        own = dist[np.arange(n), new]
         for j in range(k):
-            if not np.any(new == j):
-                own = dist[np.arange(n), new]
-                far = int(np.argmax(own))
+            if counts[j] == 0:
+                # k <= n: some category holds two atoms; take its farthest atom
+                cand = np.nonzero(counts[new] > 1)[0]
+                far = int(cand[np.argmax(own[cand])])
+                counts[new[far]] -= 1
                 new[far] = j
+                counts[j] = 1
         if np.array_equal(new, labels):
             break
         labels = new

@@ -72,6 +72,16 @@ def test_kmeans_stops_at_a_fixed_point():
         np.testing.assert_allclose(centres[j], pts[labels == j].mean(0))
 
 
+def test_kmeans_degenerate_inputs():
+    """Fewer atoms than ranks, and coincident atoms: valid owners, no error."""
+    own = sharding.kmeans_owner(np.array([[0.0, 0, 0], [5.0, 0, 0]]), 4)
+    assert sorted(own.tolist()) == [0, 1]
+    pts = np.zeros((6, 3))
+    own = sharding.kmeans_owner(pts, 3)
+    assert own.shape == (6,) and own.min() >= 0 and own.max() < 3
+    assert sharding.kmeans_owner(np.array([[1.0, 2.0, 3.0]]), 1).tolist() == [0]
+
+
 def _chain(natoms=48):
     s = synth.custom("chain", 1.0, 100000, [[3 * i, 0, 0] for i in range(natoms)], 4, 6)
     ck = np.array([(i, j, *n) for i, j, n, _ in s.pairs_within(7.0)])
