@@ -20,7 +20,10 @@ norm).  Reading: the paper does not name the norm; with the Frobenius norm all
 three are Hoelder bounds (|tr ABCD| <= prod of Schatten-4 norms;
 |tr[X^T W D^T]| <= |X|_4 |W| |D|_4; Cauchy-Schwarz), so each is a true bound.
 The block screen of the library (block max-norm product > theta) is applied
-first, as the first level of Algorithm 4.
+first, as the first level of Algorithm 4; the Cauchy-Schwarz ERI screen
+(Eq. CS-ERI, per quadruple of atoms) optionally before the element bounds.
+A diagonal ERI can be negative when the synthetic V is not positive
+semi-definite; the screen then uses 0 for it.
 """
 from __future__ import annotations
 
@@ -56,16 +59,56 @@ class _Sites:
                                               int(self.nao[y[0]]))
 
 
-def build(wl, theta: float, eps: float):
-    """Sigma with the block screen at theta and the three element-level bounds
-    at eps.  Returns (Sigma {key: block}, kept {level: count}) where level 0..2
-    counts elements stopped by L1, L2, L3 and level 3 the elements computed."""
+def diag_eri_max(wl) -> dict:
+    """For every C key (A, F, n): the largest diagonal ERI
+    (phi_Aa phi_Ff | phi_Aa phi_Ff) over a in A, f in F (Sec. III.C,
+    Cauchy-Schwarz ERI screening).  By Eq. LRI the pair expands on the ABFs of
+    A with C(A, F, n)[:, a, f] and, when F is another site, on those of F with
+    C(F, A, -n)[:, f, a]; the ERI is that vector's V-norm with the V blocks
+    between the two sites (a missing block is zero)."""
     S = _Sites(wl)
+    out = {}
+    for (A, F, n1, n2, n3), blk in S.C.items():
+        n = (n1, n2, n3)
+        pa, na, nf = int(S.nabf[A]), int(S.nao[A]), int(S.nao[F])
+        cA = blk.reshape(pa, na, nf)
+        vAA = S.V.get((A, A, 0, 0, 0))
+        vAA = np.zeros((pa, pa)) if vAA is None else vAA.reshape(pa, pa)
+        same = A == F and n == (0, 0, 0)
+        q = np.einsum("xaf,xy,yaf->af", cA, vAA, cA)
+        if not same:
+            pf = int(S.nabf[F])
+            m = (-n1, -n2, -n3)
+            cF = S.C.get((F, A) + m)
+            cF = np.zeros((pf, nf, na)) if cF is None else cF.reshape(pf, nf, na)
+            vAF = S.V.get((A, F) + n)
+            vAF = np.zeros((pa, pf)) if vAF is None else vAF.reshape(pa, pf)
+            vFA = S.V.get((F, A) + m)
+            vFA = np.zeros((pf, pa)) if vFA is None else vFA.reshape(pf, pa)
+            vFF = S.V.get((F, F, 0, 0, 0))
+            vFF = np.zeros((pf, pf)) if vFF is None else vFF.reshape(pf, pf)
+            q = q + np.einsum("xaf,xy,yfa->af", cA, vAF, cF) \
+                  + np.einsum("xfa,xy,yaf->af", cF, vFA, cA) \
+                  + np.einsum("xfa,xy,yfa->af", cF, vFF, cF)
+        out[(A, F) + n] = float(q.max())
+    return out
+
+
+def build(wl, theta: float, eps: float, eps_eri: float = None):
+    """Sigma with the block screen at theta, the Cauchy-Schwarz ERI screen at
+    eps_eri (a quadruple (A, F, B, G) is kept iff
+    sqrt(Q(A,F)) sqrt(Q(B,G)) > eps_eri, Q from diag_eri_max; None skips it)
+    and the three element-level bounds at eps.  Returns (Sigma {key: block},
+    counts) where counts[0..2] are the elements stopped by L1, L2, L3,
+    counts[3] the elements computed and counts[4] the quadruples the ERI
+    screen removed."""
+    S = _Sites(wl)
+    qeri = diag_eri_max(wl) if eps_eri is not None else None
     mx = {k: float(np.abs(v).max()) for k, v in S.C.items()}
     mv = {k: float(np.abs(v).max()) for k, v in S.V.items()}
     md = {k: float(np.abs(v).max()) for k, v in S.D.items()}
     sig = {}
-    stats = np.zeros(4, np.int64)
+    stats = np.zeros(5, np.int64)
     z3 = (0, 0, 0)
     for a in range(wl.system.natoms):
         A = (a, z3)
@@ -79,6 +122,11 @@ def build(wl, theta: float, eps: float):
                 cAF = S.c(A, F)
                 for G in Gs:
                     cBG = S.c(B, G)
+                    if qeri is not None:
+                        qa, qb = qeri[S.key(A, F)], qeri[S.key(B, G)]
+                        if not np.sqrt(max(qa, 0.0)) * np.sqrt(max(qb, 0.0)) > eps_eri:
+                            stats[4] += 1
+                            continue
                     cc = mx[S.key(A, F)] * mx[S.key(B, G)]
                     for v, (dsrc, tx, tgt) in enumerate(((F, G, (A, B)), (F, B, (A, G)),
                                                          (A, G, (F, B)), (A, B, (F, G)))):

@@ -76,3 +76,45 @@ def test_dropped_mass_and_monotone_in_eps():
     # all three levels stop some element at eps = 0.1
     _, stats = multilevel.build(wl, 0.0, 0.1)
     assert (stats[:3] > 0).all()
+
+
+def test_diagonal_eris_match_the_lri_map():
+    """Q(A, F) from the oracle equals the largest diagonal of M_A V M_A^T over
+    the rows (F, a, f) of the brute-force LRI map."""
+    wl = _cell()
+    q = multilevel.diag_eri_max(wl)
+    S = refforms.Sites(wl)
+    for a in range(wl.system.natoms):
+        A = (a, (0, 0, 0))
+        sites = sorted({A} | set(S.partners(A)))
+        abf, c = {}, 0
+        for s in sites:
+            abf[s] = (c, c + int(S.nabf[s[0]]))
+            c += int(S.nabf[s[0]])
+        V = np.zeros((c, c))
+        for s in sites:
+            for t in sites:
+                vb = S.v(s, t)
+                if vb is not None:
+                    V[abf[s][0]:abf[s][1], abf[t][0]:abf[t][1]] = vb
+        M, rows = refforms._lri_matrix(S, A, abf)
+        diag = np.einsum("ij,jk,ik->i", M, V, M)
+        r0 = 0
+        for (F, nx, ny) in rows:
+            key = S.key(A, F)
+            if key in q:
+                assert abs(diag[r0:r0 + nx * ny].max() - q[key]) <= 1e-12 * max(1.0, abs(q[key]))
+            r0 += nx * ny
+
+
+def test_eri_screen_limits():
+    """eps_eri below every bound keeps every quadruple (the plain build); the
+    screen removes more quadruples as eps_eri grows."""
+    wl = _cell()
+    ref, _ = multilevel.build(wl, 0.0, 0.0)
+    got, stats = multilevel.build(wl, 0.0, 0.0, eps_eri=-1.0)
+    keys = sorted(ref)
+    np.testing.assert_array_equal(_flat(got, keys), _flat(ref, keys))
+    assert stats[4] == 0
+    removed = [int(multilevel.build(wl, 0.0, 0.0, eps_eri=e)[1][4]) for e in (0.1, 1.0, 5.0, 50.0)]
+    assert removed == sorted(removed) and removed[-1] > removed[0]
