@@ -1,0 +1,45 @@
+"""Host-side helpers of the benchmark: the k_zc traffic guard, the clock
+sampler's parsing of nvidia-smi records, and the named workloads."""
+import os
+
+import numpy as np
+
+import bench
+
+
+def test_traffic_follows_the_captured_source_only(monkeypatch):
+    t = bench.zc_traffic(1e12)
+    assert t is not None and 1e9 < t < 1e10      # ~2.1e-3 bytes per issued flop
+    monkeypatch.setattr(bench, "ZC_CAPTURED_SHA", "0000000000000000")
+    assert bench.zc_traffic(1e12) is None
+
+
+def test_clock_summary_median_max_and_reasons(tmp_path):
+    c = bench.ClockSampler(0)
+    c.path = os.path.join(tmp_path, "clocks.csv")
+    c.proc = object()  # as if sampling had run
+    rows = [
+        "0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ]
+    with open(c.path, "w") as f:
+        f.write("\n".join(rows) + "\n")
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
+
+
+def test_named_workloads():
+    assert set(bench.WORKLOADS) >= {"si8", "si64", "si8_fullrange", "si8_metal"}
+    metal = bench.workload("si8_metal", 0)
+    full = bench.workload("si8_fullrange", 0)
+    assert metal.cut_D == 24.0 and full.cut_V == 50.0
+    assert "metallic D" in bench.workload_desc(metal)
+    assert "full-range Coulomb V" in bench.workload_desc(full)
+    # ranks draw different cells of the same shape (weak scaling)
+    a, b = bench.workload("si8", 0), bench.workload("si8", 1)
+    assert a.seed != b.seed
+    np.testing.assert_array_equal(a.C.keys, b.C.keys)
+    assert not np.array_equal(a.C.data, b.C.data)
