@@ -53,6 +53,8 @@ def _load():
             lib.orc_ex.argtypes = [P, i64, P, P, P]
             lib.orc_maxabs.argtypes = [P, ctypes.c_char, P]
             lib.orc_set_maxabs.argtypes = [P, ctypes.c_char, P]
+            lib.orc_set_eri.argtypes = [P, f64]
+            lib.orc_eri_sq.argtypes = [P, P]
             _lib = lib
     return _lib
 
@@ -146,6 +148,17 @@ class Oracle:
         assert v.shape[0] == self.counts_blocks[which]
         self._keep.append(v)
         self._lib.orc_set_maxabs(self._h, which.encode()[0:1], _ptr(v))
+
+    def set_eri(self, eps_eri):
+        """Turn on the Cauchy-Schwarz ERI screen at eps_eri (Eq. CS-ERI): a
+        term also needs sqrt(Q_AF) sqrt(Q_BG) > eps_eri; None turns it off."""
+        self._lib.orc_set_eri(self._h, -1.0 if eps_eri is None else float(eps_eri))
+
+    def eri_sq(self) -> np.ndarray:
+        """sqrt(max(Q, 0)) per C block (key order) of the ERI screen."""
+        out = np.zeros(self.counts_blocks["C"], np.float64)
+        self._lib.orc_eri_sq(self._h, _ptr(out))
+        return out
 
     def maxabs(self, which: str) -> np.ndarray:
         out = np.zeros(self.counts_blocks[which], np.float64)

@@ -27,6 +27,9 @@
  *      S = (maxabs(C_A-side) * maxabs(C_B-side)) * (maxabs(V_AB) * maxabs(D_KL)),
  *    multiplied in exactly that association in round-to-nearest FP64 (block
  *    upper limits, Sec. III.B; strict ">" as in Algorithm 4);
+ *  - optional Cauchy-Schwarz ERI screen (Sec. III.C, Eq. CS-ERI; orc_set_eri):
+ *    a term also needs sqrt(Q_AF) * sqrt(Q_BG) > eps_eri, Q the largest
+ *    diagonal ERI of the AO-pair sites {A, F} and {B, G} under Eq. LRI;
  *  - a block exists iff it was supplied; missing blocks are zero.
  *
  * Coefficient roles: cA[alpha][i][k] = C(I,K)[alpha][i][k] when A = I and
@@ -121,6 +124,10 @@ typedef struct orc {
   /* per atom a: V(a, b, n) blocks */
   int64_t *vout_start;
   nbr_t *vout;
+  /* Cauchy-Schwarz ERI screen: per C block sqrt(max(Q, 0)); off when !eri_on */
+  int eri_on;
+  double eps_eri;
+  double *eri_sq;
 } orc;
 
 static void bset_init(bset_t *b, int64_t n, const int32_t *keys, const double *data,
@@ -204,7 +211,79 @@ void orc_destroy(orc *o) {
   free(o->C.maxabs); free(o->V.maxabs); free(o->D.maxabs);
   free(o->cout_start); free(o->cin_start); free(o->cout); free(o->cin);
   free(o->vout_start); free(o->vout);
+  free(o->eri_sq);
   free(o->nao); free(o->nabf); free(o);
+}
+
+/* x^T V y over the V block between two sites (row-major [nx][ny]); a missing
+ * block (v < 0) contributes zero. */
+static double vform(const orc *o, int64_t v, const double *x, int nx, const double *y, int ny) {
+  if (v < 0) return 0.0;
+  const double *V = o->V.data + o->V.offs[v];
+  double q = 0.0;
+  for (int al = 0; al < nx; ++al) {
+    double t = 0.0;
+    for (int be = 0; be < ny; ++be) t += V[(int64_t)al * ny + be] * y[be];
+    q += x[al] * t;
+  }
+  return q;
+}
+
+/*
+ * Cauchy-Schwarz ERI screen (Sec. III.C, Eq. CS-ERI).  For every C block
+ * (x, y, n) -- the AO-pair sites X = (x, 0), Y = (y, n) -- the largest diagonal
+ * ERI Q = max over a in x, f in y of (phi_Xa phi_Yf | phi_Xa phi_Yf).  By
+ * Eq. LRI the pair is sum_alpha C(x,y,n)[alpha][a][f] P_{X alpha} plus, when Y
+ * is another site, sum_beta C(y,x,-n)[beta][f][a] P_{Y beta}; the diagonal ERI
+ * is the V-norm of that expansion, with the V blocks V_XX, V_XY, V_YX, V_YY
+ * (missing blocks and missing C(y,x,-n) are zero).  Q is the same for both C
+ * blocks of one site pair.  A term with AO pairs {A,F} and {B,G} (C blocks
+ * eK and eL) is then kept only if sqrt(max(Q_eK, 0)) * sqrt(max(Q_eL, 0)) >
+ * eps; eps < 0 turns the screen off.
+ */
+void orc_set_eri(orc *o, double eps) {
+  free(o->eri_sq);
+  o->eri_sq = NULL;
+  o->eri_on = eps >= 0.0;
+  o->eps_eri = eps;
+  if (!o->eri_on) return;
+  o->eri_sq = (double *)malloc(sizeof(double) * (size_t)(o->C.n > 0 ? o->C.n : 1));
+#pragma omp parallel for schedule(dynamic, 16)
+  for (int64_t e = 0; e < o->C.n; ++e) {
+    const int32_t *k = o->C.keys + 5 * e;
+    const int32_t x = k[0], y = k[1];
+    const int32_t zero[3] = {0, 0, 0}, n[3] = {k[2], k[3], k[4]}, m[3] = {-k[2], -k[3], -k[4]};
+    const int px = o->nabf[x], py = o->nabf[y], nx = o->nao[x], ny = o->nao[y];
+    const int same = x == y && n[0] == 0 && n[1] == 0 && n[2] == 0;
+    const double *cX = o->C.data + o->C.offs[e];
+    const int64_t eY = same ? -1 : bset_find(&o->C, y, x, m);
+    const double *cY = eY >= 0 ? o->C.data + o->C.offs[eY] : NULL;
+    const int64_t vXX = bset_find(&o->V, x, x, zero);
+    const int64_t vXY = same ? -1 : bset_find(&o->V, x, y, n);
+    const int64_t vYX = same ? -1 : bset_find(&o->V, y, x, m);
+    const int64_t vYY = same ? -1 : bset_find(&o->V, y, y, zero);
+    double *u = (double *)malloc(sizeof(double) * (size_t)(px + py));
+    double *w = u + px;
+    double qmax = -INFINITY;
+    for (int a = 0; a < nx; ++a)
+      for (int f = 0; f < ny; ++f) {
+        for (int al = 0; al < px; ++al) u[al] = cX[((int64_t)al * nx + a) * ny + f];
+        double q = vform(o, vXX, u, px, u, px);
+        if (!same) {
+          for (int be = 0; be < py; ++be) w[be] = cY ? cY[((int64_t)be * ny + f) * nx + a] : 0.0;
+          q += vform(o, vXY, u, px, w, py) + vform(o, vYX, w, py, u, px) +
+               vform(o, vYY, w, py, w, py);
+        }
+        if (q > qmax) qmax = q;
+      }
+    free(u);
+    o->eri_sq[e] = sqrt(qmax > 0.0 ? qmax : 0.0);
+  }
+}
+
+/* sqrt(max(Q, 0)) per C block of the last orc_set_eri (zeros when off). */
+void orc_eri_sq(const orc *o, double *out) {
+  for (int64_t e = 0; e < o->C.n; ++e) out[e] = o->eri_on ? o->eri_sq[e] : 0.0;
 }
 
 /* One way an ABF centre is placed for an AO pair (X, Y), X the Sigma-side site:
@@ -257,6 +336,15 @@ static double screen_S(const orc *o, const role_t *eK, const role_t *eL, int64_t
   double cc = o->C.maxabs[eK->cblk] * o->C.maxabs[eL->cblk];
   double vd = o->V.maxabs[v] * o->D.maxabs[d];
   return cc * vd;
+}
+
+/* Does a term survive: the block screen S > theta and, when on, the
+ * Cauchy-Schwarz ERI screen of its two AO pairs. */
+static int survives(const orc *o, const role_t *eK, const role_t *eL, int64_t v, int64_t d,
+                    double theta) {
+  if (!(screen_S(o, eK, eL, v, d) > theta)) return 0;
+  if (o->eri_on && !(o->eri_sq[eK->cblk] * o->eri_sq[eL->cblk] > o->eps_eri)) return 0;
+  return 1;
 }
 
 /* variant index: 0 = ABFs on (I,J), 1 = (I,L), 2 = (K,J), 3 = (K,L) */
@@ -329,7 +417,7 @@ int64_t orc_keys(orc *o, double theta, int32_t a0, int32_t a1, int32_t *keys_out
             int64_t d = find_between(&o->D, K, &Y);
             if (d >= 0) {
               eL.partner = Y; eL.abf = B; eL.cblk = p->blk; eL.transposed = 0;
-              if (screen_S(o, eK, &eL, vb, d) > theta) {
+              if (survives(o, eK, &eL, vb, d, theta)) {
                 const int v = variant_of(eK, &eL);
                 c[v]++;
                 alive = 1;
@@ -341,7 +429,7 @@ int64_t orc_keys(orc *o, double theta, int32_t a0, int32_t a1, int32_t *keys_out
             /* L = B, J = Y */
             if (dKB >= 0 && !same_site(&Y, &B)) {
               eL.partner = B; eL.abf = B; eL.cblk = p->blk; eL.transposed = 1;
-              if (screen_S(o, eK, &eL, vb, dKB) > theta) {
+              if (survives(o, eK, &eL, vb, dKB, theta)) {
                 const int v = variant_of(eK, &eL);
                 c[v]++;
                 alive = 1;
@@ -454,7 +542,7 @@ static int64_t sigma_block(const orc *o, double theta, int32_t i, int32_t j, con
       if (d < 0) continue;
       const int64_t v = find_between(&o->V, A, B);
       if (v < 0) continue;
-      if (!(screen_S(o, eK, eL, v, d) > theta)) continue;
+      if (!survives(o, eK, eL, v, d, theta)) continue;
       ++nterms;
       const int nk = o->nao[K->a];
       const int pA = o->nabf[A->a];
