@@ -52,6 +52,10 @@
  * Sigma is accumulated in 128-bit fixed point (integer adds, 2^-64 Ha
  * resolution) and converted to FP64 once, and E_X is summed from it in a
  * fixed order, so results are bitwise reproducible run to run in every mode.
+ * Range: every partial contribution a kernel adds, and every finished Sigma
+ * element, must stay below 2^31 Ha in magnitude; a kernel that meets a larger
+ * contribution adds nothing and the build returns HFX_E_CUDA ("reported
+ * error 8").
  *
  * Ownership.  hfx_set_* copy the caller's data (host pointers) or read device
  * pointers on the context's stream before returning; the caller may free or
@@ -201,7 +205,9 @@ hfx_status hfx_grad(hfx_ctx *ctx, double *dC, double *dV);
 
 /*
  * Build many independent cells (contexts), cell c with theta thetas[c]: the
- * same as hfx_build on each context in order, on each context's own stream,
+ * same as hfx_build on each context in order, on each context's own stream
+ * (the cells run one after another, each with its own launches and host
+ * synchronisations; there is no single grouped launch over the cells yet),
  * with ex_out[c] (if ex_out is not NULL) receiving cell c's E_X.  The cells
  * share nothing; results are bitwise those of separate hfx_build calls.
  * Errors: HFX_E_ARG (NULL arrays, ncells < 0), else the first failing cell's
@@ -210,6 +216,23 @@ hfx_status hfx_grad(hfx_ctx *ctx, double *dC, double *dV);
  */
 hfx_status hfx_build_batch(hfx_ctx **cells, int32_t ncells, const double *thetas, hfx_prec prec,
                            int32_t nslices, double *ex_out);
+
+/*
+ * Cauchy-Schwarz ERI screen (Sec. III.C, Eq. CS-ERI), applied by the next
+ * builds on top of the block screen at theta.  For every C block (x, y, n)
+ * the library computes, in FP64 on the GPU, Q = the largest diagonal ERI
+ * (phi_Xa phi_Yf | phi_Xa phi_Yf) over the AO pairs of the sites X = (x, 0),
+ * Y = (y, n), with the pair expanded by Eq. LRI on the ABFs of X
+ * (C(x,y,n)[:, a, f]) and, when Y is another site, of Y (C(y,x,-n)[:, f, a]),
+ * using the V blocks between X and Y (missing blocks count as zero).  A
+ * quadruple (A, B, F, G) -- AO pairs {A, F} and {B, G} -- keeps its terms only
+ * if sqrt(max(Q_AF, 0)) * sqrt(max(Q_BG, 0)) > eps_eri (strict, round-to-
+ * nearest FP64).  The bounds are computed once per change of C or V.
+ *   eps_eri   threshold in Ha; a negative value turns the screen off (the
+ *             default for a new context)
+ * Errors: HFX_E_ARG (NULL ctx, NaN or infinite eps_eri).  Marks results stale.
+ */
+hfx_status hfx_set_eri_screen(hfx_ctx *ctx, double eps_eri);
 
 /* Statistics of the last build (layout: struct hfx_stats_v1 below). */
 typedef struct {
@@ -237,6 +260,17 @@ typedef struct {
   double kernel_tensor_flops[8]; /* bf16 tensor-core flops issued per kernel (split modes) */
   double canonical_flops_piece[4]; /* canonical_flops split by piece (T and Ht stages) ... */
   double canonical_flops_y;        /* ... and the Y = V C part; the five sum to canonical_flops */
+  /* split modes: FP64-equivalent flops (2 per multiply-add of the unsplit
+     operands) of each tensor-core product, without row, column or K padding
+     and without zero tiles; [1] Y, [4] D_FG + D_FB products, else 0 */
+  double kernel_unpadded_flops[8];
+  /* split modes with tensor-core D_FG / D_FB products: load balance of those
+     persistent launches, sum over waves of the largest CTA busy time over the
+     sum of the mean CTA busy time (Sec. IV's Delta t_max / Delta t_av with
+     CTAs as the workers), else 0 */
+  double zc_dt_max_over_avg;
+  double eps_eri;           /* the ERI screen's threshold in this build (< 0: off) */
+  int64_t n_eri_removed;    /* quadruples (A, B, F, G) the ERI screen removed */
 } hfx_stats_v1;
 
 hfx_status hfx_stats(const hfx_ctx *ctx, void *stats);
@@ -264,8 +298,11 @@ hfx_status hfx_stats(const hfx_ctx *ctx, void *stats);
  * nabf_a*nao_j*nao_k must both be <= 131072, else HFX_E_SHAPE).  Every GPU
  * that loads the library holds that array until the process exits.  The first
  * call on each device looks the array's address up (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  No
- * call allocates or frees device memory.  All calls share the one array:
+ * that device current; make that first call before any stream capture.  The
+ * address is kept per device and per CUDA context: after cudaDeviceReset, or
+ * with another context current, the next call looks it up again, so that call
+ * too must come before any stream capture.  No call allocates or frees device
+ * memory.  All calls share the one array:
  * calls whose kernels overlap on the GPU (different streams, or different host
  * threads on one device) race on it and give wrong results -- order them on
  * one stream.  Each call writes every intermediate element it reads, so
@@ -273,7 +310,8 @@ hfx_status hfx_stats(const hfx_ctx *ctx, void *stats);
  *
  * The call is asynchronous: results are in out once the stream reaches them.
  * Errors: HFX_E_ARG (null pointer, size < 1), HFX_E_SHAPE (intermediates
- * larger than the static array), HFX_E_CUDA (device lookup or launch failed).
+ * larger than the static array, or nao_i*nao_j > 2^31 - 1), HFX_E_CUDA
+ * (device lookup or launch failed).
  */
 hfx_status hfx_term_noalloc(int32_t nabf_a, int32_t nabf_b, int32_t nao_i, int32_t nao_k,
                             int32_t nao_j, int32_t nao_l, const double *cA, const double *V,
@@ -302,6 +340,17 @@ hfx_status hfx_selftest_ozaki(int32_t M, int32_t N, int32_t K, const double *A, 
  * Errors: HFX_E_ARG (limit out of range), HFX_E_CUDA.
  */
 hfx_status hfx_selftest_timeout(int64_t limit_cycles, int64_t *waited_cycles);
+
+/*
+ * Diagnostic (no counterpart in the paper): the measured FP64 rates that
+ * bound the HFX_FP64 mode on the current device.  Every SM runs warps that
+ * issue long chains of independent FP64 multiply-adds, once as DFMA on CUDA
+ * cores and once as FP64 tensor-core products (mma.sync m8n8k4 f64), each
+ * timed with CUDA events after a warm-up run; writes the achieved TFLOP/s
+ * (2 flops per multiply-add) of each.  Allocates a small temporary buffer.
+ * Errors: HFX_E_ARG (NULL outputs), HFX_E_NOMEM, HFX_E_CUDA.
+ */
+hfx_status hfx_probe_fp64(double *dfma_tflops, double *dmma_tflops);
 
 /* Message for the last failing call on ctx (never NULL; "" when none). */
 const char *hfx_last_error(const hfx_ctx *ctx);

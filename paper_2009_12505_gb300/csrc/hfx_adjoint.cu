@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_dcb(ContractArgs A) {
     double s = 0.0;
     for (int al = 0; al < pA; ++al)
       s = fma(V[(int64_t)al * pB + be], R[((int64_t)al * nb + b) * ncol + g], s);
-    fx_add(acc + 2 * o, -0.5 * s);
+    fx_add(acc + 2 * o, -0.5 * s, A.err);
   }
 }
 
@@ -252,7 +252,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_dca(ContractArgs A) {
         for (int b = 0; b < nb; ++b) s = fma(Dab[a * nb + b], T1[(al * nb + b) * nf + f], s);
       if (use23)
         for (int b = 0; b < nb; ++b) s = fma(Dfb[f * nb + b], Ts[(al * na + a) * nb + b], s);
-      fx_add(acc + 2 * ((int64_t)(al0 + al) * na * nf + r), -0.5 * s);
+      fx_add(acc + 2 * ((int64_t)(al0 + al) * na * nf + r), -0.5 * s, A.err);
     }
     __syncthreads();
     macs += (unsigned long long)ac * (per1 + per2) * 13 * (n14 + n23);

@@ -159,6 +159,8 @@ struct hfx_ctx {
   int nsm = 0;
   DevBuf<ZcJob> d_zcjobs;
   DevBuf<ZcEnt> d_zcents;
+  DevBuf<int> d_zckeys;           // job-cost histogram / range starts (256)
+  DevBuf<long long> d_ctans;      // per-CTA busy time of the last D_FG / D_FB launch
   DevBuf<int64_t> d_split_meta;   // cy_base, cy_rowpre, c4_base, c4_rowpre, vs_base, v_rowpre, nc_start
   DevBuf<int32_t> d_kt;           // ktY, kt4
   std::vector<int32_t> ktY, kt4;
@@ -168,6 +170,12 @@ struct hfx_ctx {
   DevBuf<int> d_njobs;
   DevBuf<unsigned long long> d_tmacs;
   cudaEvent_t sev[4] = {nullptr, nullptr, nullptr, nullptr};
+
+  // Cauchy-Schwarz ERI screen (off while eps_eri < 0); bounds per C block,
+  // recomputed when C or V change
+  double eps_eri = -1.0;
+  bool eri_valid = false;
+  DevBuf<double> d_eri_sq;
 
   bool sym = false;             // V and D blocks all have transposed mirrors
   std::vector<int32_t> owner;   // shard: central atom -> rank (empty: no shard)
@@ -214,6 +222,7 @@ bool key_ok(const hfx_ctx *ctx, const int32_t *k) {
 
 void invalidate(hfx_ctx *ctx, int k, bool keys) {
   ctx->K[k].dirty = true;
+  if (k < 2) ctx->eri_valid = false;
   if (keys) ctx->K[k].keys_changed = true;
   if (keys && k == 2) ctx->dz_nd = -1;
   ctx->results_valid = false;
@@ -258,6 +267,33 @@ hfx_status pack_kind(hfx_ctx *ctx, int k) {
       if (kv.second.chunk < 0) kv.second.chunk = id;
     K.pending.clear();
     K.pending.shrink_to_fit();
+  }
+  // free chunks no block refers to any more (every block they held was set
+  // again), so that a full re-set of a kind leaves one chunk to adopt
+  {
+    std::vector<char> used(K.chunks.size(), 0);
+    for (auto &kv : K.map)
+      if (kv.second.chunk >= 0) used[kv.second.chunk] = 1;
+    std::vector<int32_t> remap(K.chunks.size(), -1);
+    std::vector<Chunk> keep;
+    for (size_t c = 0; c < K.chunks.size(); ++c) {
+      if (used[c]) {
+        remap[c] = (int32_t)keep.size();
+        keep.push_back(K.chunks[c]);
+        continue;
+      }
+      if (K.data_is_chunk && K.chunks[c].dev == K.data.p) {
+        K.data.p = nullptr;
+        K.data.n = 0;
+        K.data_is_chunk = false;
+      }
+      if (K.chunks[c].dev) cudaFree(K.chunks[c].dev);
+    }
+    if (keep.size() != K.chunks.size()) {
+      K.chunks.swap(keep);
+      for (auto &kv : K.map)
+        if (kv.second.chunk >= 0) kv.second.chunk = remap[kv.second.chunk];
+    }
   }
   const int64_t nblk = (int64_t)K.map.size();
   K.keys.clear();
@@ -722,6 +758,50 @@ SplitShared split_shared(hfx_ctx *ctx) {
   return S;
 }
 
+// Cauchy-Schwarz ERI bounds sqrt(max(Q, 0)) per C block (k_diag_eri): the
+// V blocks XX, XY, YX, YY and the partner C block of every C block (x, y, n).
+hfx_status eri_prepare(hfx_ctx *ctx) {
+  const Kind &C = ctx->K[0], &V = ctx->K[1];
+  cudaStream_t st = ctx->stream;
+  const int64_t nC = (int64_t)C.keys.size();
+  auto findk = [](const std::vector<uint64_t> &keys, uint64_t k) -> int64_t {
+    auto it = std::lower_bound(keys.begin(), keys.end(), k);
+    return (it != keys.end() && *it == k) ? (int64_t)(it - keys.begin()) : -1;
+  };
+  std::vector<int64_t> meta(5 * std::max<int64_t>(nC, 1), -1);
+  std::vector<int32_t> cxy(2 * std::max<int64_t>(nC, 1), 0);
+  for (int64_t e = 0; e < nC; ++e) {
+    int32_t q[5];
+    hk_unpack(C.keys[e], q);
+    const int x = q[0], y = q[1];
+    cxy[2 * e] = x;
+    cxy[2 * e + 1] = y;
+    meta[5 * e] = findk(V.keys, hk_pack(x, x, 0, 0, 0));
+    const bool same = x == y && q[2] == 0 && q[3] == 0 && q[4] == 0;
+    if (!same) {
+      meta[5 * e + 1] = findk(V.keys, hk_pack(x, y, q[2], q[3], q[4]));
+      meta[5 * e + 2] = findk(V.keys, hk_pack(y, x, -q[2], -q[3], -q[4]));
+      meta[5 * e + 3] = findk(V.keys, hk_pack(y, y, 0, 0, 0));
+      meta[5 * e + 4] = findk(C.keys, hk_pack(y, x, -q[2], -q[3], -q[4]));
+    }
+  }
+  DevBuf<int64_t> d_meta;
+  DevBuf<int32_t> d_cxy;
+  CK(d_meta.reserve(meta.size()));
+  CK(d_cxy.reserve(cxy.size()));
+  CK(ctx->d_eri_sq.reserve(std::max<int64_t>(nC, 1)));
+  CK(cudaMemcpyAsync(d_meta.p, meta.data(), sizeof(int64_t) * meta.size(), cudaMemcpyHostToDevice,
+                     st));
+  CK(cudaMemcpyAsync(d_cxy.p, cxy.data(), sizeof(int32_t) * cxy.size(), cudaMemcpyHostToDevice,
+                     st));
+  CK(launch_diag_eri(C.data.p, C.d_offs.p, V.data.p, V.d_offs.p, d_meta.p, d_cxy.p,
+                     ctx->d_nao.p, ctx->d_nabf.p, nC, ctx->d_eri_sq.p, st));
+  ctx->launches += nC > 0;
+  CK(cudaStreamSynchronize(st));  // meta and cxy are freed on return
+  ctx->eri_valid = true;
+  return HFX_OK;
+}
+
 size_t scratch_budget_doubles() {
   size_t freeb = 0, totalb = 0;
   cudaMemGetInfo(&freeb, &totalb);
@@ -952,6 +1032,10 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
     hfx_status s = build_plan(ctx);
     if (s != HFX_OK) return s;
   }
+  if (ctx->eps_eri >= 0.0 && !ctx->eri_valid) {
+    hfx_status s = eri_prepare(ctx);
+    if (s != HFX_OK) return s;
+  }
   // ---- screen (retry with a larger Sigma key table on overflow)
   CK(ctx->d_masks.reserve(ctx->nmask));
   CK(ctx->d_wg.reserve(ctx->nwg));
@@ -987,6 +1071,8 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
     a.sig_count = ctx->d_counters.p + 7;
     a.sig_limit = ctx->stab_cap / 2;
     a.counters = ctx->d_counters.p;
+    a.eri_sq = ctx->eps_eri >= 0.0 ? ctx->d_eri_sq.p : nullptr;
+    a.eps_eri = ctx->eps_eri;
     a.err = ctx->d_err.p;
     CK(cudaEventRecord(ctx->kev[8], st));
     CK(launch_screen(a, st));
@@ -1069,9 +1155,10 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
     CK(split_dz_prepare(SS, nslices, st));
     ctx->launches += 2 * (SS.h_nd > 0);
     CK(ctx->d_njobs.reserve(4));
-    CK(ctx->d_tmacs.reserve(3));
+    CK(ctx->d_tmacs.reserve(4));
   }
-  double tmac_y = 0, tmac_v4 = 0, tmac_z = 0;
+  double tmac_y = 0, tmac_v4 = 0, tmac_z = 0, umac_z = 0;
+  double zc_tmax = 0, zc_tavg = 0;  // summed over the waves' D_FG / D_FB launches
   // D_FG and D_FB pieces on the tensor cores (HFX_ZJOBS=0 keeps them in FP64)
   const char *zenv = std::getenv("HFX_ZJOBS");
   const bool zjobs = split && !(zenv && zenv[0] == '0');
@@ -1171,6 +1258,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
       c.err = ctx->d_err.p;
       c.sym = ctx->sym ? 1 : 0;
       int nl = 0;
+      int zc_ctas = 0;
       SplitWave SW{};
       if (split) {
         // per-wave split metadata
@@ -1220,7 +1308,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         CK(ctx->d_jobs.reserve(std::max<int64_t>(ycand[nw], 1)));
         CK(ctx->d_jobs4.reserve(std::max<int64_t>(v4max, 1)));
         CK(cudaMemsetAsync(ctx->d_njobs.p, 0, 4 * sizeof(int), st));
-        CK(cudaMemsetAsync(ctx->d_tmacs.p, 0, 3 * sizeof(unsigned long long), st));
+        CK(cudaMemsetAsync(ctx->d_tmacs.p, 0, 4 * sizeof(unsigned long long), st));
         SW.w0 = (int64_t)w0;
         SW.nw = (int32_t)nw;
         SW.scratch = ctx->d_scratch.p;
@@ -1267,12 +1355,33 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         ctx->launches += (SW.h_pgcand > 0) + (SW.h_v4cand > 0) + 1;
       }
       if (split && zjobs) {
-        // D_FG and D_FB pieces: count jobs and entries, size the lists, plan and run
+        // D_FG and D_FB pieces: count jobs and entries and histogram their cost
+        // keys, size the lists, place the jobs longest first (Algorithm 6's
+        // order), plan and run
+        constexpr int NKEYS = 256;
+        CK(ctx->d_zckeys.reserve(NKEYS));
+        CK(ctx->d_ctans.reserve(std::max(ctx->nsm, 1)));
+        CK(cudaMemsetAsync(ctx->d_zckeys.p, 0, NKEYS * sizeof(int), st));
+        SW.zc_keys = ctx->d_zckeys.p;
+        SW.cta_ns = ctx->d_ctans.p;
         CK(cudaEventRecord(ctx->kev[8], st));
         CK(split_zc_plan(SS, SW, 0, st));
         int nz[2] = {0, 0};
+        std::vector<int> hist(NKEYS, 0);
         CK(cudaMemcpyAsync(nz, ctx->d_njobs.p + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(hist.data(), ctx->d_zckeys.p, NKEYS * sizeof(int),
+                           cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        {
+          int off = 0;
+          for (int key = NKEYS - 1; key >= 0; --key) {
+            const int c = hist[key];
+            hist[key] = off;
+            off += c;
+          }
+        }
+        CK(cudaMemcpyAsync(ctx->d_zckeys.p, hist.data(), NKEYS * sizeof(int),
+                           cudaMemcpyHostToDevice, st));
         CK(ctx->d_zcjobs.reserve(std::max(nz[0], 1)));
         CK(ctx->d_zcents.reserve(std::max(nz[1], 1)));
         CK(cudaMemsetAsync(ctx->d_njobs.p + 2, 0, 2 * sizeof(int), st));
@@ -1283,6 +1392,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         CK(split_zc_run(SS, SW, nslices, ctx->zc_shape, ctx->nsm, st));
         CK(cudaEventRecord(ctx->kev[9], st));
         ctx->launches += 2 * (nw > 0) + (nz[0] > 0);
+        zc_ctas = nz[0] > 0 ? (int)std::min<int64_t>(nz[0], ctx->nsm) : 0;
       }
       // the host offsets vector is reused next wave: order the copy first
       CK(cudaStreamSynchronize(st));
@@ -1301,12 +1411,27 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
           cudaEventElapsedTime(&ms, ctx->kev[8], ctx->kev[9]);
           kms[4] += ms;
         }
-        unsigned long long tm[3] = {0, 0, 0};
+        unsigned long long tm[4] = {0, 0, 0, 0};
         CK(cudaMemcpyAsync(tm, ctx->d_tmacs.p, sizeof(tm), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         tmac_y += (double)tm[0];
         tmac_v4 += (double)tm[1];
         tmac_z += (double)tm[2];
+        umac_z += (double)tm[3];
+        if (zc_ctas > 0) {
+          // load balance of this launch: largest and mean CTA busy time
+          std::vector<long long> ns(zc_ctas);
+          CK(cudaMemcpyAsync(ns.data(), ctx->d_ctans.p, sizeof(long long) * zc_ctas,
+                             cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+          double mx = 0, sum = 0;
+          for (long long v : ns) {
+            mx = std::max(mx, (double)v);
+            sum += (double)v;
+          }
+          zc_tmax += mx;
+          zc_tavg += sum / zc_ctas;
+        }
       }
       ++nwaves;
       w0 = w1;
@@ -1348,6 +1473,8 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
   S.canonical_flops = 2.0 * (double)counters[5];
   for (int v = 0; v < 4; ++v) S.canonical_flops_piece[v] = 2.0 * (double)counters[16 + v];
   S.canonical_flops_y = 2.0 * (double)counters[20];
+  S.eps_eri = ctx->eps_eri;
+  S.n_eri_removed = (int64_t)counters[21];
   double macs = 0;
   for (int q = 0; q < 7; ++q) macs += (double)kmacs[q];
   S.executed_flops = 2.0 * macs;
@@ -1369,6 +1496,12 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
     S.kernel_flops[4] += 2.0 * tmac_z;
     S.executed_flops += 2.0 * tmac_z;
     S.kernel_tensor_flops[4] = 2.0 * tmac_z * pairs;
+    // FP64-equivalent work of the tensor products without padding or zero
+    // tiles: the Y product's canonical count, the D_FG / D_FB products' count
+    // from the job plan
+    S.kernel_unpadded_flops[1] = S.canonical_flops_y;
+    S.kernel_unpadded_flops[4] = 2.0 * umac_z;
+    S.zc_dt_max_over_avg = zc_tavg > 0 ? zc_tmax / zc_tavg : 0.0;
   }
   S.ms_screen = ms01;
   S.ms_contract = ms12;
@@ -1392,6 +1525,15 @@ hfx_status hfx_build_batch(hfx_ctx **cells, int32_t ncells, const double *thetas
     if (s != HFX_OK) return s;
     if (ex_out) ex_out[c] = ex;
   }
+  return HFX_OK;
+}
+
+hfx_status hfx_set_eri_screen(hfx_ctx *ctx, double eps_eri) {
+  if (!ctx) return HFX_E_ARG;
+  if (std::isnan(eps_eri) || std::isinf(eps_eri))
+    return fail(ctx, HFX_E_ARG, "eps_eri must be finite (negative turns the screen off)");
+  ctx->eps_eri = eps_eri < 0.0 ? -1.0 : eps_eri;
+  ctx->results_valid = false;
   return HFX_OK;
 }
 

@@ -200,8 +200,8 @@ __global__ void __launch_bounds__(kThreads) k_v1(ContractArgs A) {
   for (int q = 0; q < kMaxOut; ++q) {
     const int o = threadIdx.x + q * kThreads;
     if (o >= nout) break;
-    if (off >= 0) fx_add(A.acc + 2 * (off + o), -acc[q]);
-    if (moff >= 0) fx_add(A.acc + 2 * (moff + (o % nb) * na + o / nb), -acc[q]);
+    if (off >= 0) fx_add(A.acc + 2 * (off + o), -acc[q], A.err);
+    if (moff >= 0) fx_add(A.acc + 2 * (moff + (o % nb) * na + o / nb), -acc[q], A.err);
   }
   if (threadIdx.x == 0) atomicAdd(A.macs + 3, macs);
 }
@@ -261,8 +261,8 @@ __global__ void __launch_bounds__(kThreads) k_v2(ContractArgs A) {
   for (int q = 0; q < kMaxOut; ++q) {
     const int o = threadIdx.x + q * kThreads;
     if (o >= nout) break;
-    if (off >= 0) fx_add(A.acc + 2 * (off + o), -acc[q]);
-    if (moff >= 0) fx_add(A.acc + 2 * (moff + (o % ng) * na + o / ng), -acc[q]);
+    if (off >= 0) fx_add(A.acc + 2 * (off + o), -acc[q], A.err);
+    if (moff >= 0) fx_add(A.acc + 2 * (moff + (o % ng) * na + o / ng), -acc[q], A.err);
   }
   if (threadIdx.x == 0) atomicAdd(A.macs + 5, macs);
 }
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(kThreads) k_v3(ContractArgs A) {
     for (int q = 0; q < kMaxOut; ++q) {
       const int o = threadIdx.x + q * kThreads;
       if (o >= nout) break;
-      fx_add(A.acc + 2 * (off + o), -acc[q]);
+      fx_add(A.acc + 2 * (off + o), -acc[q], A.err);
     }
   if (threadIdx.x == 0) atomicAdd(A.macs + 4, macs);
 }
@@ -357,8 +357,8 @@ __global__ void __launch_bounds__(kThreads) k_v4(ContractArgs A) {
       const int f = o / ng, g = o - f * ng;
       double s = 0.0;
       for (int r = 0; r < K; ++r) s = fma(Caf[(int64_t)r * nf + f], P[(int64_t)r * ncol + g], s);
-      if (off >= 0) fx_add(A.acc + 2 * (off + o), -s);
-      if (moff >= 0) fx_add(A.acc + 2 * (moff + g * nf + f), -s);
+      if (off >= 0) fx_add(A.acc + 2 * (off + o), -s, A.err);
+      if (moff >= 0) fx_add(A.acc + 2 * (moff + g * nf + f), -s, A.err);
     }
     macs += (unsigned long long)nout * K;
   }

@@ -87,9 +87,15 @@ struct DevBlocks {
 // x is split as hi * 2^-32 + lo * 2^-64 with hi = rint(x 2^32) and
 // lo = rint((x 2^32 - hi) 2^32); both are added with integer atomics, which
 // are associative, so the sum does not depend on the order of arrival.
-// |x| < 2^31 per contribution; the per-contribution error is <= 2^-65.
+// |x| < 2^31 per contribution; the per-contribution error is <= 2^-65.  A
+// contribution outside that range (or NaN) is not added: the adder records
+// HFX_DEV_ERR_BOUNDS in *err and the build fails with an error status.
 // ---------------------------------------------------------------------------
-__device__ inline void fx_add(unsigned long long *hi_lo, double x) {
+__device__ inline void fx_add(unsigned long long *hi_lo, double x, unsigned *err) {
+  if (!(fabs(x) < 2147483648.0)) {
+    atomicOr(err, 8u);  // HFX_DEV_ERR_BOUNDS
+    return;
+  }
   double s = x * 4294967296.0;  // exact
   double h = rint(s);
   double r = (s - h) * 4294967296.0;  // s - h exact
@@ -132,7 +138,11 @@ struct ScreenArgs {
   uint64_t sig_mask;
   unsigned long long *sig_count;
   unsigned long long sig_limit;
-  unsigned long long *counters;  // [0..3] survivors per variant, [4] active (A,B,G), [5] canonical MACs
+  unsigned long long *counters;  // [0..3] survivors per variant, [4] active (A,B,G), [5] canonical MACs,
+                                 // [16..19] canonical MACs per piece, [20] Y MACs,
+                                 // [21] quadruples (A,B,F,G) removed by the ERI screen
+  const double *eri_sq;    // per C block sqrt(max(Q, 0)) of the ERI screen; null: screen off
+  double eps_eri;
   unsigned *err;
 };
 
@@ -167,6 +177,14 @@ struct ContractArgs {
 cudaError_t launch_maxabs(const double *data, const int64_t *offs, int64_t nblk, double *out,
                           unsigned *err, cudaStream_t st);
 cudaError_t launch_screen(const ScreenArgs &a, cudaStream_t st);
+// Cauchy-Schwarz ERI screen: per C block e (atoms cxy[2e], cxy[2e+1]) the
+// largest diagonal ERI of its AO pairs under the LRI expansion, from the V
+// blocks meta[5e .. 5e+3] (XX, XY, YX, YY; -1 = absent) and the partner C
+// block meta[5e+4] (-1 = absent or the same site); writes sqrt(max(Q, 0)).
+cudaError_t launch_diag_eri(const double *Cd, const int64_t *Co, const double *Vd,
+                            const int64_t *Vo, const int64_t *meta, const int32_t *cxy,
+                            const int32_t *nao, const int32_t *nabf, int64_t nC, double *sq,
+                            cudaStream_t st);
 cudaError_t launch_collect_keys(const unsigned long long *keys, uint64_t cap,
                                 unsigned long long *out, unsigned long long *n, cudaStream_t st);
 // Launches the seven FP64 contraction kernels; ev (8 events or null) is recorded

@@ -24,7 +24,41 @@ static __device__ __align__(256) double g_noalloc_scratch[2 * kHalf];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
+// Per device: the CUDA context the address was looked up in (its process-wide
+// unique id, 0 = none yet) and the address.  A static __device__ array has one
+// copy per context, so a cached address is only valid in the context it came
+// from: after cudaDeviceReset (a new primary context) or under another context
+// made current with the driver API, the address is looked up again.
+unsigned long long g_scratch_ctx[kMaxDevices] = {0};
 double *g_scratch_ptr[kMaxDevices] = {nullptr};
+
+typedef int (*CtxGetCurrentFn)(void **);
+typedef int (*CtxGetIdFn)(void *, unsigned long long *);
+
+// Id of the current context (0 when none is current or the driver calls are
+// unavailable; the lookup then runs on every call).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    cudaDriverEntryPointQueryResult q1, q2;
+    void *f1 = nullptr, *f2 = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) ==
+            cudaSuccess && q1 == cudaDriverEntryPointSuccess &&
+        cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) ==
+            cudaSuccess && q2 == cudaDriverEntryPointSuccess) {
+      get_current = (CtxGetCurrentFn)f1;
+      get_id = (CtxGetIdFn)f2;
+    }
+    resolved = true;
+  }
+  if (!get_current || !get_id) return 0;
+  void *c = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&c) != 0 || !c || get_id(c, &id) != 0) return 0;
+  return id;
+}
 
 // Y[al][j][l] = sum_be V[al][be] cB[be][j][l]
 __global__ void k_term_y(int pA, int pB, int nj, int nl, const double *V, const double *cB,
@@ -70,19 +104,24 @@ __global__ void k_term_out(int pA, int ni, int nj, int nk, const double *cA, con
   }
 }
 
-// Device address of the static array for the current device, looked up once
-// per device (host code may not use the array's name as a device pointer).
+// Device address of the static array in the current context, looked up once
+// per device and context (host code may not use the array's name as a device
+// pointer).  The first call on a device, and the first after a device reset,
+// does the lookup; make it outside stream capture.
 cudaError_t scratch_for_current_device(double **out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
+  if (!g_scratch_ptr[dev] || ctx == 0 || g_scratch_ctx[dev] != ctx) {
     void *p = nullptr;
+    // makes the device's primary context current when no context is
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
     g_scratch_ptr[dev] = (double *)p;
+    g_scratch_ctx[dev] = current_context_id();
   }
   *out = g_scratch_ptr[dev];
   return cudaSuccess;
@@ -100,6 +139,8 @@ extern "C" hfx_status hfx_term_noalloc(int32_t nabf_a, int32_t nabf_b, int32_t n
   // both intermediates must fit their half of the static array
   if ((int64_t)nabf_a * nao_j * nao_l > kHalf || (int64_t)nabf_a * nao_j * nao_k > kHalf)
     return HFX_E_SHAPE;
+  // the output kernel indexes ni * nj outputs in 32-bit arithmetic
+  if ((int64_t)nao_i * nao_j > 2147483647ll) return HFX_E_SHAPE;
   double *scratch = nullptr;
   if (scratch_for_current_device(&scratch) != cudaSuccess) return HFX_E_CUDA;
   cudaStream_t st = (cudaStream_t)cuda_stream;

@@ -355,8 +355,8 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
           if (!live) continue;
           const int g = cG - gpre;
           const int e = ea + eb_p[c0 + i] - SH;
-          if (off >= 0) fx_add_scaled(S.acc + 2 * (off + (int64_t)f * ng + g), -Wv[i], e);
-          if (moff >= 0) fx_add_scaled(S.acc + 2 * (moff + (int64_t)g * nf + f), -Wv[i], e);
+          if (off >= 0) fx_add_scaled(S.acc + 2 * (off + (int64_t)f * ng + g), -Wv[i], e, S.err);
+          if (moff >= 0) fx_add_scaled(S.acc + 2 * (moff + (int64_t)g * nf + f), -Wv[i], e, S.err);
         }
       }
     }

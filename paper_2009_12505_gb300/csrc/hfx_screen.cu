@@ -7,8 +7,14 @@
 //    D_FG -> Sigma_AB, D_FB -> Sigma_AG, D_AG -> Sigma_FB, D_AB -> Sigma_FG)
 //    it evaluates S = (max|C_AF| max|C_BG|)(max|V_AB| max|D_src|) with
 //    round-to-nearest multiplies in that association and keeps the term iff
-//    S > theta (strict, as Algorithm 4).  Survivors become bits of four
-//    F-bitmasks per (A,B,G); their Sigma keys go into a hash set.
+//    S > theta (strict, as Algorithm 4).  With the Cauchy-Schwarz ERI screen
+//    on (Sec. III.C, Eq. CS-ERI) a quadruple (A,B,F,G) also needs
+//    sqrt(Q_AF) sqrt(Q_BG) > eps_eri, else all four of its terms go.
+//    Survivors become bits of four F-bitmasks per (A,B,G); their Sigma keys go
+//    into a hash set.
+//  * k_diag_eri: one block per C block, the largest diagonal ERI Q of its AO
+//    pairs (phi_Xa phi_Yf | phi_Xa phi_Yf) under the LRI expansion of the pair
+//    on the ABFs of X and of Y (Eq. LRI), in FP64.
 #include "hfx_internal.h"
 
 __global__ void k_maxabs(const double *__restrict__ data, const int64_t *__restrict__ offs,
@@ -27,6 +33,62 @@ __global__ void k_maxabs(const double *__restrict__ data, const int64_t *__restr
   for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, HFX_DEV_ERR_NONFINITE);
   if (lane == 0) out[warp] = m;
+}
+
+// u^T V w over one V block ([nu][nw] row-major, nullptr = absent), with u and
+// w strided views into C blocks.
+__device__ inline double vform(const double *V, const double *u, int64_t su, int nu,
+                               const double *w, int64_t sw, int nw) {
+  if (!V) return 0.0;
+  double q = 0.0;
+  for (int al = 0; al < nu; ++al) {
+    const double *row = V + (int64_t)al * nw;
+    double t = 0.0;
+    for (int be = 0; be < nw; ++be) t = fma(row[be], w[be * sw], t);
+    q = fma(u[al * su], t, q);
+  }
+  return q;
+}
+
+// The pair (X a, Y f) of C block (x, y, n) expands as sum_alpha C_XY[alpha][a][f]
+// P_X alpha + sum_beta C_YX[beta][f][a] P_Y beta; its diagonal ERI is that
+// vector's V-norm: u^T V_XX u + u^T V_XY w + w^T V_YX u + w^T V_YY w.
+__global__ void __launch_bounds__(128) k_diag_eri(const double *Cd, const int64_t *Co,
+                                                  const double *Vd, const int64_t *Vo,
+                                                  const int64_t *meta, const int32_t *cxy,
+                                                  const int32_t *nao, const int32_t *nabf,
+                                                  double *sq) {
+  __shared__ double red[4];
+  const int64_t e = blockIdx.x;
+  const int x = cxy[2 * e], y = cxy[2 * e + 1];
+  const int px = nabf[x], py = nabf[y], nx = nao[x], ny = nao[y];
+  const int64_t *m = meta + 5 * e;
+  const double *VXX = m[0] >= 0 ? Vd + Vo[m[0]] : nullptr;
+  const double *VXY = m[1] >= 0 ? Vd + Vo[m[1]] : nullptr;
+  const double *VYX = m[2] >= 0 ? Vd + Vo[m[2]] : nullptr;
+  const double *VYY = m[3] >= 0 ? Vd + Vo[m[3]] : nullptr;
+  const double *CX = Cd + Co[e];
+  const double *CY = m[4] >= 0 ? Cd + Co[m[4]] : nullptr;
+  double qmax = -INFINITY;
+  for (int c = threadIdx.x; c < nx * ny; c += blockDim.x) {
+    const int a = c / ny, f = c - a * ny;
+    const double *u = CX + c;                    // u[alpha] at alpha nx ny
+    double q = vform(VXX, u, (int64_t)nx * ny, px, u, (int64_t)nx * ny, px);
+    if (CY) {
+      const double *w = CY + (int64_t)f * nx + a;  // w[beta] at beta ny nx
+      q += vform(VXY, u, (int64_t)nx * ny, px, w, (int64_t)ny * nx, py);
+      q += vform(VYX, w, (int64_t)ny * nx, py, u, (int64_t)nx * ny, px);
+      q += vform(VYY, w, (int64_t)ny * nx, py, w, (int64_t)ny * nx, py);
+    }
+    qmax = fmax(qmax, q);
+  }
+  for (int o = 16; o; o >>= 1) qmax = fmax(qmax, __shfl_xor_sync(0xffffffffu, qmax, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = qmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double q = fmax(fmax(red[0], red[1]), fmax(red[2], red[3]));
+    sq[e] = sqrt(q > 0.0 ? q : 0.0);
+  }
 }
 
 // Insert k into the mutable Sigma key table (open addressing, linear probe).
@@ -83,7 +145,8 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A) {
   const int pA = A.nabf[it.a];
   const int na = A.nao[it.a], nb = A.nao[it.b], ng = A.nao[gt];
   unsigned long long cnt[4] = {0, 0, 0, 0};
-  unsigned long long macs = 0, pm[4] = {0, 0, 0, 0};
+  unsigned long long macs = 0, pm[4] = {0, 0, 0, 0}, eri_cut = 0;
+  const double sqBG = A.eri_sq ? A.eri_sq[eg.cblk] : 0.0;
   unsigned any = 0;
   uint32_t *mrow = A.masks + it.mask_off + (int64_t)g * 4 * it.nFw;
   for (int f0 = 0; f0 < it.nF; f0 += 32) {
@@ -96,18 +159,23 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A) {
       nf = A.nao[ft];
       const bool f_is_a = (ft == it.a) && mF0 == 0 && mF1 == 0 && mF2 == 0;
       const double cc = __dmul_rn(A.C.maxabs[ef.cblk], mcBG);
-      // variant 1: D_FG -> Sigma_AB
-      const int64_t dFG = dfind(A.dhash, ft, gt, nG0 - mF0, nG1 - mF1, nG2 - mF2);
-      if (dFG >= 0) b1 = __dmul_rn(cc, __dmul_rn(mv, A.D.maxabs[dFG])) > A.theta;
-      // variant 2: D_FB -> Sigma_AG (not when G is B)
-      if (!g_is_b) {
-        const int64_t dFB = dfind(A.dhash, ft, it.b, it.n[0] - mF0, it.n[1] - mF1, it.n[2] - mF2);
-        if (dFB >= 0) b2 = __dmul_rn(cc, __dmul_rn(mv, A.D.maxabs[dFB])) > A.theta;
+      // the Cauchy-Schwarz ERI screen removes the whole quadruple
+      const bool eri_ok = !A.eri_sq || __dmul_rn(A.eri_sq[ef.cblk], sqBG) > A.eps_eri;
+      eri_cut += eri_ok ? 0 : 1;
+      if (eri_ok) {
+        // variant 1: D_FG -> Sigma_AB
+        const int64_t dFG = dfind(A.dhash, ft, gt, nG0 - mF0, nG1 - mF1, nG2 - mF2);
+        if (dFG >= 0) b1 = __dmul_rn(cc, __dmul_rn(mv, A.D.maxabs[dFG])) > A.theta;
+        // variant 2: D_FB -> Sigma_AG (not when G is B)
+        if (!g_is_b) {
+          const int64_t dFB = dfind(A.dhash, ft, it.b, it.n[0] - mF0, it.n[1] - mF1, it.n[2] - mF2);
+          if (dFB >= 0) b2 = __dmul_rn(cc, __dmul_rn(mv, A.D.maxabs[dFB])) > A.theta;
+        }
+        // variant 3: D_AG -> Sigma_FB (not when F is A)
+        if (!f_is_a && dAG >= 0) b3 = __dmul_rn(cc, mvAG) > A.theta;
+        // variant 4: D_AB -> Sigma_FG (neither)
+        if (!f_is_a && !g_is_b && it.dab >= 0) b4 = __dmul_rn(cc, mvAB) > A.theta;
       }
-      // variant 3: D_AG -> Sigma_FB (not when F is A)
-      if (!f_is_a && dAG >= 0) b3 = __dmul_rn(cc, mvAG) > A.theta;
-      // variant 4: D_AB -> Sigma_FG (neither)
-      if (!f_is_a && !g_is_b && it.dab >= 0) b4 = __dmul_rn(cc, mvAB) > A.theta;
     }
     const uint32_t w1 = __ballot_sync(0xffffffffu, b1);
     const uint32_t w2 = __ballot_sync(0xffffffffu, b2);
@@ -142,6 +210,8 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A) {
     for (int o = 16; o; o >>= 1) pm[v] += __shfl_xor_sync(0xffffffffu, pm[v], o);
     macs += pm[v];
   }
+  for (int o = 16; o; o >>= 1) eri_cut += __shfl_xor_sync(0xffffffffu, eri_cut, o);
+  if (lane == 0 && eri_cut) atomicAdd(&A.counters[21], eri_cut);
   if (lane == 0) {
     A.wg_flags[it.wg_off + g] = (uint8_t)any;
     if (any & 1u) sig_insert(A.sig_keys, A.sig_mask, hk_pack(it.a, it.b, it.n[0], it.n[1], it.n[2]),
@@ -187,6 +257,15 @@ cudaError_t launch_screen(const ScreenArgs &a, cudaStream_t st) {
   if (a.nwg <= 0) return cudaSuccess;
   const int64_t threads = a.nwg * 32;
   k_screen<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_eri(const double *Cd, const int64_t *Co, const double *Vd,
+                            const int64_t *Vo, const int64_t *meta, const int32_t *cxy,
+                            const int32_t *nao, const int32_t *nabf, int64_t nC, double *sq,
+                            cudaStream_t st) {
+  if (nC <= 0) return cudaSuccess;
+  k_diag_eri<<<(unsigned)nC, 128, 0, st>>>(Cd, Co, Vd, Vo, meta, cxy, nao, nabf, sq);
   return cudaGetLastError();
 }
 

@@ -103,6 +103,8 @@ struct SplitWave {
   Job *jobs, *jobs4;
   int *njobs;                      // [0] Y jobs, [1] D_AB jobs, [2] Z jobs, [3] Z entries
   unsigned long long *tmacs;       // [0] Y, [1] D_AB, [2] Z: multiply-adds of the launched jobs
+                                   // (per digit product, padding included); [3] Z: those that
+                                   // are neither padding nor zero tiles
   int64_t h_ycand, h_v4cand, h_prows, h_v4jobs_max;
   // Y as (hi, lo) f32 pairs in 16-column blocks, [cb][al][b][16], for the
   // D_FG / D_FB product epilogues and P; written only when y2_on (the region exists)
@@ -114,6 +116,11 @@ struct SplitWave {
   ZcJob *zc_jobs;
   ZcEnt *zc_ents;
   int64_t h_zc_jobs;
+  // 256 job-cost keys: the plan's count pass histograms them, the fill pass
+  // takes them as the start offsets of each key's range (longest first)
+  int *zc_keys;
+  // per CTA of the D_FG / D_FB product launch: its busy time in ns
+  long long *cta_ns;
 };
 
 cudaError_t split_slice_inputs(const SplitShared &S, int ks, cudaStream_t st);
@@ -121,7 +128,10 @@ cudaError_t split_slice_cz(const SplitShared &S, int ks, cudaStream_t st);
 // D digit tiles (needs S.de zeroed); run whenever D changes.
 cudaError_t split_dz_prepare(const SplitShared &S, int ks, cudaStream_t st);
 // D_FG / D_FB job plan for one wave: fill == 0 counts jobs and entries into
-// W.njobs[2], W.njobs[3]; fill == 1 writes W.zc_jobs and W.zc_ents.
+// W.njobs[2], W.njobs[3] and histograms the jobs' cost keys into W.zc_keys
+// (256 ints, zeroed by the caller); fill == 1 writes W.zc_jobs (longest first:
+// W.zc_keys must then hold each key's start offset, keys in descending order)
+// and W.zc_ents.
 cudaError_t split_zc_plan(const SplitShared &S, const SplitWave &W, int fill, cudaStream_t st);
 // Launch shape of the D_FG / D_FB products: widest F block (16 or 32),
 // largest block output count, shared bytes of one staged Y block.

@@ -29,7 +29,9 @@
 // stored digit-major).  The epilogue adds the order groups (exact f32
 // integers times powers of two) in packed double-float arithmetic.
 //
-// Roles (one CTA per SM, persistent over a static round-robin job split):
+// Roles (one CTA per SM, persistent over the job list, which the plan writes
+// longest first and the CTAs deal out among themselves in snake order; each
+// CTA records its busy time so the host can report the load balance):
 // warp 8 streams A and B tiles with 1-D bulk copies into a ring of shared
 // stages; warp 9 issues the MMAs into one of two TMEM accumulators; warp 10
 // copies the Y rows of each tile (f32 pairs, laid out [16-column block][al]
@@ -162,22 +164,43 @@ __global__ void k_dz_slice(SplitShared S) {
 
 // ---------------------------------------------------------------- job plan
 
+// Cost key of a job (Algorithm 6's processing time, in 256 buckets): row
+// tiles x operand stages of 16 K, a quarter per bucket.  The plan's count
+// pass histograms the keys, the host turns the histogram into descending
+// start offsets, and the fill pass places each job in its key's range, so the
+// list runs longest first (longest-processing-time order).
+constexpr int ZC_NKEYS = 256;
+__device__ __forceinline__ int zc_cost_key(int mtz, int k) {
+  return min(ZC_NKEYS - 1, (mtz * (k / 16) + 3) / 4);
+}
+
+// Job handed to CTA b in round r of the persistent loop: rounds alternate
+// direction (snake order), so over a longest-first list every CTA gets a
+// similar mix of long and short jobs.  The last round is partial.
+__device__ __forceinline__ int zc_job_of(int r, int b, int G) {
+  return r * G + ((r & 1) ? G - 1 - b : b);
+}
+
 // Runs of the union of a group's surviving F with at most ZC_KMAX K each: one
 // job per run.  Called by one lane per group.  fill == 0 only counts.
 __device__ void zc_plan_group(const SplitShared &S, const SplitWave &W, const WorkItem &it,
                               int32_t w, const int (&bg)[2], const int (&bp)[2], int nblk,
-                              int mtz, int fill, unsigned long long &macs) {
+                              int mtz, int fill, unsigned long long &macs,
+                              unsigned long long &umacs) {
   const uint32_t *mr[2] = {nullptr, nullptr};
   for (int q = 0; q < nblk; ++q)
     mr[q] = S.masks + it.mask_off + ((int64_t)bg[q] * 4 + (bp[q] - 1)) * it.nFw;
   int64_t eg_n[2][4];
+  int ncv[2] = {0, 0};  // Z columns of each block
   for (int q = 0; q < nblk; ++q) {
     const NbrEntry eg = S.nbr[it.gbase + bg[q]];
     eg_n[q][0] = eg.other;
     eg_n[q][1] = eg.n[0];
     eg_n[q][2] = eg.n[1];
     eg_n[q][3] = eg.n[2];
+    ncv[q] = bp[q] == 1 ? S.nao[eg.other] : S.nao[it.b];
   }
+  const unsigned long long rows = (unsigned long long)S.nabf[it.a] * S.nao[it.a];
   // cursor over the union bits: word wd, remaining bits u
   int wd = 0;
   uint32_t u = 0;
@@ -211,12 +234,15 @@ __device__ void zc_plan_group(const SplitShared &S, const SplitWave &W, const Wo
       ma = next(fa);
     }
     macs += (unsigned long long)mtz * 128 * ZC_COLS * k;
+    const int key = zc_cost_key(mtz, k);
     int64_t eo = 0;
     if (!fill) {
       atomicAdd(W.njobs + 2, 1);
       atomicAdd(W.njobs + 3, n);
+      atomicAdd(W.zc_keys + key, 1);
     } else {
-      const int js = atomicAdd(W.njobs + 2, 1);
+      atomicAdd(W.njobs + 2, 1);
+      const int js = atomicAdd(W.zc_keys + key, 1);  // next slot of this key's range
       eo = (int64_t)atomicAdd(W.njobs + 3, n);
       ZcJob jb{};
       jb.w = w;
@@ -249,8 +275,13 @@ __device__ void zc_plan_group(const SplitShared &S, const SplitWave &W, const Wo
           else
             d = dh_find(S.dhash, hk_pack(ef.other, it.b, it.n[0] - ef.n[0], it.n[1] - ef.n[1],
                                          it.n[2] - ef.n[2]));
-          if (d < 0) atomicOr(S.err, HFX_DEV_ERR_MISSING);
-          else en.dz[c] = S.dz_off[d];
+          if (d < 0) {
+            atomicOr(S.err, HFX_DEV_ERR_MISSING);
+          } else {
+            en.dz[c] = S.dz_off[d];
+            // products that are not padding or zero tiles
+            umacs += rows * (unsigned long long)S.nao[ef.other] * ncv[c];
+          }
         }
         W.zc_ents[eo + q] = en;
         if (q + 1 < n) next(fe);
@@ -277,7 +308,7 @@ __global__ void __launch_bounds__(128) k_zc_plan(SplitShared S, SplitWave W, int
   const WorkItem it = S.items[W.w0 + wl];
   const int pA = S.nabf[it.a], na = S.nao[it.a], nb = S.nao[it.b];
   const int mtz = (pA * na + 127) / 128;
-  unsigned long long macs = 0;
+  unsigned long long macs = 0, umacs = 0;
   // lane 0 state: cursor (g, piece) and the open group
   int g = 0, piece = 1, nblk = 0, rows = 0, cg[2] = {0, 0}, cp[2] = {0, 0};
   bool finished = false;
@@ -329,13 +360,17 @@ __global__ void __launch_bounds__(128) k_zc_plan(SplitShared S, SplitWave W, int
     if (lane < cnt) {
       const int *o = sgrp[wib][lane];
       const int bg[2] = {o[0], o[2]}, bp[2] = {o[1], o[3]};
-      zc_plan_group(S, W, it, (int32_t)(W.w0 + wl), bg, bp, o[4], mtz, fill, macs);
+      zc_plan_group(S, W, it, (int32_t)(W.w0 + wl), bg, bp, o[4], mtz, fill, macs, umacs);
     }
     __syncwarp();
     if (fin) break;
   }
-  for (int o = 16; o; o >>= 1) macs += __shfl_xor_sync(0xffffffffu, macs, o);
+  for (int o = 16; o; o >>= 1) {
+    macs += __shfl_xor_sync(0xffffffffu, macs, o);
+    umacs += __shfl_xor_sync(0xffffffffu, umacs, o);
+  }
   if (fill && lane == 0 && macs) atomicAdd(W.tmacs + 2, macs);
+  if (fill && lane == 0 && umacs) atomicAdd(W.tmacs + 3, umacs);
 }
 
 // ---------------------------------------------------------------- product
@@ -510,6 +545,8 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tbase = ctl->tslot;
+  unsigned long long t_start = 0;
+  if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
 
   if (warp == ZC_EPI) {
     // ------------------------------------------------------------ A / B loader
@@ -518,7 +555,9 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
     // the stage, then lane 0 copies the A tile and lanes 1 .. nblk one whole
     // B block each
     long long step = 0;
-    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+    for (int r = 0;; ++r) {
+      const int j = zc_job_of(r, blockIdx.x, gridDim.x);
+      if (r * (int)gridDim.x >= njobs || j >= njobs) break;
       // one decision for the whole warp
       if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
       const ZcJob jb = W.zc_jobs[j];
@@ -595,7 +634,9 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
     // ------------------------------------------------------------ Y loader
     if constexpr (YST) {
       long long hand = 0;
-      for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+      for (int r = 0;; ++r) {
+        const int j = zc_job_of(r, blockIdx.x, gridDim.x);
+        if (r * (int)gridDim.x >= njobs || j >= njobs) break;
         if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
         const ZcJob jb = W.zc_jobs[j];
         const WorkItem it = S.items[jb.w];
@@ -653,7 +694,9 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         idesc32[i] = umma::idesc_bf16_f32(128, 32 * (KS - i));
       }
       const uint32_t sbase = umma::smem_u32(smem);
-      for (int j = blockIdx.x; j < njobs && !*abort_f; j += gridDim.x) {
+      for (int r = 0; !*abort_f; ++r) {
+        const int j = zc_job_of(r, blockIdx.x, gridDim.x);
+        if (r * (int)gridDim.x >= njobs || j >= njobs) break;
         const ZcJob jb = W.zc_jobs[j];
         const WorkItem it = S.items[jb.w];
         const int mtz = (S.nabf[it.a] * S.nao[it.a] + 127) / 128;
@@ -702,7 +745,9 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
     const int et = threadIdx.x;  // 0 .. ZC_ET - 1
     const int rs = cfg.rs;
     long long hand = 0;
-    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+    for (int r = 0;; ++r) {
+      const int j = zc_job_of(r, blockIdx.x, gridDim.x);
+      if (r * (int)gridDim.x >= njobs || j >= njobs) break;
       const ZcJob jb = W.zc_jobs[j];
       const WorkItem it = S.items[jb.w];
       const int wl = (int)(jb.w - W.w0);
@@ -918,9 +963,15 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         asm volatile("bar.sync 1, %0;" ::"r"(ZC_ET) : "memory");
       }
       if (aborted) break;
-      // add the finished blocks to Sigma (and mirrors)
+      // add the finished blocks to Sigma (and mirrors); a sum outside the
+      // fixed-point range is not added and fails the build
+      bool inrange = true;
 #pragma unroll
-      for (int k = 0; k < ZC_OWN; ++k) {
+      for (int k = 0; k < ZC_OWN; ++k)
+        if (et + k * ZC_ET < nown) inrange = inrange && fx_df_in_range(jh[k]);
+      if (!inrange) atomicOr(S.err, HFX_DEV_ERR_BOUNDS);
+#pragma unroll
+      for (int k = 0; k < ZC_OWN && inrange; ++k) {
         const int idx = et + k * ZC_ET;
         if (idx >= nown) break;
         const bool b1 = idx >= own0;
@@ -952,6 +1003,11 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
   umma::fence_before_sync();
   __syncthreads();
   if (warp == 0) umma::tmem_dealloc(tbase, 512);
+  if (threadIdx.x == 0) {
+    unsigned long long t_end;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+    W.cta_ns[blockIdx.x] = (long long)(t_end - t_start);
+  }
 }
 
 // Y staged in shared memory (two buffers per block) with a shorter operand

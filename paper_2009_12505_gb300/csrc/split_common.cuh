@@ -50,9 +50,16 @@ __device__ __forceinline__ void to_digits_i64(long long X, int (&d)[KS]) {
 }
 
 // Add W * 2^e to a fixed-point Sigma element (hi: 2^-32 units, lo: 2^-64
-// units) with integer arithmetic; |W 2^e| < 2^31.
-__device__ __forceinline__ void fx_add_scaled(unsigned long long *hi_lo, long long W, int e) {
+// units) with integer arithmetic; |W 2^e| < 2^31, else nothing is added and
+// HFX_DEV_ERR_BOUNDS is recorded in *err.
+__device__ __forceinline__ void fx_add_scaled(unsigned long long *hi_lo, long long W, int e,
+                                              unsigned *err) {
   if (W == 0) return;
+  const unsigned long long mag = W < 0 ? 0ull - (unsigned long long)W : (unsigned long long)W;
+  if (64 - __clzll((long long)mag) + e > 31) {  // |W| 2^e >= 2^31 possible
+    atomicOr(err, 8u);
+    return;
+  }
   const int t = e + 64;  // W * 2^t in units of 2^-64
   __int128 V;
   if (t >= 0) {
@@ -107,7 +114,8 @@ __device__ __forceinline__ __int128 fx128_f32(float f) {
 }
 
 // Add -(v.x + v.y) (neg) or v.x + v.y to a fixed-point Sigma element
-// (hi: 2^-32 units, lo: 2^-64 units) with integer arithmetic only.
+// (hi: 2^-32 units, lo: 2^-64 units) with integer arithmetic only.  Requires
+// |v| < 2^31: the caller checks (fx_df_in_range) and records an error instead.
 __device__ __forceinline__ void fx_add_df(unsigned long long *hi_lo, float2 v, bool neg) {
   __int128 V = fx128_f32(v.x) + fx128_f32(v.y);
   if (neg) V = -V;
@@ -116,6 +124,9 @@ __device__ __forceinline__ void fx_add_df(unsigned long long *hi_lo, float2 v, b
   if (hi) atomicAdd(hi_lo, (unsigned long long)hi);
   if (lo) atomicAdd(hi_lo + 1, (unsigned long long)lo);
 }
+
+// fx_add_df's range: |h| < 2^31 (false for NaN).
+__device__ __forceinline__ bool fx_df_in_range(float h) { return fabsf(h) < 2147483648.f; }
 
 // (sh, sl) += (ah, al) * (bh, bl), error-free products and sums (no
 // contraction: every operation is an explicit round-to-nearest intrinsic).

@@ -39,7 +39,10 @@ class Stats(ctypes.Structure):
                 ("kernel_ms", ctypes.c_double * 8), ("kernel_flops", ctypes.c_double * 8),
                 ("n_launches", ctypes.c_int64), ("mirror", ctypes.c_int32),
                 ("nslices", ctypes.c_int32), ("kernel_tensor_flops", ctypes.c_double * 8),
-                ("canonical_flops_piece", ctypes.c_double * 4), ("canonical_flops_y", ctypes.c_double)]
+                ("canonical_flops_piece", ctypes.c_double * 4), ("canonical_flops_y", ctypes.c_double),
+                ("kernel_unpadded_flops", ctypes.c_double * 8),
+                ("zc_dt_max_over_avg", ctypes.c_double), ("eps_eri", ctypes.c_double),
+                ("n_eri_removed", ctypes.c_int64)]
 
 KERNELS = ["screen", "Y", "Dstage", "Q", "v1_DFG", "v3_DAG", "v2_DFB", "v4_DAB"]
 
@@ -76,10 +79,12 @@ def load_library():
             "hfx_last_error": (ctypes.c_char_p, [P]),
             "hfx_term_noalloc": (S, [i32, i32, i32, i32, i32, i32, P, P, P, P, P, P]),
             "hfx_set_shard": (S, [P, P, i32]),
+            "hfx_set_eri_screen": (S, [P, f64]),
             "hfx_get_H_fixed": (S, [P, P, ctypes.c_int]),
             "hfx_set_H_fixed": (S, [P, P, ctypes.c_int, P]),
             "hfx_selftest_ozaki": (S, [i32, i32, i32, P, P, P, i32]),
             "hfx_selftest_timeout": (S, [i64, P]),
+            "hfx_probe_fp64": (S, [P, P]),
             "hfx_build_batch": (S, [P, i32, P, ctypes.c_int, i32, P]),
             "hfx_density_from_eigvecs": (S, [P, i32, P, i32, P, P, i64, P, P, P]),
             "hfx_sigma_k": (S, [P, i32, P, P]),
@@ -137,6 +142,16 @@ def selftest_timeout(limit_cycles: int):
     w = ctypes.c_int64(0)
     rc = lib.hfx_selftest_timeout(int(limit_cycles), ctypes.byref(w))
     return int(rc), int(w.value)
+
+
+def probe_fp64():
+    """(DFMA TFLOP/s, FP64 tensor-core TFLOP/s) measured on the current device."""
+    lib = load_library()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = lib.hfx_probe_fp64(ctypes.byref(a), ctypes.byref(b))
+    if rc != 0:
+        raise HfxError(rc, "hfx_probe_fp64 failed")
+    return a.value, b.value
 
 
 def term_noalloc(cA, V, cB, D, out, stream=None):
@@ -293,6 +308,12 @@ class Context:
         self._check(self._lib.hfx_get_H(self._h, i, j, _p(nn), _p(out)))
         return out
 
+    def set_eri_screen(self, eps_eri):
+        """Cauchy-Schwarz ERI screen at eps_eri for the next builds (None or a
+        negative value: off)."""
+        self._check(self._lib.hfx_set_eri_screen(self._h, -1.0 if eps_eri is None
+                                                 else float(eps_eri)))
+
     def set_shard(self, owner, rank: int):
         """Contract only the pairs of central atoms with owner[a] == rank (None: all)."""
         if owner is None:
@@ -303,17 +324,22 @@ class Context:
             raise HfxError(1, "owner needs one rank per atom")
         self._check(self._lib.hfx_set_shard(self._h, _p(o), int(rank)))
 
-    def sigma_fixed(self) -> np.ndarray:
-        """The Sigma accumulators, (nelem, 2) int64 (units 2^-32, 2^-64)."""
-        out = np.zeros((int(self.offsets()[-1]), 2), np.int64)
-        self._check(self._lib.hfx_get_H_fixed(self._h, _p(out), 0))
+    def sigma_fixed(self, out=None, on_device: bool = False) -> np.ndarray:
+        """The Sigma accumulators, (nelem, 2) int64 (units 2^-32, 2^-64); into
+        ``out`` (a host array, or a CUDA int64 tensor with on_device) if given."""
+        if out is None:
+            out = np.zeros((int(self.offsets()[-1]), 2), np.int64)
+            on_device = False
+        self._check(self._lib.hfx_get_H_fixed(self._h, _p(out), 1 if on_device else 0))
         return out
 
-    def set_sigma_fixed(self, words) -> float:
-        """Load summed accumulators and recompute Sigma and E_X; returns E_X."""
-        w = np.ascontiguousarray(words, np.int64)
+    def set_sigma_fixed(self, words, on_device: bool = False) -> float:
+        """Load summed accumulators (host array, or CUDA int64 tensor with
+        on_device) and recompute Sigma and E_X; returns E_X."""
+        w = words if on_device else np.ascontiguousarray(words, np.int64)
         ex = ctypes.c_double()
-        self._check(self._lib.hfx_set_H_fixed(self._h, _p(w), 0, ctypes.byref(ex)))
+        self._check(self._lib.hfx_set_H_fixed(self._h, _p(w), 1 if on_device else 0,
+                                              ctypes.byref(ex)))
         return ex.value
 
     def grad(self, nC: int, nV: int):
@@ -360,6 +386,7 @@ class Context:
         d["kernel_ms"] = dict(zip(KERNELS, list(s.kernel_ms)))
         d["kernel_flops"] = dict(zip(KERNELS, list(s.kernel_flops)))
         d["kernel_tensor_flops"] = dict(zip(KERNELS, list(s.kernel_tensor_flops)))
+        d["kernel_unpadded_flops"] = dict(zip(KERNELS, list(s.kernel_unpadded_flops)))
         d["canonical_flops_piece"] = list(s.canonical_flops_piece)
         d["canonical_flops_y"] = s.canonical_flops_y
         return d

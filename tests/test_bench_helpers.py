@@ -8,10 +8,26 @@ import bench
 
 
 def test_traffic_follows_the_captured_source_only(monkeypatch):
+    import hashlib
+    src = os.path.join(bench.ROOT, "paper_2009_12505_gb300", "csrc", "hfx_zc.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    monkeypatch.setattr(bench, "ZC_CAPTURED_SHA", sha)
     t = bench.zc_traffic(1e12)
-    assert t is not None and 1e9 < t < 1e10      # ~2.1e-3 bytes per issued flop
+    assert t == bench.ZC_BYTES_PER_TENSOR_FLOP * 1e12
     monkeypatch.setattr(bench, "ZC_CAPTURED_SHA", "0000000000000000")
     assert bench.zc_traffic(1e12) is None
+
+
+def test_sample_atoms_and_term_total():
+    assert bench.sample_atoms(8) == list(range(8))
+    a = bench.sample_atoms(512)
+    assert len(a) == 8 and a[0] == 0 and max(a) < 512 and len(set(a)) == 8
+
+    class Fake:   # every atom: 3 + 2 + 1 + 0 surviving terms
+        def keys(self, theta, atoms=None):
+            return None, np.array([3, 2, 1, 0])
+    tot, atoms = bench.oracle_term_total(Fake(), 512, 1e-6)
+    assert tot == 6 * 512 and atoms == a
 
 
 def test_clock_summary_median_max_and_reasons(tmp_path):

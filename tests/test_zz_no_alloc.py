@@ -6,13 +6,14 @@ cudaMalloc/cudaFree are not allowed, or a process whose device memory is
 already reserved), so it keeps its intermediates in a fixed static device
 array.  This test checks it, twice in a row, against the exchange block the
 regular hfx_build entry point produces for a cluster whose only contribution
-to that block is the same term.  It lives in a file of its own that pytest
-collects last."""
+to that block is the same term, and against the CPU oracle's block.  It lives
+in a file of its own that pytest collects last."""
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import synth
 
 torch = pytest.importorskip("torch")
@@ -56,6 +57,9 @@ def test_noalloc_term_matches_build_twice():
         torch.cuda.synchronize()
         got = -out.cpu().numpy()                # the build adds minus the term
         assert np.abs(got - ref).max() <= TOL, (call, np.abs(got - ref).max())
+        orc = oracle.Oracle.of(wl).build(0.0)
+        blk = oracle.block_dict(orc["keys"], orc["data"], orc["offs"], wl.system.nao)
+        assert np.abs(got - blk[(0, 1, 0, 0, 0)]).max() <= TOL, call
 
 
 def test_noalloc_rejects_oversize():
@@ -67,3 +71,5 @@ def test_noalloc_rejects_oversize():
     p = ctypes.c_void_p(x.data_ptr())
     # nabf_a * nao_j * nao_l = 256 * 32 * 32 > 131072: rejected before any launch
     assert lib.hfx_term_noalloc(256, 4, 4, 4, 32, 32, p, p, p, p, p, None) == 2
+    # nao_i * nao_j = 2^31 (with 1-wide intermediates): rejected before any launch
+    assert lib.hfx_term_noalloc(1, 1, 1 << 16, 1, 1 << 15, 1, p, p, p, p, p, None) == 2
