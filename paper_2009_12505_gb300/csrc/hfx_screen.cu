@@ -126,7 +126,7 @@ __device__ inline int64_t dfind(const DevHash &h, int i, int j, int n0, int n1, 
   return dh_find(h, hk_pack(i, j, n0, n1, n2));
 }
 
-__global__ void __launch_bounds__(256) k_screen(ScreenArgs A) {
+__global__ void __launch_bounds__(256, 3) k_screen(ScreenArgs A) {
   const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (p >= A.nwg) return;
@@ -145,7 +145,8 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A) {
   const int pA = A.nabf[it.a];
   const int na = A.nao[it.a], nb = A.nao[it.b], ng = A.nao[gt];
   unsigned long long cnt[4] = {0, 0, 0, 0};
-  unsigned long long macs = 0, pm[4] = {0, 0, 0, 0}, eri_cut = 0;
+  unsigned long long macs = 0, pm[4] = {0, 0, 0, 0};
+  unsigned eri_cut = 0;
   const double sqBG = A.eri_sq ? A.eri_sq[eg.cblk] : 0.0;
   unsigned any = 0;
   uint32_t *mrow = A.masks + it.mask_off + (int64_t)g * 4 * it.nFw;
@@ -211,7 +212,7 @@ __global__ void __launch_bounds__(256) k_screen(ScreenArgs A) {
     macs += pm[v];
   }
   for (int o = 16; o; o >>= 1) eri_cut += __shfl_xor_sync(0xffffffffu, eri_cut, o);
-  if (lane == 0 && eri_cut) atomicAdd(&A.counters[21], eri_cut);
+  if (lane == 0 && eri_cut) atomicAdd(&A.counters[21], (unsigned long long)eri_cut);
   if (lane == 0) {
     A.wg_flags[it.wg_off + g] = (uint8_t)any;
     if (any & 1u) sig_insert(A.sig_keys, A.sig_mask, hk_pack(it.a, it.b, it.n[0], it.n[1], it.n[2]),
