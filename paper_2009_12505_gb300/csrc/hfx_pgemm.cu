@@ -16,7 +16,9 @@
 //
 // Roles (one CTA per SM, static round-robin over the wave's jobs): warp 8
 // copies each K tile's A and B digits (lanes 0 and 1, 1-D bulk copies) into a
-// ring of shared stages; warp 9 issues the MMAs into the TMEM accumulator;
+// ring of shared stages and, for Y jobs, then writes the job's epilogue data
+// (row exponents and Y2 offsets, column exponents) into one of two shared
+// slots, off the epilogue's path; warp 9 issues the MMAs into the TMEM accumulator;
 // warps 0-7 (TMEM lanes 32 (w % 4).., columns 32 (w / 4)..) drain the
 // accumulator into those sums, release it to the next job's MMAs, and then
 // write Y (f32 pairs, and FP64 where read) or add the surviving Sigma_FG
@@ -36,9 +38,86 @@ constexpr long long PG_WAIT = 2000000000ll;    // cycles per bounded wait
 
 struct PgSmem {
   uint64_t full[PG_NST], empty[PG_NST], tfull, tempty, drain;
+  uint64_t mfull[2], mempty[2];  // Y jobs: the epilogue-data ring (PgMetaY)
   uint32_t tslot;
   int abort_f;
 };
+
+constexpr int PG_CTL_BYTES = (int)((sizeof(PgSmem) + 15) / 16 * 16);
+
+// One Y job's epilogue data, written by the loader warp ahead of the job into
+// one of two slots, so the epilogue reads shared memory instead of running a
+// chain of dependent global loads per job.
+struct PgMetaY {
+  int64_t y2base;     // scratch offset (doubles) of the pair's Y2 region
+  int64_t y64base;    // scratch offset of the pair's FP64 Y region
+  int32_t pA, nbY, nrowY, pad;
+  int32_t y2row[TM];  // Y2 offset (pairs) of each row, -1: the row is not stored;
+                      // below 2^31: at most 512 blocks of 16 x 256 x 32 x 16 pairs
+  int16_t ea[TM];     // row exponents
+  int16_t eb[NT];     // column exponents (0 beyond nabf(A))
+};
+
+// Fill m for Y job jb (the whole loader warp; lane l takes rows l, l + 32,
+// l + 64, l + 96).  The loads are issued level by level for the four rows at
+// once, so the dependent chain is three loads deep, not twelve.
+__device__ __forceinline__ void y_meta_fill(const SplitShared &S, const SplitWave &W,
+                                            const Job &jb, const WorkItem &it, PgMetaY &m,
+                                            int lane) {
+  constexpr int RPL = TM / 32;  // rows per lane
+  const int wl = (int)(jb.w - W.w0);
+  const int nbY = S.nao[it.b], ncol = S.ncol[it.b], pA = S.nabf[it.a];
+  const int64_t coloff = S.coloff[it.b];
+  const int16_t *ea_p = S.cy_e + S.cy_rowpre[it.b] + jb.mt * TM;
+  const int16_t *eb_p = S.vs_e + S.v_rowpre[it.vblk] + jb.nt * NT;
+  const int nrowY = nbY * ncol;
+  if (lane == 0) {
+    m.y2base = W.y2_on ? W.y2_off[wl] : 0;
+    m.y64base = W.y_off[wl];
+    m.pA = pA;
+    m.nbY = nbY;
+    m.nrowY = nrowY;
+  }
+  int b[RPL], col[RPL], G[RPL];
+  bool live[RPL];
+  int16_t ea[RPL];
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) {
+    const int rowY = jb.mt * TM + lane + 32 * u;
+    live[u] = rowY < nrowY && W.y2_on;
+    b[u] = live[u] ? rowY / ncol : 0;
+    col[u] = live[u] ? rowY - b[u] * ncol : 0;
+    ea[u] = ea_p[lane + 32 * u];  // padded rows hold the slicing's exponent too
+  }
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) G[u] = live[u] ? S.colG[coloff + col[u]] : 0;
+  int aopre[RPL], kofs[RPL];
+  unsigned bits[RPL];
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) {
+    aopre[u] = live[u] ? S.nbr[it.gbase + G[u]].aopre : 0;
+    kofs[u] = live[u] ? S.kofs[it.gbase + G[u]] : 0;
+    bits[u] = live[u] ? S.wg[it.wg_off + G[u]] : 0u;
+  }
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) {
+    // only rows of G with survivors are read: the f32 pairs by the D_FG /
+    // D_FB products and by P of the D_AB piece
+    int32_t y2 = -1;
+    if (live[u] && (bits[u] & 11u)) {
+      const int g = col[u] - aopre[u];
+      y2 = (((kofs[u] / 16 + g / 16) * pA) * nbY + b[u]) * 16 + (g & 15);
+    }
+    m.y2row[lane + 32 * u] = y2;
+    m.ea[lane + 32 * u] = ea[u];
+  }
+  const int ncl = pA - jb.nt * NT;
+#pragma unroll
+  for (int u = 0; u < NT / 32; ++u) {
+    const int c = lane + 32 * u;
+    m.eb[c] = c < ncl ? eb_p[c] : (int16_t)0;
+  }
+}
 
 // Operand tiles, exponents and K range of job jb.
 template <int KS, int JOB>
@@ -70,6 +149,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
   constexpr int SH = 7 * (KS + 1);
   extern __shared__ __align__(1024) uint8_t smem[];
   PgSmem *ctl = reinterpret_cast<PgSmem *>(smem + PG_NST * STAGE);
+  PgMetaY *meta = reinterpret_cast<PgMetaY *>(smem + PG_NST * STAGE + PG_CTL_BYTES);
   volatile int *abort_f = &ctl->abort_f;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int njobs = W.njobs[JOB];
@@ -83,6 +163,10 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
     umma::mbar_init(&ctl->tfull, 1);
     umma::mbar_init(&ctl->tempty, PG_EPI);
     umma::mbar_init(&ctl->drain, 1);
+    for (int m = 0; m < 2; ++m) {
+      umma::mbar_init(&ctl->mfull[m], 1);
+      umma::mbar_init(&ctl->mempty[m], PG_EPI);
+    }
     ctl->abort_f = 0;
     umma::fence_barrier_init();
   }
@@ -97,7 +181,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
 
   if (warp == PG_EPI) {
     // ------------------------------------------------------------ loader
-    long long step = 0;
+    long long step = 0, mcount = 0;
     for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
       if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
       const Job jb = jobs[j];
@@ -130,6 +214,27 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
           umma::bulk_g2s(st + A_BYTES, Bb + (int64_t)kt * KS * NT * TK, B_BYTES, &ctl->full[s]);
       }
       if (!ok) break;
+      if constexpr (JOB == 0) {
+        if (jb.nk > 0) {
+          // the job's epilogue data, while its operand copies are in flight
+          const int ms = (int)(mcount & 1);
+          const long long use = mcount >> 1;
+          bool w = true;
+          if (lane == 0) {
+            if (use >= 1)
+              w = umma::mbar_wait(&ctl->mempty[ms], (uint32_t)((use - 1) & 1), S.err, PG_WAIT);
+            w = w && !*abort_f;
+          }
+          if (!__shfl_sync(0xffffffffu, (int)w, 0)) {
+            if (lane == 0) *abort_f = 1;
+            break;
+          }
+          y_meta_fill(S, W, jb, it, meta[ms], lane);
+          __syncwarp();
+          if (lane == 0) umma::mbar_arrive(&ctl->mfull[ms]);
+          ++mcount;
+        }
+      }
     }
     // drain: the last stages issued must have landed before the CTA exits
     if (lane == 0) {
@@ -197,58 +302,60 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
     const int row = q4 * 32 + lane;
     const int c0 = hf * 32;  // this warp's 32 of the 64 columns
     long long hand = 0;
+    long long mcount = 0;
     for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
       const Job jb = jobs[j];
       if (jb.nk == 0) continue;  // no MMAs, no accumulator handoff
-      // everything this thread needs from global memory, before the wait, so
-      // the dependent lookups overlap the job's MMAs
-      const WorkItem it = S.items[jb.w];
-      const int wl = (int)(jb.w - W.w0);
-      const __nv_bfloat16 *Ab, *Bb;
-      const int16_t *ea_p, *eb_p;
-      pg_operands<KS, JOB>(S, W, jb, it, Ab, Bb, ea_p, eb_p);
-      const int ea = ea_p[row];
-      // Y: the column exponents too (pairs of int16), before the wait
+      int ea;
+      // Y: the column exponents (pairs of int16)
       uint32_t ebp[JOB == 0 ? 16 : 1];
-      if constexpr (JOB == 0) {
-        const int ncl = S.nabf[it.a] - (jb.nt * NT + c0);  // valid columns of this warp
-#pragma unroll
-        for (int p = 0; p < 16; ++p) {
-          const uint32_t e0 = 2 * p < ncl ? (uint16_t)eb_p[c0 + 2 * p] : 0u;
-          const uint32_t e1 = 2 * p + 1 < ncl ? (uint16_t)eb_p[c0 + 2 * p + 1] : 0u;
-          ebp[p] = e0 | (e1 << 16);
-        }
-      }
       bool valid;
-      // Y job: row (b, G, g) of Y, Y2 row, FP64 need
-      int64_t yrow = 0, y2row = -1, nrowY = 0;
+      // Y job: row (b, G, g) of Y, Y2 row, FP64 need, Y regions
+      int64_t yrow = 0, y2row = -1, nrowY = 0, y2base = 0, y64base = 0;
       bool need64 = false;
       int pA = 0, nbY = 0;
-      // D_AB job: row (F, f)
+      // D_AB job: row (F, f) and everything it needs from global memory
       int F = 0, nf = 0, f = 0;
       NbrEntry ef{};
-      if (JOB == 0) {
-        nbY = S.nao[it.b];
-        const int ncol = S.ncol[it.b];
-        nrowY = (int64_t)nbY * ncol;
+      WorkItem it{};
+      const int16_t *eb_p = nullptr;
+      if constexpr (JOB == 0) {
+        // the loader warp wrote this job's data into slot mcount & 1
+        const int ms = (int)(mcount & 1);
+        const bool okm = umma::mbar_wait(&ctl->mfull[ms], (uint32_t)((mcount >> 1) & 1), S.err,
+                                         PG_WAIT);
+        ++mcount;
+        if (umma::bar_any(!okm || *abort_f, PG_EPI * 32)) {
+          *abort_f = 1;
+          break;
+        }
+        const PgMetaY &m = meta[ms];
+        ea = m.ea[row];
+#pragma unroll
+        for (int p = 0; p < 16; ++p)
+          ebp[p] = (uint32_t)(uint16_t)m.eb[c0 + 2 * p] |
+                   ((uint32_t)(uint16_t)m.eb[c0 + 2 * p + 1] << 16);
+        nbY = m.nbY;
+        pA = m.pA;
+        nrowY = m.nrowY;
+        y2base = m.y2base;
+        y64base = m.y64base;
         const int rowY = jb.mt * TM + row;
-        pA = S.nabf[it.a];
         valid = rowY < nrowY;
         yrow = rowY;
         need64 = W.y64_mode == 1;
-        if (valid && W.y2_on) {
-          const int b = rowY / ncol, col = rowY - b * ncol;
-          const int G = S.colG[S.coloff[it.b] + col];
-          const int g = col - S.nbr[it.gbase + G].aopre;
-          // only rows of G with survivors are read: the f32 pairs by the D_FG /
-          // D_FB products and by P of the D_AB piece
-          const unsigned bits = S.wg[it.wg_off + G];
-          if (bits & 11u) {
-            const int cb = S.kofs[it.gbase + G] / 16 + g / 16;
-            y2row = (((int64_t)cb * pA) * nbY + b) * 16 + (g & 15);
-          }
-        }
+        y2row = m.y2row[row];
+        // the slot is free for the loader once every warp has read it
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&ctl->mempty[ms]);
       } else {
+        // everything this thread needs from global memory, before the wait, so
+        // the dependent lookups overlap the job's MMAs
+        it = S.items[jb.w];
+        const __nv_bfloat16 *Ab, *Bb;
+        const int16_t *ea_p;
+        pg_operands<KS, JOB>(S, W, jb, it, Ab, Bb, ea_p, eb_p);
+        ea = ea_p[row];
         const int rF = jb.mt * TM + row;
         valid = rF < S.ncol[it.a];
         if (valid) {
@@ -306,8 +413,8 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
       if constexpr (JOB == 0) {
         // Y[al][b * ncol + col(G,g)] (FP64) and Y2 (f32 pairs) in 16-column
         // blocks [cb][al][b][16], cb = kofs(G) / 16 + g / 16
-        double *Y = W.scratch + W.y_off[wl];
-        float2 *Y2 = reinterpret_cast<float2 *>(W.scratch + W.y2_off[wl]);
+        double *Y = W.scratch + y64base;
+        float2 *Y2 = reinterpret_cast<float2 *>(W.scratch + y2base);
 #pragma unroll
         for (int p = 0; p < 16; ++p) {
           const int al = jb.nt * NT + c0 + 2 * p;
@@ -371,7 +478,8 @@ cudaError_t launch_pgemm_t(const SplitShared &S, const SplitWave &W, int64_t max
                            cudaStream_t st) {
   const int blocks = (int)std::min<int64_t>(maxjobs, S.nsm > 0 ? S.nsm : 1);
   if (blocks <= 0) return cudaSuccess;
-  const size_t smem = (size_t)PG_NST * KS * (TM + NT) * TK * 2 + sizeof(PgSmem) + 64;
+  const size_t smem = (size_t)PG_NST * KS * (TM + NT) * TK * 2 + PG_CTL_BYTES +
+                      (JOB == 0 ? 2 * sizeof(PgMetaY) : 0) + 64;
   cudaError_t e = cudaFuncSetAttribute(k_pgemm<KS, JOB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
