@@ -61,6 +61,32 @@ WORKLOADS = {"si512": ("si", 4, 3, {}), "si64": ("si", 2, 2, {}), "si8": ("si", 
              "si8_metal": ("si", 1, 6, {"cut_D": 24.0, "d_decay": "power"})}
 
 
+# The batched form: cells drawn (seeded) from Si-like 1x1x1 and 2x2x2 cells and the
+# two-element 1x1x1 cell, each with a threshold drawn from {1e-5, 1e-6, 1e-7}.
+BATCHES = {"batch12": 12}
+
+
+def batch_cells(name: str, rank: int):
+    """[(workload, theta)] of a batch; cell i has seed 1000 + i."""
+    import numpy as np
+
+    import synth
+    rng = np.random.default_rng(12345 + rank)
+    out = []
+    for i in range(BATCHES[name]):
+        kind = ["si8", "si64", "ab8"][int(rng.integers(3))]
+        theta = [1e-5, 1e-6, 1e-7][int(rng.integers(3))]
+        seed = 1000 + i + 100000 * rank
+        if kind == "si8":
+            system = synth.si_diamond(1)
+        elif kind == "si64":
+            system = synth.si_diamond(2)
+        else:
+            system = synth.two_element_rocksalt(1, seed=seed)
+        out.append((synth.make_workload(system, seed=seed, name=kind), theta))
+    return out
+
+
 def workload(name: str, rank: int):
     import synth
     kind, ncell, seed, opts = WORKLOADS[name]
@@ -303,6 +329,83 @@ def pinned_copy(blocks):
     t = torch.from_numpy(np.ascontiguousarray(blocks.data)).pin_memory()
     return (np.ascontiguousarray(blocks.keys, np.int32), t.numpy(),
             np.ascontiguousarray(blocks.offs, np.int64), t)
+
+
+def run_batch(args):
+    """Many independent cells of uneven size with their own thresholds, built
+    by one hfx_build_batch (one merged build: per wave one launch of each
+    persistent kernel for all cells), against the same cells built one by
+    one."""
+    import torch
+
+    import paper_2009_12505_gb300 as hfx
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    cells = batch_cells(args.workload, 0)
+    stream = torch.cuda.Stream()
+    ctxs = []
+    for wl, _ in cells:
+        c = hfx.Context(wl.system.nao, wl.system.nabf, stream=stream.cuda_stream)
+        for k in "CVD":
+            c.set_blocks(k, getattr(wl, k))
+        ctxs.append(c)
+    thetas = [th for _, th in cells]
+    prec, nsl = args.prec, args.nslices
+    for _ in range(args.warmup):
+        hfx.build_batch(ctxs, thetas, prec, nsl)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    clk = ClockSampler(0)
+    with clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            hfx.build_batch(ctxs, thetas, prec, nsl)
+            launches += ctxs[0].stats()["n_launches"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+    clocks = clk.summary()
+    clk.close()
+    ms = e0.elapsed_time(e1) / args.steps
+    st = ctxs[0].stats()
+    flops = st["canonical_flops"]
+    # the same cells one by one, each on a fresh context freed after its build
+    # (every context keeps its own scratch, so twelve at once would not fit)
+    for c in ctxs:
+        c.close()
+    ctxs = []
+    ms_seq = 0.0
+    for wl, th in cells:
+        c = hfx.Context(wl.system.nao, wl.system.nabf, stream=stream.cuda_stream)
+        for k in "CVD":
+            c.set_blocks(k, getattr(wl, k))
+        c.build(th, prec, nsl)           # slicing and planning, not timed
+        torch.cuda.synchronize()
+        e0.record(stream)
+        c.build(th, prec, nsl)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms_seq += e0.elapsed_time(e1)
+        c.close()
+    kinds = {}
+    for wl, th in cells:
+        kinds[f"{wl.name}@{th:g}"] = kinds.get(f"{wl.name}@{th:g}", 0) + 1
+    line = {"metric": METRIC, "value": flops / (ms / 1e3) / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if prec != "fp64" else "f64", "data": "synthetic",
+            "config": {"workload": f"{args.workload}: {len(cells)} independent cells "
+                                   f"(Si-like 8 and 64 atoms, two-element 8 atoms; seeds 1000+i), "
+                                   f"theta per cell from {{1e-5, 1e-6, 1e-7}}: {kinds}",
+                       "prec": prec, "nslices": nsl if prec == "ozaki" else None,
+                       "parallelism": "one merged build (hfx_build_batch)"},
+            "canonical_tflop": flops / 1e12, "batch_s": ms / 1e3,
+            "cells_one_by_one_s": ms_seq / 1e3, "batch_speedup": ms_seq / ms,
+            "one_by_one_is": "sum of each cell's second hfx_build on its own context (the "
+                             "first slices and plans), CUDA events",
+            "n_waves": st["n_waves"], "gpu_launches": launches,
+            "kernel_ms_per_step": st["kernel_ms"], "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    return 0
 
 
 def run_gpu(args):
@@ -627,7 +730,7 @@ def main():
     ap.add_argument("--replicas", action="store_true",
                     help="under torchrun: one independent cell per rank instead of one shared, "
                          "sharded cell")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="si512")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + sorted(BATCHES), default="si512")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--eps-eri", type=float, default=1e-3,
                     help="also time a build with the Cauchy-Schwarz ERI screen at this "
@@ -639,6 +742,12 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--ref-seconds", type=float, default=4.0)
     args = ap.parse_args()
+    if args.workload in BATCHES:
+        if args.impl == "reference":
+            print(json.dumps({"impl": "reference", "unavailable": "the batched cells have no "
+                              "reference arm; use a single-cell workload"}))
+            return 0
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -204,15 +204,27 @@ hfx_status hfx_get_H_all(const hfx_ctx *ctx, double *out, int on_device);
 hfx_status hfx_grad(hfx_ctx *ctx, double *dC, double *dV);
 
 /*
- * Build many independent cells (contexts), cell c with theta thetas[c]: the
- * same as hfx_build on each context in order, on each context's own stream
- * (the cells run one after another, each with its own launches and host
- * synchronisations; there is no single grouped launch over the cells yet),
- * with ex_out[c] (if ex_out is not NULL) receiving cell c's E_X.  The cells
- * share nothing; results are bitwise those of separate hfx_build calls.
- * Errors: HFX_E_ARG (NULL arrays, ncells < 0), else the first failing cell's
- * status, with its message in that cell's hfx_last_error; cells after it are
- * not built.
+ * Build many independent cells (contexts) together, cell c with theta
+ * thetas[c] (spec batching; the paper builds one system at a time).
+ * The cells are merged into one system -- cell c's atoms follow those of the
+ * cells before it, its blocks keep their keys with both atoms offset, no
+ * block joins two cells -- and built once: one screen launch and, per wave,
+ * one launch of each persistent kernel serve the jobs of every cell, uneven
+ * block sizes included.  The screen uses each central atom's own cell's
+ * theta.  Each cell then receives its Sigma blocks, its fixed-point words and
+ * its E_X (ex_out[c] if ex_out is not NULL), bitwise equal to hfx_build of
+ * that cell alone when the cells agree on whether their V and D are exactly
+ * Hermitian (the mirror pieces are used for all cells or for none).
+ * The cells' input blocks are copied into the merged system for the call, so
+ * the device needs room for them twice.  Runs on cells[0]'s stream; cells
+ * must be distinct and use the same ERI-screen threshold; shards are ignored.
+ * After a batch, hfx_get_H*, hfx_H_*, hfx_get_H_fixed, hfx_sigma_k and
+ * hfx_stats (batch-wide figures) work on each cell; hfx_grad and
+ * hfx_set_H_fixed need a build of the cell alone and return HFX_E_STATE.
+ * Errors: HFX_E_ARG (NULL arrays, ncells < 0, a repeated cell, a bad theta,
+ * different ERI thresholds), HFX_E_SHAPE (more than 2^20 atoms in all),
+ * else the merged build's status, with its message in every cell's
+ * hfx_last_error; no cell then holds results.
  */
 hfx_status hfx_build_batch(hfx_ctx **cells, int32_t ncells, const double *thetas, hfx_prec prec,
                            int32_t nslices, double *ex_out);

@@ -177,6 +177,13 @@ struct hfx_ctx {
   bool eri_valid = false;
   DevBuf<double> d_eri_sq;
 
+  // batch builds: per-atom screening threshold of the merged cells (empty:
+  // the build's theta), and whether this context's results came from a batch
+  std::vector<double> theta_atom;
+  DevBuf<double> d_theta_atom;
+  bool from_batch = false;
+  DevBuf<double> d_ex_cells;
+
   bool sym = false;             // V and D blocks all have transposed mirrors
   std::vector<int32_t> owner;   // shard: central atom -> rank (empty: no shard)
   int32_t rank = 0;
@@ -1001,9 +1008,15 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
     if (ctx->K[k].map.empty())
       return fail(ctx, HFX_E_STATE, std::string("no ") + ctx->K[k].name + " blocks set");
   ctx->results_valid = false;
+  ctx->from_batch = false;
   ctx->launches = 0;
   double kms[8] = {0};
   cudaStream_t st = ctx->stream;
+  if (!ctx->theta_atom.empty()) {
+    CK(ctx->d_theta_atom.reserve(ctx->theta_atom.size()));
+    CK(cudaMemcpyAsync(ctx->d_theta_atom.p, ctx->theta_atom.data(),
+                       sizeof(double) * ctx->theta_atom.size(), cudaMemcpyHostToDevice, st));
+  }
   CK(cudaEventRecord(ctx->ev[0], st));
   CK(cudaMemsetAsync(ctx->d_err.p, 0, sizeof(unsigned), st));
   const bool vd_dirty = ctx->K[1].dirty || ctx->K[2].dirty;
@@ -1072,6 +1085,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
     a.sig_limit = ctx->stab_cap / 2;
     a.counters = ctx->d_counters.p;
     a.eri_sq = ctx->eps_eri >= 0.0 ? ctx->d_eri_sq.p : nullptr;
+    a.theta_atom = ctx->theta_atom.empty() ? nullptr : ctx->d_theta_atom.p;
     a.eps_eri = ctx->eps_eri;
     a.err = ctx->d_err.p;
     CK(cudaEventRecord(ctx->kev[8], st));
@@ -1515,16 +1529,155 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
   return HFX_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The cells of a batch as one system: cell c's atoms follow those of cells
+// 0 .. c-1, its blocks keep their keys with both atoms offset, and no block
+// joins two cells, so the merged build's terms are exactly the union of the
+// cells' terms.  The packed device data of each cell is copied as it is.
+hfx_status merge_cells(hfx_ctx *const *cells, int32_t ncells, const double *thetas,
+                       std::vector<int32_t> &first, hfx_ctx **out) {
+  first.assign(ncells + 1, 0);
+  for (int32_t c = 0; c < ncells; ++c) first[c + 1] = first[c] + cells[c]->natoms;
+  const int32_t natoms = first[ncells];
+  if (natoms >= (1 << 20)) return fail(cells[0], HFX_E_SHAPE, "batch: more than 2^20 atoms");
+  std::vector<int32_t> nao(natoms), nabf(natoms), species(natoms);
+  for (int32_t c = 0; c < ncells; ++c)
+    for (int32_t a = 0; a < cells[c]->natoms; ++a) {
+      nao[first[c] + a] = cells[c]->nao[a];
+      nabf[first[c] + a] = cells[c]->nabf[a];
+    }
+  for (int32_t a = 0; a < natoms; ++a) species[a] = a;
+  hfx_ctx *m = nullptr;
+  hfx_status s = hfx_create(nullptr, natoms, nullptr, species.data(), natoms, nao.data(),
+                            nabf.data(), cells[0]->stream, &m);
+  if (s != HFX_OK) return fail(cells[0], s, "batch: cannot create the merged system");
+  for (int32_t c = 0; c < ncells && s == HFX_OK; ++c) {
+    hfx_ctx *ctx = cells[c];
+    for (int k = 0; k < 3 && s == HFX_OK; ++k) {
+      // packing here must not hide from the cell's own next build that its
+      // blocks changed since its last one: keep the kind's dirty flag
+      const bool was_dirty = ctx->K[k].dirty;
+      s = pack_kind(ctx, k);
+      ctx->K[k].dirty = was_dirty;
+      if (s != HFX_OK) break;
+      if (ctx->stream && cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        s = fail(ctx, HFX_E_CUDA, "batch: stream synchronisation failed");
+        break;
+      }
+      const Kind &K = ctx->K[k];
+      const int64_t nblk = (int64_t)K.keys.size();
+      if (nblk == 0) continue;
+      std::vector<int32_t> keys(5 * nblk);
+      for (int64_t e = 0; e < nblk; ++e) {
+        hk_unpack(K.keys[e], &keys[5 * e]);
+        keys[5 * e] += first[c];
+        keys[5 * e + 1] += first[c];
+      }
+      s = hfx_set_many(m, K.name, nblk, keys.data(), K.data.p, K.offs.data(), 1);
+      if (s != HFX_OK) fail(ctx, s, std::string("batch: ") + m->err);
+    }
+  }
+  if (s != HFX_OK) {
+    hfx_destroy(m);
+    return s;
+  }
+  m->theta_atom.resize(natoms);
+  for (int32_t c = 0; c < ncells; ++c)
+    for (int32_t a = first[c]; a < first[c + 1]; ++a) m->theta_atom[a] = thetas[c];
+  m->eps_eri = cells[0]->eps_eri;
+  *out = m;
+  return HFX_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 hfx_status hfx_build_batch(hfx_ctx **cells, int32_t ncells, const double *thetas, hfx_prec prec,
                            int32_t nslices, double *ex_out) {
   if (ncells < 0 || (ncells > 0 && (!cells || !thetas))) return HFX_E_ARG;
+  if (ncells == 0) return HFX_OK;
   for (int32_t c = 0; c < ncells; ++c) {
     if (!cells[c]) return HFX_E_ARG;
-    double ex = 0.0;
-    const hfx_status s = hfx_build(cells[c], thetas[c], prec, nslices, &ex);
-    if (s != HFX_OK) return s;
-    if (ex_out) ex_out[c] = ex;
+    if (!(thetas[c] >= 0.0) || !std::isfinite(thetas[c]))
+      return fail(cells[c], HFX_E_ARG, "batch: theta must be >= 0");
+    for (int32_t d = 0; d < c; ++d)
+      if (cells[d] == cells[c]) return fail(cells[c], HFX_E_ARG, "batch: a cell appears twice");
+    if (cells[c]->eps_eri != cells[0]->eps_eri)
+      return fail(cells[c], HFX_E_ARG, "batch: the cells' ERI screen thresholds differ");
+    cells[c]->results_valid = false;
   }
+  std::vector<int32_t> first;
+  hfx_ctx *m = nullptr;
+  hfx_status s = merge_cells(cells, ncells, thetas, first, &m);
+  if (s != HFX_OK) return s;
+  s = hfx_build(m, 0.0, prec, nslices, nullptr);
+  if (s != HFX_OK) {
+    for (int32_t c = 0; c < ncells; ++c) fail(cells[c], s, "batch: " + m->err);
+    hfx_destroy(m);
+    return s;
+  }
+  // Sigma, its fixed-point words and E_X of each cell from the merged result:
+  // cell c's keys are the contiguous range with first atom in [first[c],
+  // first[c + 1]); E_X reduces that range's per-block partials exactly as a
+  // build of the cell alone does
+  hfx_ctx *ctx = nullptr;
+  auto fail_all = [&](const char *what, cudaError_t e) {
+    for (int32_t c = 0; c < ncells; ++c)
+      fail(cells[c], HFX_E_CUDA, std::string("batch: ") + what + ": " + cudaGetErrorString(e));
+    hfx_destroy(m);
+    return HFX_E_CUDA;
+  };
+  cudaStream_t st = m->stream;
+  cudaError_t e = m->d_ex_cells.reserve(ncells);
+  if (e != cudaSuccess) return fail_all("cudaMalloc", e);
+  std::vector<int64_t> k0(ncells), k1(ncells);
+  for (int32_t c = 0; c < ncells; ++c) {
+    k0[c] = std::lower_bound(m->sig_keys.begin(), m->sig_keys.end(),
+                             (uint64_t)first[c] << 44) - m->sig_keys.begin();
+    k1[c] = std::lower_bound(m->sig_keys.begin(), m->sig_keys.end(),
+                             (uint64_t)first[c + 1] << 44) - m->sig_keys.begin();
+    e = launch_ex_reduce(m->d_partials.p + k0[c], k1[c] - k0[c], m->d_ex_cells.p + c, st);
+    if (e != cudaSuccess) return fail_all("E_X reduction", e);
+  }
+  std::vector<double> exs(ncells);
+  e = cudaMemcpyAsync(exs.data(), m->d_ex_cells.p, sizeof(double) * ncells,
+                      cudaMemcpyDeviceToHost, st);
+  for (int32_t c = 0; c < ncells && e == cudaSuccess; ++c) {
+    ctx = cells[c];
+    const int64_t nk = k1[c] - k0[c];
+    const int64_t e0 = m->sig_offs[k0[c]], ne = m->sig_offs[k1[c]] - e0;
+    ctx->sig_keys.resize(nk);
+    ctx->sig_offs.assign(nk + 1, 0);
+    for (int64_t q = 0; q < nk; ++q) {
+      int32_t kk[5];
+      hk_unpack(m->sig_keys[k0[c] + q], kk);
+      ctx->sig_keys[q] = hk_pack(kk[0] - first[c], kk[1] - first[c], kk[2], kk[3], kk[4]);
+      ctx->sig_offs[q + 1] = m->sig_offs[k0[c] + q + 1] - e0;
+    }
+    e = ctx->d_sigma.reserve(std::max<int64_t>(ne, 1));
+    if (e == cudaSuccess) e = ctx->d_acc.reserve(2 * std::max<int64_t>(ne, 1));
+    if (e == cudaSuccess && ne > 0)
+      e = cudaMemcpyAsync(ctx->d_sigma.p, m->d_sigma.p + e0, sizeof(double) * ne,
+                          cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess && ne > 0)
+      e = cudaMemcpyAsync(ctx->d_acc.p, m->d_acc.p + 2 * e0, sizeof(unsigned long long) * 2 * ne,
+                          cudaMemcpyDeviceToDevice, st);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail_all("copying the cells' results", e);
+  for (int32_t c = 0; c < ncells; ++c) {
+    ctx = cells[c];
+    ctx->ex = exs[c];
+    ctx->stats = m->stats;  // batch-wide counts and times
+    ctx->results_valid = true;
+    ctx->from_batch = true;
+    if (ex_out) ex_out[c] = exs[c];
+  }
+  hfx_destroy(m);
   return HFX_OK;
 }
 
@@ -1570,6 +1723,8 @@ hfx_status hfx_get_H_fixed(const hfx_ctx *ctx, int64_t *words, int on_device) {
 hfx_status hfx_set_H_fixed(hfx_ctx *ctx, const int64_t *words, int on_device, double *ex_out) {
   if (!ctx || !words) return HFX_E_ARG;
   if (!ctx->results_valid) return fail(ctx, HFX_E_STATE, "no build whose key set to use");
+  if (ctx->from_batch)
+    return fail(ctx, HFX_E_STATE, "results of a batch build: build the cell alone to shard it");
   cudaStream_t st = ctx->stream;
   const int64_t nsig = (int64_t)ctx->sig_keys.size();
   const int64_t nelem = ctx->sig_offs.empty() ? 0 : ctx->sig_offs.back();
@@ -1640,6 +1795,8 @@ hfx_status hfx_get_H_all(const hfx_ctx *ctx, double *out, int on_device) {
 hfx_status hfx_grad(hfx_ctx *ctx, double *dC, double *dV) {
   if (!ctx) return HFX_E_ARG;
   if (!ctx->results_valid) return fail(ctx, HFX_E_STATE, "no build to differentiate");
+  if (ctx->from_batch)
+    return fail(ctx, HFX_E_STATE, "results of a batch build: build the cell alone to differentiate");
   cudaStream_t st = ctx->stream;
   const int64_t nC = ctx->K[0].offs.back(), nV = ctx->K[1].offs.back();
   DevBuf<unsigned long long> dcacc;

@@ -143,6 +143,7 @@ struct ScreenArgs {
                                  // [21] quadruples (A,B,F,G) removed by the ERI screen
   const double *eri_sq;    // per C block sqrt(max(Q, 0)) of the ERI screen; null: screen off
   double eps_eri;
+  const double *theta_atom;  // per central atom threshold (batched cells); null: theta
   unsigned *err;
 };
 
@@ -194,6 +195,8 @@ cudaError_t launch_contract_fp64(const ContractArgs &a, cudaStream_t st, cudaEve
 cudaError_t launch_adjoint(const ContractArgs &a, cudaStream_t st);
 cudaError_t launch_fx_to_double(const unsigned long long *acc, int64_t n, double *out,
                                 cudaStream_t st);
+// E_X = 1/2 the sum of n per-block partials, in the fixed order of the build.
+cudaError_t launch_ex_reduce(const double *partials, int64_t n, double *ex, cudaStream_t st);
 cudaError_t launch_finalize(const unsigned long long *acc, int64_t nelem, double *sigma,
                             const uint64_t *skeys, const int64_t *soffs, int64_t nsig,
                             DevBlocks D, DevHash dhash, double *partials, double *ex,

@@ -106,6 +106,11 @@ cudaError_t launch_finalize(const unsigned long long *acc, int64_t nelem, double
   return cudaGetLastError();
 }
 
+cudaError_t launch_ex_reduce(const double *partials, int64_t n, double *ex, cudaStream_t st) {
+  k_ex_reduce<<<1, 1024, 0, st>>>(partials, n, ex);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gather(const double *const *src, const int64_t *dst_off, const int64_t *len,
                           int64_t nblk, double *dst, cudaStream_t st) {
   if (nblk <= 0) return cudaSuccess;

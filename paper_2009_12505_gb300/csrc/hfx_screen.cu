@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(256, 3) k_screen(ScreenArgs A) {
   const bool g_is_b = (gt == it.b) && eg.n[0] == 0 && eg.n[1] == 0 && eg.n[2] == 0;
   const double mcBG = A.C.maxabs[eg.cblk];
   const double mv = A.V.maxabs[it.vblk];
+  const double theta = A.theta_atom ? A.theta_atom[it.a] : A.theta;
   const int64_t dAG = dfind(A.dhash, it.a, gt, nG0, nG1, nG2);
   const double mvAG = dAG >= 0 ? __dmul_rn(mv, A.D.maxabs[dAG]) : 0.0;
   const double mvAB = it.dab >= 0 ? __dmul_rn(mv, A.D.maxabs[it.dab]) : 0.0;
@@ -166,16 +167,16 @@ __global__ void __launch_bounds__(256, 3) k_screen(ScreenArgs A) {
       if (eri_ok) {
         // variant 1: D_FG -> Sigma_AB
         const int64_t dFG = dfind(A.dhash, ft, gt, nG0 - mF0, nG1 - mF1, nG2 - mF2);
-        if (dFG >= 0) b1 = __dmul_rn(cc, __dmul_rn(mv, A.D.maxabs[dFG])) > A.theta;
+        if (dFG >= 0) b1 = __dmul_rn(cc, __dmul_rn(mv, A.D.maxabs[dFG])) > theta;
         // variant 2: D_FB -> Sigma_AG (not when G is B)
         if (!g_is_b) {
           const int64_t dFB = dfind(A.dhash, ft, it.b, it.n[0] - mF0, it.n[1] - mF1, it.n[2] - mF2);
-          if (dFB >= 0) b2 = __dmul_rn(cc, __dmul_rn(mv, A.D.maxabs[dFB])) > A.theta;
+          if (dFB >= 0) b2 = __dmul_rn(cc, __dmul_rn(mv, A.D.maxabs[dFB])) > theta;
         }
         // variant 3: D_AG -> Sigma_FB (not when F is A)
-        if (!f_is_a && dAG >= 0) b3 = __dmul_rn(cc, mvAG) > A.theta;
+        if (!f_is_a && dAG >= 0) b3 = __dmul_rn(cc, mvAG) > theta;
         // variant 4: D_AB -> Sigma_FG (neither)
-        if (!f_is_a && !g_is_b && it.dab >= 0) b4 = __dmul_rn(cc, mvAB) > A.theta;
+        if (!f_is_a && !g_is_b && it.dab >= 0) b4 = __dmul_rn(cc, mvAB) > theta;
       }
     }
     const uint32_t w1 = __ballot_sync(0xffffffffu, b1);

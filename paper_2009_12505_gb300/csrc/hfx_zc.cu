@@ -377,6 +377,7 @@ __global__ void __launch_bounds__(128) k_zc_plan(SplitShared S, SplitWave W, int
 
 struct ZcSmem {
   uint64_t full[8], empty[8], tfull[2], tempty[2], yfull[2], yempty[2], drain;
+  unsigned long long t_start;  // globaltimer at the start of the roles
   uint32_t tslot;
   int abort_f;
   int stkb[8];  // K of the entry in each operand stage (16 or 32)
@@ -424,14 +425,20 @@ __device__ __forceinline__ void zc_stage_mmas(uint32_t a0, uint32_t b0, uint32_t
 // One row's contraction with Y in double-float: out[o] = sum_{c < cend} z[c]
 // yb[o so + c sc] for o < no, four outputs at a time; out[o] is stored at
 // outp[o 128] (the reduction buffer is output-major, so a warp's 32 rows
-// store to consecutive addresses).
+// store to consecutive addresses).  The even and the odd columns are summed
+// separately and added at the end, in exactly the order of the packed form
+// below (zc_contract2), so the kernel variants that read Y from global memory
+// and from shared memory give the same bits: which variant runs depends on
+// the largest atom of the whole system, and a cell must not change its result
+// when it is built together with other cells.
 template <int CW>
 __device__ __forceinline__ void zc_contract(const float2 (&z)[CW], int cend,
                                             const float2 *__restrict__ yb, int so, int sc, int no,
                                             float2 *__restrict__ outp) {
   const int no4 = no & ~3;
   for (int o0 = 0; o0 < no4; o0 += 4) {
-    float sh[4] = {0.f, 0.f, 0.f, 0.f}, sl[4] = {0.f, 0.f, 0.f, 0.f};
+    float eh[4] = {0.f, 0.f, 0.f, 0.f}, el[4] = {0.f, 0.f, 0.f, 0.f};
+    float oh[4] = {0.f, 0.f, 0.f, 0.f}, ol[4] = {0.f, 0.f, 0.f, 0.f};
     const float2 *y0 = yb + o0 * so;
 #pragma unroll
     for (int c = 0; c < CW; ++c) {
@@ -439,19 +446,27 @@ __device__ __forceinline__ void zc_contract(const float2 (&z)[CW], int cend,
       const float2 *yc = y0 + c * sc;
       const float2 v[4] = {yc[0], yc[so], yc[2 * so], yc[3 * so]};
 #pragma unroll
-      for (int u = 0; u < 4; ++u) df_mac(sh[u], sl[u], z[c], v[u]);
+      for (int u = 0; u < 4; ++u) {
+        if (c & 1) df_mac(oh[u], ol[u], z[c], v[u]);
+        else df_mac(eh[u], el[u], z[c], v[u]);
+      }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) outp[(o0 + u) * 128] = make_float2(sh[u], sl[u]);
+    for (int u = 0; u < 4; ++u) {
+      df_add(eh[u], el[u], make_float2(oh[u], ol[u]));
+      outp[(o0 + u) * 128] = make_float2(eh[u], el[u]);
+    }
   }
   for (int o = no4; o < no; ++o) {
-    float sh = 0.f, sl = 0.f;
+    float eh = 0.f, el = 0.f, oh = 0.f, ol = 0.f;
 #pragma unroll
     for (int c = 0; c < CW; ++c) {
       if (c >= cend) break;
-      df_mac(sh, sl, z[c], yb[o * so + c * sc]);
+      if (c & 1) df_mac(oh, ol, z[c], yb[o * so + c * sc]);
+      else df_mac(eh, el, z[c], yb[o * so + c * sc]);
     }
-    outp[o * 128] = make_float2(sh, sl);
+    df_add(eh, el, make_float2(oh, ol));
+    outp[o * 128] = make_float2(eh, el);
   }
 }
 
@@ -545,8 +560,11 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
   __syncthreads();
   umma::fence_after_sync();
   const uint32_t tbase = ctl->tslot;
-  unsigned long long t_start = 0;
-  if (threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+  if (threadIdx.x == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    ctl->t_start = t;  // in shared memory: no register held across the roles
+  }
 
   if (warp == ZC_EPI) {
     // ------------------------------------------------------------ A / B loader
@@ -1006,7 +1024,7 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
   if (threadIdx.x == 0) {
     unsigned long long t_end;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
-    W.cta_ns[blockIdx.x] = (long long)(t_end - t_start);
+    W.cta_ns[blockIdx.x] = (long long)(t_end - ctl->t_start);
   }
 }
 
