@@ -215,9 +215,13 @@ hfx_status hfx_grad(hfx_ctx *ctx, double *dC, double *dV);
  * its E_X (ex_out[c] if ex_out is not NULL), bitwise equal to hfx_build of
  * that cell alone when the cells agree on whether their V and D are exactly
  * Hermitian (the mirror pieces are used for all cells or for none).
- * The cells' input blocks are copied into the merged system for the call, so
- * the device needs room for them twice.  Runs on cells[0]'s stream; cells
- * must be distinct and use the same ERI-screen threshold; shards are ignored.
+ * The cells' input blocks are copied into the merged system, so the device
+ * needs room for them twice.  cells[0] keeps the merged system (freed with
+ * it): a later batch of the same cells in the same order, in which no cell's
+ * C or V blocks and no cell's D key set changed, reuses its plan and sliced
+ * operands and copies in only the D blocks that changed (the cached-plan path
+ * of an SCF iteration).  Runs on cells[0]'s stream; cells must be distinct
+ * and use the same ERI-screen threshold; shards are ignored.
  * After a batch, hfx_get_H*, hfx_H_*, hfx_get_H_fixed, hfx_sigma_k and
  * hfx_stats (batch-wide figures) work on each cell; hfx_grad and
  * hfx_set_H_fixed need a build of the cell alone and return HFX_E_STATE.

@@ -11,7 +11,10 @@
 //      budget (Algorithm 3, C((VC)D) order);
 //   5. convert the fixed-point Sigma accumulators to FP64 and reduce E_X.
 #include <algorithm>
+#include <array>
+#include <atomic>
 #include <cmath>
+#include <memory>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -86,7 +89,24 @@ struct Kind {
 
 }  // namespace
 
+// The merged system of the last hfx_build_batch whose first cell is this
+// context, kept for the next batch of the same cells: identified by the
+// cells' ids and the change counters of their C, V and D blocks.
+struct BatchCache {
+  std::vector<uint64_t> ids;
+  std::vector<std::array<uint64_t, 3>> gens, kgens;
+  std::vector<int32_t> first;
+  hfx_ctx *merged = nullptr;
+  ~BatchCache() { hfx_destroy(merged); }
+};
+
+static std::atomic<uint64_t> g_next_ctx_id{1};
+
 struct hfx_ctx {
+  uint64_t id = g_next_ctx_id.fetch_add(1);  // unique for the process
+  uint64_t gen[3] = {0, 0, 0};               // changes of the C, V and D blocks
+  uint64_t kgen[3] = {0, 0, 0};              // changes of their key sets
+  std::unique_ptr<BatchCache> batch;
   int32_t natoms = 0;
   std::vector<int32_t> nao, nabf;
   double lattice[9] = {0};
@@ -229,6 +249,8 @@ bool key_ok(const hfx_ctx *ctx, const int32_t *k) {
 
 void invalidate(hfx_ctx *ctx, int k, bool keys) {
   ctx->K[k].dirty = true;
+  ++ctx->gen[k];
+  if (keys) ++ctx->kgen[k];
   if (k < 2) ctx->eri_valid = false;
   if (keys) ctx->K[k].keys_changed = true;
   if (keys && k == 2) ctx->dz_nd = -1;
@@ -1533,6 +1555,31 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
 
 namespace {
 
+// Copy one kind of a cell's blocks into the merged system m, atoms offset
+// by first (blocks already there are replaced).
+hfx_status copy_cell_kind(hfx_ctx *m, hfx_ctx *ctx, int k, int32_t first) {
+  // packing here must not hide from the cell's own next build that its
+  // blocks changed since its last one: keep the kind's dirty flag
+  const bool was_dirty = ctx->K[k].dirty;
+  hfx_status s = pack_kind(ctx, k);
+  ctx->K[k].dirty = was_dirty;
+  if (s != HFX_OK) return s;
+  if (ctx->stream && cudaStreamSynchronize(ctx->stream) != cudaSuccess)
+    return fail(ctx, HFX_E_CUDA, "batch: stream synchronisation failed");
+  const Kind &K = ctx->K[k];
+  const int64_t nblk = (int64_t)K.keys.size();
+  if (nblk == 0) return HFX_OK;
+  std::vector<int32_t> keys(5 * nblk);
+  for (int64_t e = 0; e < nblk; ++e) {
+    hk_unpack(K.keys[e], &keys[5 * e]);
+    keys[5 * e] += first;
+    keys[5 * e + 1] += first;
+  }
+  s = hfx_set_many(m, K.name, nblk, keys.data(), K.data.p, K.offs.data(), 1);
+  if (s != HFX_OK) fail(ctx, s, std::string("batch: ") + m->err);
+  return s;
+}
+
 // The cells of a batch as one system: cell c's atoms follow those of cells
 // 0 .. c-1, its blocks keep their keys with both atoms offset, and no block
 // joins two cells, so the merged build's terms are exactly the union of the
@@ -1554,40 +1601,12 @@ hfx_status merge_cells(hfx_ctx *const *cells, int32_t ncells, const double *thet
   hfx_status s = hfx_create(nullptr, natoms, nullptr, species.data(), natoms, nao.data(),
                             nabf.data(), cells[0]->stream, &m);
   if (s != HFX_OK) return fail(cells[0], s, "batch: cannot create the merged system");
-  for (int32_t c = 0; c < ncells && s == HFX_OK; ++c) {
-    hfx_ctx *ctx = cells[c];
-    for (int k = 0; k < 3 && s == HFX_OK; ++k) {
-      // packing here must not hide from the cell's own next build that its
-      // blocks changed since its last one: keep the kind's dirty flag
-      const bool was_dirty = ctx->K[k].dirty;
-      s = pack_kind(ctx, k);
-      ctx->K[k].dirty = was_dirty;
-      if (s != HFX_OK) break;
-      if (ctx->stream && cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
-        s = fail(ctx, HFX_E_CUDA, "batch: stream synchronisation failed");
-        break;
-      }
-      const Kind &K = ctx->K[k];
-      const int64_t nblk = (int64_t)K.keys.size();
-      if (nblk == 0) continue;
-      std::vector<int32_t> keys(5 * nblk);
-      for (int64_t e = 0; e < nblk; ++e) {
-        hk_unpack(K.keys[e], &keys[5 * e]);
-        keys[5 * e] += first[c];
-        keys[5 * e + 1] += first[c];
-      }
-      s = hfx_set_many(m, K.name, nblk, keys.data(), K.data.p, K.offs.data(), 1);
-      if (s != HFX_OK) fail(ctx, s, std::string("batch: ") + m->err);
-    }
-  }
+  for (int32_t c = 0; c < ncells && s == HFX_OK; ++c)
+    for (int k = 0; k < 3 && s == HFX_OK; ++k) s = copy_cell_kind(m, cells[c], k, first[c]);
   if (s != HFX_OK) {
     hfx_destroy(m);
     return s;
   }
-  m->theta_atom.resize(natoms);
-  for (int32_t c = 0; c < ncells; ++c)
-    for (int32_t a = first[c]; a < first[c + 1]; ++a) m->theta_atom[a] = thetas[c];
-  m->eps_eri = cells[0]->eps_eri;
   *out = m;
   return HFX_OK;
 }
@@ -1610,16 +1629,59 @@ hfx_status hfx_build_batch(hfx_ctx **cells, int32_t ncells, const double *thetas
       return fail(cells[c], HFX_E_ARG, "batch: the cells' ERI screen thresholds differ");
     cells[c]->results_valid = false;
   }
-  std::vector<int32_t> first;
-  hfx_ctx *m = nullptr;
-  hfx_status s = merge_cells(cells, ncells, thetas, first, &m);
-  if (s != HFX_OK) return s;
+  // the merged system of the last batch of the same cells is reused when no
+  // cell's C or V blocks changed and no D key set changed: its plan and
+  // sliced operands stay valid, and changed D values are copied in again
+  std::vector<uint64_t> ids(ncells);
+  std::vector<std::array<uint64_t, 3>> gens(ncells), kgens(ncells);
+  for (int32_t c = 0; c < ncells; ++c) {
+    ids[c] = cells[c]->id;
+    for (int k = 0; k < 3; ++k) {
+      gens[c][k] = cells[c]->gen[k];
+      kgens[c][k] = cells[c]->kgen[k];
+    }
+  }
+  BatchCache *bc = cells[0]->batch.get();
+  bool reuse = bc && bc->ids == ids;
+  for (int32_t c = 0; reuse && c < ncells; ++c)
+    reuse = bc->gens[c][0] == gens[c][0] && bc->gens[c][1] == gens[c][1] &&
+            bc->kgens[c][2] == kgens[c][2];
+  hfx_status s = HFX_OK;
+  if (reuse) {
+    for (int32_t c = 0; c < ncells && s == HFX_OK; ++c)
+      if (bc->gens[c][2] != gens[c][2]) s = copy_cell_kind(bc->merged, cells[c], 2, bc->first[c]);
+  } else {
+    cells[0]->batch.reset();
+    std::vector<int32_t> first;
+    hfx_ctx *m0 = nullptr;
+    s = merge_cells(cells, ncells, thetas, first, &m0);
+    if (s == HFX_OK) {
+      cells[0]->batch.reset(new BatchCache());
+      bc = cells[0]->batch.get();
+      bc->ids = ids;
+      bc->first = first;
+      bc->merged = m0;
+    }
+  }
+  if (s != HFX_OK) {
+    cells[0]->batch.reset();
+    return s;
+  }
+  hfx_ctx *m = bc->merged;
+  const std::vector<int32_t> &first = bc->first;
+  m->theta_atom.resize(first[ncells]);
+  for (int32_t c = 0; c < ncells; ++c)
+    for (int32_t a = first[c]; a < first[c + 1]; ++a) m->theta_atom[a] = thetas[c];
+  m->eps_eri = cells[0]->eps_eri;
+  m->results_valid = false;
   s = hfx_build(m, 0.0, prec, nslices, nullptr);
   if (s != HFX_OK) {
     for (int32_t c = 0; c < ncells; ++c) fail(cells[c], s, "batch: " + m->err);
-    hfx_destroy(m);
+    cells[0]->batch.reset();
     return s;
   }
+  bc->gens = gens;
+  bc->kgens = kgens;
   // Sigma, its fixed-point words and E_X of each cell from the merged result:
   // cell c's keys are the contiguous range with first atom in [first[c],
   // first[c + 1]); E_X reduces that range's per-block partials exactly as a
@@ -1628,7 +1690,7 @@ hfx_status hfx_build_batch(hfx_ctx **cells, int32_t ncells, const double *thetas
   auto fail_all = [&](const char *what, cudaError_t e) {
     for (int32_t c = 0; c < ncells; ++c)
       fail(cells[c], HFX_E_CUDA, std::string("batch: ") + what + ": " + cudaGetErrorString(e));
-    hfx_destroy(m);
+    cells[0]->batch.reset();
     return HFX_E_CUDA;
   };
   cudaStream_t st = m->stream;
@@ -1677,7 +1739,6 @@ hfx_status hfx_build_batch(hfx_ctx **cells, int32_t ncells, const double *thetas
     ctx->from_batch = true;
     if (ex_out) ex_out[c] = exs[c];
   }
-  hfx_destroy(m);
   return HFX_OK;
 }
 

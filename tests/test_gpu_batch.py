@@ -90,3 +90,34 @@ def test_batch_argument_errors():
     with pytest.raises(hfx.HfxError) as e:
         hfx.build_batch([c], [-1.0], "fp64")
     assert e.value.status == 1
+
+
+def test_batch_reuses_its_merged_system_and_follows_new_d():
+    """A second batch of the same cells reuses the merged system; after one
+    cell's D values change, the next batch copies them in and still equals a
+    build of that cell alone with the new D, bitwise."""
+    import paper_2009_12505_gb300 as hfx
+    wls = [synth.si_shrunk(seed=11), synth.ab_shrunk(seed=12)]
+    thetas = [1e-3, 1e-5]
+    ctxs = []
+    for wl in wls:
+        c = hfx.Context(wl.system.nao, wl.system.nabf)
+        for k in "CVD":
+            c.set_blocks(k, getattr(wl, k))
+        ctxs.append(c)
+    hfx.build_batch(ctxs, thetas, "ozaki", 6)
+    first = [c.sigma() for c in ctxs]
+    ex2 = hfx.build_batch(ctxs, thetas, "ozaki", 6)      # the cached plan
+    for c, f in zip(ctxs, first):
+        np.testing.assert_array_equal(c.sigma(), f)
+    # new D values for cell 1 (same keys; a common scale keeps D Hermitian)
+    d_new = synth.Blocks(wls[1].D.keys, wls[1].D.data * 1.5, wls[1].D.offs)
+    ctxs[1].set_blocks("D", d_new)
+    ex3 = hfx.build_batch(ctxs, thetas, "ozaki", 6)
+    wl_new = synth.Workload(wls[1].name, wls[1].system, wls[1].C, wls[1].V, d_new,
+                            wls[1].cut_C, wls[1].cut_V, wls[1].cut_D, wls[1].seed)
+    _, alone = gpu_build(wl_new, thetas[1], "ozaki", 6)
+    np.testing.assert_array_equal(ctxs[1].keys(), alone["keys"])
+    np.testing.assert_array_equal(ctxs[1].sigma(), alone["data"])
+    assert ex3[1] == alone["ex"] and ex3[0] == ex2[0]
+    np.testing.assert_array_equal(ctxs[0].sigma(), first[0])
