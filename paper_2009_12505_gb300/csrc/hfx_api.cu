@@ -684,9 +684,14 @@ hfx_status dz_prepare_meta(hfx_ctx *ctx, int ks) {
     naomin = std::min(naomin, ctx->nao[x]);
   }
   // staged Y rows per tile: al rows spanned by 128 (al, a) rows, all b (plus
-  // 2 pairs of padding per al), the 16-column blocks of one G
+  // 2 pairs of padding per al), the 16-column blocks of one G; for the small
+  // class (jobs whose blocks have at most 16 AOs) with the largest such atom
+  int naosmall = 1;
+  for (int x = 0; x < n; ++x)
+    if (ctx->nao[x] <= 16) naosmall = std::max(naosmall, ctx->nao[x]);
   ctx->zc_shape = ZcPlanShape{kbmax, naomax,
-                              (127 / naomin + 2) * (naomax * 16 + 2) * 8 * ((naomax + 15) / 16)};
+                              (127 / naomin + 2) * (naomax * 16 + 2) * 8 * ((naomax + 15) / 16),
+                              (127 / naomin + 2) * (naosmall * 16 + 2) * 8};
   CK(ctx->d_dz.reserve(std::max<int64_t>(off[nd], 1)));
   CK(ctx->d_dz_off.reserve(std::max<int64_t>(nd, 1)));
   CK(ctx->d_dij.reserve(std::max<int64_t>(2 * nd, 1)));
@@ -1294,7 +1299,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
       c.err = ctx->d_err.p;
       c.sym = ctx->sym ? 1 : 0;
       int nl = 0;
-      int zc_ctas = 0;
+      int zc_ctas[2] = {0, 0};  // CTAs of the small-class and the other D_FG / D_FB launch
       SplitWave SW{};
       if (split) {
         // per-wave split metadata
@@ -1394,9 +1399,9 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         // D_FG and D_FB pieces: count jobs and entries and histogram their cost
         // keys, size the lists, place the jobs longest first (Algorithm 6's
         // order), plan and run
-        constexpr int NKEYS = 256;
+        constexpr int NKEYS = 512, NCOST = 256;  // size class x cost
         CK(ctx->d_zckeys.reserve(NKEYS));
-        CK(ctx->d_ctans.reserve(std::max(ctx->nsm, 1)));
+        CK(ctx->d_ctans.reserve(2 * std::max(ctx->nsm, 1)));
         CK(cudaMemsetAsync(ctx->d_zckeys.p, 0, NKEYS * sizeof(int), st));
         SW.zc_keys = ctx->d_zckeys.p;
         SW.cta_ns = ctx->d_ctans.p;
@@ -1408,13 +1413,17 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         CK(cudaMemcpyAsync(hist.data(), ctx->d_zckeys.p, NKEYS * sizeof(int),
                            cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
+        // the small class's range first, each class longest first
+        int nsmall = 0;
+        for (int key = 0; key < NCOST; ++key) nsmall += hist[key];
         {
           int off = 0;
-          for (int key = NKEYS - 1; key >= 0; --key) {
-            const int c = hist[key];
-            hist[key] = off;
-            off += c;
-          }
+          for (int cls = 0; cls < 2; ++cls)
+            for (int key = cls * NCOST + NCOST - 1; key >= cls * NCOST; --key) {
+              const int c = hist[key];
+              hist[key] = off;
+              off += c;
+            }
         }
         CK(cudaMemcpyAsync(ctx->d_zckeys.p, hist.data(), NKEYS * sizeof(int),
                            cudaMemcpyHostToDevice, st));
@@ -1425,10 +1434,11 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         SW.zc_ents = ctx->d_zcents.p;
         SW.h_zc_jobs = nz[0];
         CK(split_zc_plan(SS, SW, 1, st));
-        CK(split_zc_run(SS, SW, nslices, ctx->zc_shape, ctx->nsm, st));
+        CK(split_zc_run(SS, SW, nslices, ctx->zc_shape, ctx->nsm, nsmall, st));
         CK(cudaEventRecord(ctx->kev[9], st));
-        ctx->launches += 2 * (nw > 0) + (nz[0] > 0);
-        zc_ctas = nz[0] > 0 ? (int)std::min<int64_t>(nz[0], ctx->nsm) : 0;
+        ctx->launches += 2 * (nw > 0) + (nsmall > 0) + (nz[0] > nsmall);
+        zc_ctas[0] = (int)std::min<int64_t>(nsmall, ctx->nsm);
+        zc_ctas[1] = (int)std::min<int64_t>(nz[0] - nsmall, ctx->nsm);
       }
       // the host offsets vector is reused next wave: order the copy first
       CK(cudaStreamSynchronize(st));
@@ -1454,11 +1464,12 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
         tmac_v4 += (double)tm[1];
         tmac_z += (double)tm[2];
         umac_z += (double)tm[3];
-        if (zc_ctas > 0) {
-          // load balance of this launch: largest and mean CTA busy time
-          std::vector<long long> ns(zc_ctas);
-          CK(cudaMemcpyAsync(ns.data(), ctx->d_ctans.p, sizeof(long long) * zc_ctas,
-                             cudaMemcpyDeviceToHost, st));
+        for (int l = 0; l < 2; ++l) {
+          if (zc_ctas[l] <= 0) continue;
+          // load balance of each launch: largest and mean CTA busy time
+          std::vector<long long> ns(zc_ctas[l]);
+          CK(cudaMemcpyAsync(ns.data(), ctx->d_ctans.p + l * ctx->nsm,
+                             sizeof(long long) * zc_ctas[l], cudaMemcpyDeviceToHost, st));
           CK(cudaStreamSynchronize(st));
           double mx = 0, sum = 0;
           for (long long v : ns) {
@@ -1466,7 +1477,7 @@ hfx_status hfx_build(hfx_ctx *ctx, double theta, hfx_prec prec, int32_t nslices,
             sum += (double)v;
           }
           zc_tmax += mx;
-          zc_tavg += sum / zc_ctas;
+          zc_tavg += sum / zc_ctas[l];
         }
       }
       ++nwaves;

@@ -16,9 +16,11 @@
 //
 // Roles (one CTA per SM, static round-robin over the wave's jobs): warp 8
 // copies each K tile's A and B digits (lanes 0 and 1, 1-D bulk copies) into a
-// ring of shared stages and, for Y jobs, then writes the job's epilogue data
-// (row exponents and Y2 offsets, column exponents) into one of two shared
-// slots, off the epilogue's path; warp 9 issues the MMAs into the TMEM accumulator;
+// ring of shared stages and then writes the job's epilogue data into one of
+// two shared slots, off the epilogue's path (Y jobs: row exponents and Y2
+// offsets, column exponents; D_AB jobs: the rows' (F, f) and columns' (G, g)
+// decoding with their exponents and the tile's Sigma_FG offsets per block
+// pair); warp 9 issues the MMAs into the TMEM accumulator;
 // warps 0-7 (TMEM lanes 32 (w % 4).., columns 32 (w / 4)..) drain the
 // accumulator into those sums, release it to the next job's MMAs, and then
 // write Y (f32 pairs, and FP64 where read) or add the surviving Sigma_FG
@@ -57,6 +59,135 @@ struct PgMetaY {
   int16_t ea[TM];     // row exponents
   int16_t eb[NT];     // column exponents (0 beyond nabf(A))
 };
+
+// One D_AB job's epilogue data, written by the loader warp ahead of the job:
+// the row (F, f) and column (G, g) decoding of the tile and, when the tile
+// spans at most PG_TBL (F block, G block) pairs, each pair's Sigma_FG offset
+// and that of its mirror (-1: no surviving term or no mirror).
+constexpr int PG_TBL = 160;
+struct PgMetaD {
+  int32_t fb0, gb0, nfb, ngb;  // first F and G neighbour index of the tile, block counts
+  int32_t tbl, mir, pad0, pad1;  // tbl: the offset table is filled; mir: mirror adds
+  int16_t fi[TM];     // row's F - fb0, -1: row past the atom's neighbour columns
+  int8_t f[TM], nf[TM];
+  int16_t ea[TM];     // row exponents
+  int16_t gi[NT];     // column's G - gb0, -1: column past the pair's columns
+  int8_t g[NT], ng[NT];
+  int16_t eb[NT];     // column exponents
+  int64_t off[PG_TBL], moff[PG_TBL];  // [fi * ngb + gi]
+};
+
+// Fill m for D_AB job jb (the whole loader warp); loads issued level by level.
+__device__ __forceinline__ void dab_meta_fill(const SplitShared &S, const SplitWave &W,
+                                              const Job &jb, const WorkItem &it, PgMetaD &m,
+                                              int lane) {
+  constexpr int RPL = TM / 32, CPL = NT / 32;
+  const int wl = (int)(jb.w - W.w0);
+  const int ncolA = S.ncol[it.a], ncolB = S.ncol[it.b];
+  const int64_t coloffA = S.coloff[it.a], coloffB = S.coloff[it.b];
+  const int16_t *ea_p = S.c4_e + S.c4_rowpre[it.a] + jb.mt * TM;
+  const int16_t *eb_p = W.ps_e + W.p_rowpre[wl] + jb.nt * NT;
+  int F[RPL], G[CPL];
+  bool rv[RPL], cv[CPL];
+  int16_t ea[RPL], eb[CPL];
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) {
+    const int rF = jb.mt * TM + lane + 32 * u;
+    rv[u] = rF < ncolA;
+    F[u] = rv[u] ? S.colG[coloffA + rF] : 0;
+    ea[u] = ea_p[lane + 32 * u];
+  }
+#pragma unroll
+  for (int u = 0; u < CPL; ++u) {
+    const int cG = jb.nt * NT + lane + 32 * u;
+    cv[u] = cG < ncolB;
+    G[u] = cv[u] ? S.colG[coloffB + cG] : 0;
+    eb[u] = cv[u] ? eb_p[lane + 32 * u] : (int16_t)0;
+  }
+  NbrEntry ef[RPL], eg[CPL];
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) ef[u] = S.nbr[it.fbase + F[u]];
+#pragma unroll
+  for (int u = 0; u < CPL; ++u) eg[u] = S.nbr[it.gbase + G[u]];
+  int fmax = 0, gmax = 0;
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) fmax = max(fmax, rv[u] ? F[u] : 0);
+#pragma unroll
+  for (int u = 0; u < CPL; ++u) gmax = max(gmax, cv[u] ? G[u] : 0);
+  for (int o = 16; o; o >>= 1) {
+    fmax = max(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
+    gmax = max(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+  }
+  // rows and columns are ordered by neighbour index: row 0 and column 0 hold
+  // the first blocks (a job's tile always starts inside the pair's columns)
+  const int fb0 = __shfl_sync(0xffffffffu, F[0], 0), gb0 = __shfl_sync(0xffffffffu, G[0], 0);
+  const int nfb = fmax - fb0 + 1, ngb = gmax - gb0 + 1;
+  const bool tbl = nfb * ngb <= PG_TBL;
+  const bool mir = S.sym && it.role == 1;
+#pragma unroll
+  for (int u = 0; u < RPL; ++u) {
+    const int r = lane + 32 * u;
+    m.fi[r] = rv[u] ? (int16_t)(F[u] - fb0) : (int16_t)-1;
+    m.f[r] = (int8_t)(rv[u] ? jb.mt * TM + r - ef[u].aopre : 0);
+    m.nf[r] = (int8_t)(rv[u] ? S.nao[ef[u].other] : 0);
+    m.ea[r] = ea[u];
+  }
+#pragma unroll
+  for (int u = 0; u < CPL; ++u) {
+    const int c = lane + 32 * u;
+    m.gi[c] = cv[u] ? (int16_t)(G[u] - gb0) : (int16_t)-1;
+    m.g[c] = (int8_t)(cv[u] ? jb.nt * NT + c - eg[u].aopre : 0);
+    m.ng[c] = (int8_t)(cv[u] ? S.nao[eg[u].other] : 0);
+    m.eb[c] = eb[u];
+  }
+  if (lane == 0) {
+    m.fb0 = fb0;
+    m.gb0 = gb0;
+    m.nfb = nfb;
+    m.ngb = ngb;
+    m.tbl = tbl ? 1 : 0;
+    m.mir = mir ? 1 : 0;
+  }
+  if (!tbl) return;
+  // Sigma_FG offsets of the tile's (F, G) block pairs with a surviving D_AB term
+  for (int q = lane; q < nfb * ngb; q += 32) {
+    const int Fq = fb0 + q / ngb, Gq = gb0 + q % ngb;
+    const NbrEntry a = S.nbr[it.fbase + Fq], b = S.nbr[it.gbase + Gq];
+    const uint32_t mw = S.masks[it.mask_off + ((int64_t)Gq * 4 + 3) * it.nFw + (Fq >> 5)];
+    int64_t off = -1, moff = -1;
+    if ((mw >> (Fq & 31)) & 1u) {
+      const int n0 = it.n[0] + b.n[0] - a.n[0], n1 = it.n[1] + b.n[1] - a.n[1],
+                n2 = it.n[2] + b.n[2] - a.n[2];
+      off = dh_find(S.shash, hk_pack(a.other, b.other, n0, n1, n2));
+      if (mir) moff = dh_find(S.shash, hk_pack(b.other, a.other, -n0, -n1, -n2));
+      if (off < 0 || (mir && moff < 0)) {
+        atomicOr(S.err, HFX_DEV_ERR_MISSING);
+        off = moff = -1;
+      }
+    }
+    m.off[q] = off;
+    m.moff[q] = moff;
+  }
+}
+
+// Sigma_FG offset and mirror offset of the block pair (F, G) of job jb (-1:
+// no surviving term), for tiles whose pairs do not fit the slot's table.
+__device__ __noinline__ void dab_lookup(const SplitShared &S, const Job &jb, int Fa, int Ga,
+                                        bool mir, int64_t &off, int64_t &moff) {
+  const WorkItem it = S.items[jb.w];
+  const NbrEntry ef = S.nbr[it.fbase + Fa], eg = S.nbr[it.gbase + Ga];
+  const uint32_t mw = S.masks[it.mask_off + ((int64_t)Ga * 4 + 3) * it.nFw + (Fa >> 5)];
+  off = moff = -1;
+  if (!((mw >> (Fa & 31)) & 1u)) return;
+  const int n0 = it.n[0] + eg.n[0] - ef.n[0], n1 = it.n[1] + eg.n[1] - ef.n[1],
+            n2 = it.n[2] + eg.n[2] - ef.n[2];
+  off = dh_find(S.shash, hk_pack(ef.other, eg.other, n0, n1, n2));
+  if (mir) moff = dh_find(S.shash, hk_pack(eg.other, ef.other, -n0, -n1, -n2));
+  if (off < 0 || (mir && moff < 0)) {
+    atomicOr(S.err, HFX_DEV_ERR_MISSING);
+    off = moff = -1;
+  }
+}
 
 // Fill m for Y job jb (the whole loader warp; lane l takes rows l, l + 32,
 // l + 64, l + 96).  The loads are issued level by level for the four rows at
@@ -150,6 +281,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
   extern __shared__ __align__(1024) uint8_t smem[];
   PgSmem *ctl = reinterpret_cast<PgSmem *>(smem + PG_NST * STAGE);
   PgMetaY *meta = reinterpret_cast<PgMetaY *>(smem + PG_NST * STAGE + PG_CTL_BYTES);
+  PgMetaD *metaD = reinterpret_cast<PgMetaD *>(smem + PG_NST * STAGE + PG_CTL_BYTES);
   volatile int *abort_f = &ctl->abort_f;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int njobs = W.njobs[JOB];
@@ -189,6 +321,34 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
       const __nv_bfloat16 *Ab, *Bb;
       const int16_t *ea_p, *eb_p;
       pg_operands<KS, JOB>(S, W, jb, it, Ab, Bb, ea_p, eb_p);
+      // The job's epilogue data go to slot mcount & 1, after the slot's last
+      // job is done with it.  A job of one accumulator chunk gets them after
+      // its copies (which then overlap the data's loads); a job of several
+      // chunks gets them first: its later copies wait for the MMAs of its
+      // second chunk, those for the epilogue's drain of its first, and that
+      // drain for these data.
+      auto put_meta = [&]() -> bool {
+        const int ms = (int)(mcount & 1);
+        const long long use = mcount >> 1;
+        bool w = true;
+        if (lane == 0) {
+          if (use >= 1)
+            w = umma::mbar_wait(&ctl->mempty[ms], (uint32_t)((use - 1) & 1), S.err, PG_WAIT);
+          w = w && !*abort_f;
+        }
+        if (!__shfl_sync(0xffffffffu, (int)w, 0)) {
+          if (lane == 0) *abort_f = 1;
+          return false;
+        }
+        if constexpr (JOB == 0) y_meta_fill(S, W, jb, it, meta[ms], lane);
+        else dab_meta_fill(S, W, jb, it, metaD[ms], lane);
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&ctl->mfull[ms]);
+        ++mcount;
+        return true;
+      };
+      const bool meta_first = jb.nk > KT_CHUNK;
+      if (meta_first && !put_meta()) break;
       bool ok = true;
       for (int kt = 0; kt < jb.nk; ++kt, ++step) {
         const int s = (int)(step % PG_NST);
@@ -214,27 +374,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
           umma::bulk_g2s(st + A_BYTES, Bb + (int64_t)kt * KS * NT * TK, B_BYTES, &ctl->full[s]);
       }
       if (!ok) break;
-      if constexpr (JOB == 0) {
-        if (jb.nk > 0) {
-          // the job's epilogue data, while its operand copies are in flight
-          const int ms = (int)(mcount & 1);
-          const long long use = mcount >> 1;
-          bool w = true;
-          if (lane == 0) {
-            if (use >= 1)
-              w = umma::mbar_wait(&ctl->mempty[ms], (uint32_t)((use - 1) & 1), S.err, PG_WAIT);
-            w = w && !*abort_f;
-          }
-          if (!__shfl_sync(0xffffffffu, (int)w, 0)) {
-            if (lane == 0) *abort_f = 1;
-            break;
-          }
-          y_meta_fill(S, W, jb, it, meta[ms], lane);
-          __syncwarp();
-          if (lane == 0) umma::mbar_arrive(&ctl->mfull[ms]);
-          ++mcount;
-        }
-      }
+      if (jb.nk > 0 && !meta_first && !put_meta()) break;
     }
     // drain: the last stages issued must have landed before the CTA exits
     if (lane == 0) {
@@ -314,11 +454,8 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
       int64_t yrow = 0, y2row = -1, nrowY = 0, y2base = 0, y64base = 0;
       bool need64 = false;
       int pA = 0, nbY = 0;
-      // D_AB job: row (F, f) and everything it needs from global memory
-      int F = 0, nf = 0, f = 0;
-      NbrEntry ef{};
-      WorkItem it{};
-      const int16_t *eb_p = nullptr;
+      // D_AB job: row (F - fb0, f) and the slot holding the job's data
+      int F = 0, nf = 0, f = 0, dms = 0;
       if constexpr (JOB == 0) {
         // the loader warp wrote this job's data into slot mcount & 1
         const int ms = (int)(mcount & 1);
@@ -349,21 +486,22 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         __syncwarp();
         if (lane == 0) umma::mbar_arrive(&ctl->mempty[ms]);
       } else {
-        // everything this thread needs from global memory, before the wait, so
-        // the dependent lookups overlap the job's MMAs
-        it = S.items[jb.w];
-        const __nv_bfloat16 *Ab, *Bb;
-        const int16_t *ea_p;
-        pg_operands<KS, JOB>(S, W, jb, it, Ab, Bb, ea_p, eb_p);
-        ea = ea_p[row];
-        const int rF = jb.mt * TM + row;
-        valid = rF < S.ncol[it.a];
-        if (valid) {
-          F = S.colG[S.coloff[it.a] + rF];
-          ef = S.nbr[it.fbase + F];
-          nf = S.nao[ef.other];
-          f = rF - ef.aopre;
+        // the loader warp wrote this job's data into slot mcount & 1; the slot
+        // is held until the Sigma adds at the end of the job
+        dms = (int)(mcount & 1);
+        const bool okm = umma::mbar_wait(&ctl->mfull[dms], (uint32_t)((mcount >> 1) & 1),
+                                         S.err, PG_WAIT);
+        ++mcount;
+        if (umma::bar_any(!okm || *abort_f, PG_EPI * 32)) {
+          *abort_f = 1;
+          break;
         }
+        const PgMetaD &m = metaD[dms];
+        ea = m.ea[row];
+        F = m.fi[row];
+        valid = F >= 0;
+        f = m.f[row];
+        nf = m.nf[row];
       }
 
       // one accumulator handoff per K chunk.  D_AB: the chunks' exact sums add
@@ -408,7 +546,9 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         if (lane == 0) umma::mbar_arrive(&ctl->tempty);
       }
       if (aborted) break;
-      if (!valid) continue;
+      // D_AB: every warp releases the job's slot after its adds, so a row
+      // outside the atom's columns skips the adds but not the release
+      if (!valid && JOB == 0) continue;
 
       if constexpr (JOB == 0) {
         // Y[al][b * ncol + col(G,g)] (FP64) and Y2 (f32 pairs) in 16-column
@@ -431,40 +571,41 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
           }
         }
       } else {
-        // Sigma_FG blocks: rows (F,f) of atom A, columns (G,g) of atom B
-        const int ncolB = S.ncol[it.b];
-        const bool mir = S.sym && it.role == 1;
-        int lastG = -1;
-        bool live = false;
+        // Sigma_FG blocks: rows (F,f) of atom A, columns (G,g) of atom B; the
+        // offsets come from the slot's table, or (a tile over more block pairs
+        // than the table holds) from the same lookups done here
+        const PgMetaD &m = metaD[dms];
+        const int ilim = valid ? 32 : 0;
+        int lastgi = -1;
         int64_t off = -1, moff = -1;
-        int ng = 0, gpre = 0;
-#pragma unroll 1
+        int ng = 0;
+        // unrolled, so the 32 chunk sums stay in registers
+#pragma unroll
         for (int i = 0; i < 32; ++i) {
-          const int cG = jb.nt * NT + c0 + i;
-          if (cG >= ncolB) break;
-          if (cG >= gpre + ng || lastG < 0) {
-            const int G = S.colG[S.coloff[it.b] + cG];
-            const NbrEntry eg = S.nbr[it.gbase + G];
-            lastG = G;
-            ng = S.nao[eg.other];
-            gpre = eg.aopre;
-            const uint32_t m = S.masks[it.mask_off + ((int64_t)G * 4 + 3) * it.nFw + (F >> 5)];
-            live = (m >> (F & 31)) & 1u;
-            off = moff = -1;
-            if (live) {
-              const int n0 = it.n[0] + eg.n[0] - ef.n[0], n1 = it.n[1] + eg.n[1] - ef.n[1],
-                        n2 = it.n[2] + eg.n[2] - ef.n[2];
-              off = dh_find(S.shash, hk_pack(ef.other, eg.other, n0, n1, n2));
-              if (mir) moff = dh_find(S.shash, hk_pack(eg.other, ef.other, -n0, -n1, -n2));
-              if (off < 0 || (mir && moff < 0)) atomicOr(S.err, HFX_DEV_ERR_MISSING);
+          const int c = c0 + i;
+          const int gi = m.gi[c];
+          if (i >= ilim || gi < 0) break;
+          if (gi != lastgi) {
+            lastgi = gi;
+            ng = m.ng[c];
+            if (m.tbl) {
+              off = m.off[F * m.ngb + gi];
+              moff = m.moff[F * m.ngb + gi];
+            } else {
+              dab_lookup(S, jb, m.fb0 + F, m.gb0 + gi, m.mir != 0, off, moff);
             }
           }
-          if (!live) continue;
-          const int g = cG - gpre;
-          const int e = ea + eb_p[c0 + i] - SH;
-          if (off >= 0) fx_add_scaled(S.acc + 2 * (off + (int64_t)f * ng + g), -Wv[i], e, S.err);
+          if (off < 0) continue;  // no surviving term in this block pair
+          const int g = m.g[c];
+          const int e = ea + m.eb[c] - SH;
+          fx_add_scaled(S.acc + 2 * (off + (int64_t)f * ng + g), -Wv[i], e, S.err);
           if (moff >= 0) fx_add_scaled(S.acc + 2 * (moff + (int64_t)g * nf + f), -Wv[i], e, S.err);
         }
+      }
+      if constexpr (JOB == 1) {
+        // the slot is free for the loader once every warp is done with it
+        __syncwarp();
+        if (lane == 0) umma::mbar_arrive(&ctl->mempty[dms]);
       }
     }
   }
@@ -479,7 +620,7 @@ cudaError_t launch_pgemm_t(const SplitShared &S, const SplitWave &W, int64_t max
   const int blocks = (int)std::min<int64_t>(maxjobs, S.nsm > 0 ? S.nsm : 1);
   if (blocks <= 0) return cudaSuccess;
   const size_t smem = (size_t)PG_NST * KS * (TM + NT) * TK * 2 + PG_CTL_BYTES +
-                      (JOB == 0 ? 2 * sizeof(PgMetaY) : 0) + 64;
+                      2 * (JOB == 0 ? sizeof(PgMetaY) : sizeof(PgMetaD)) + 64;
   cudaError_t e = cudaFuncSetAttribute(k_pgemm<KS, JOB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256, 3) k_screen(ScreenArgs A) {
   const double mvAB = it.dab >= 0 ? __dmul_rn(mv, A.D.maxabs[it.dab]) : 0.0;
   const int pA = A.nabf[it.a];
   const int na = A.nao[it.a], nb = A.nao[it.b], ng = A.nao[gt];
-  unsigned long long cnt[4] = {0, 0, 0, 0};
+  unsigned cnt[4] = {0, 0, 0, 0};  // surviving F per piece (at most nF each)
   unsigned long long macs = 0, pm[4] = {0, 0, 0, 0};
   unsigned eri_cut = 0;
   const double sqBG = A.eri_sq ? A.eri_sq[eg.cblk] : 0.0;
@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(256, 3) k_screen(ScreenArgs A) {
     if (any & 2u) sig_insert(A.sig_keys, A.sig_mask, hk_pack(it.a, gt, nG0, nG1, nG2),
                              A.sig_count, A.sig_limit, A.err);
     for (int v = 0; v < 4; ++v)
-      if (cnt[v]) atomicAdd(&A.counters[v], cnt[v]);
+      if (cnt[v]) atomicAdd(&A.counters[v], (unsigned long long)cnt[v]);
     if (any) {
       atomicAdd(&A.counters[4], 1ull);
       const int pB = A.nabf[it.b];

@@ -116,10 +116,12 @@ struct SplitWave {
   ZcJob *zc_jobs;
   ZcEnt *zc_ents;
   int64_t h_zc_jobs;
-  // 256 job-cost keys: the plan's count pass histograms them, the fill pass
-  // takes them as the start offsets of each key's range (longest first)
+  // 512 job keys (size class x cost): the plan's count pass histograms
+  // them, the fill pass takes them as the start offsets of each key's range
+  // (small class first, each class longest first)
   int *zc_keys;
-  // per CTA of the D_FG / D_FB product launch: its busy time in ns
+  // per CTA of the D_FG / D_FB product launches (small class at [0, nsm),
+  // the others at [nsm, 2 nsm)): busy time in ns
   long long *cta_ns;
 };
 
@@ -137,10 +139,11 @@ cudaError_t split_zc_plan(const SplitShared &S, const SplitWave &W, int fill, cu
 // largest block output count, shared bytes of one staged Y block.
 struct ZcPlanShape {
   int kbmax, nout_max, ybytes;
+  int ybytes_small;  // staged Y bytes for jobs whose blocks have at most 16 AOs
 };
 // D_FG / D_FB products of one wave (after phase 0: needs the Y pairs).
 cudaError_t split_zc_run(const SplitShared &S, const SplitWave &W, int ks, const ZcPlanShape &P,
-                         int nsm, cudaStream_t st);
+                         int nsm, int nsmall, cudaStream_t st);
 // Y products (job 0) or D_AB products (job 1) of the wave's job list,
 // persistent over at most maxjobs jobs.
 cudaError_t split_pgemm(const SplitShared &S, const SplitWave &W, int ks, int job,

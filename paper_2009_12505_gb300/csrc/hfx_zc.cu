@@ -169,9 +169,18 @@ __global__ void k_dz_slice(SplitShared S) {
 // pass histograms the keys, the host turns the histogram into descending
 // start offsets, and the fill pass places each job in its key's range, so the
 // list runs longest first (longest-processing-time order).
-constexpr int ZC_NKEYS = 256;
+constexpr int ZC_NCOST = 256;
+constexpr int ZC_NKEYS = 2 * ZC_NCOST;
 __device__ __forceinline__ int zc_cost_key(int mtz, int k) {
-  return min(ZC_NKEYS - 1, (mtz * (k / 16) + 3) / 4);
+  return min(ZC_NCOST - 1, (mtz * (k / 16) + 3) / 4);
+}
+// Size class of a job: small when every block it touches has at most 16 AOs
+// (outputs, Z columns and F entries), so its Y rows fit the staging buffers
+// of the fastest kernel variant; small jobs take keys [0, 256), the others
+// [256, 512), and the host places the small class first, so each class is a
+// contiguous, longest-first range launched with its own variant.
+__device__ __forceinline__ int zc_key(int mtz, int k, bool small) {
+  return zc_cost_key(mtz, k) + (small ? 0 : ZC_NCOST);
 }
 
 // Job handed to CTA b in round r of the persistent loop: rounds alternate
@@ -201,6 +210,9 @@ __device__ void zc_plan_group(const SplitShared &S, const SplitWave &W, const Wo
     ncv[q] = bp[q] == 1 ? S.nao[eg.other] : S.nao[it.b];
   }
   const unsigned long long rows = (unsigned long long)S.nabf[it.a] * S.nao[it.a];
+  // outputs and Z columns of both pieces are nao(B) and nao(G)
+  bool small = S.nao[it.b] <= 16;
+  for (int q = 0; q < nblk; ++q) small = small && S.nao[(int)eg_n[q][0]] <= 16;
   // cursor over the union bits: word wd, remaining bits u
   int wd = 0;
   uint32_t u = 0;
@@ -223,18 +235,19 @@ __device__ void zc_plan_group(const SplitShared &S, const SplitWave &W, const Wo
     const int wd0 = wd;
     const uint32_t u0 = u;
     const int f0 = f;
-    int n = 0, k = 0;
+    int n = 0, k = 0, kbm = 16;
     int fa = f;
     bool ma = true;
     while (ma) {
       const int kb = kb_of(S.nao[S.nbr[it.fbase + fa].other]);
       if (k + kb > ZC_KMAX) break;
       k += kb;
+      kbm = max(kbm, kb);
       ++n;
       ma = next(fa);
     }
     macs += (unsigned long long)mtz * 128 * ZC_COLS * k;
-    const int key = zc_cost_key(mtz, k);
+    const int key = zc_key(mtz, k, small && kbm == 16);
     int64_t eo = 0;
     if (!fill) {
       atomicAdd(W.njobs + 2, 1);
@@ -389,6 +402,8 @@ struct ZcSmem {
 // reduction buffer (16 or 32; the buffer is [column group][output][row]).
 struct ZcCfg {
   int ybytes, rs;
+  int jbeg, jend;  // the launch's range of the job list
+  int cta0;        // first slot of its CTAs' busy times
 };
 
 // Y rows al in [al0, al0 + nal) of the 16-column block cb: [al][b][16] pairs.
@@ -535,7 +550,7 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
   volatile int *abort_f = &ctl->abort_f;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int njobs = W.njobs[2];
+  const int njobs = cfg.jend - cfg.jbeg;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -578,7 +593,7 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
       if (r * (int)gridDim.x >= njobs || j >= njobs) break;
       // one decision for the whole warp
       if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
-      const ZcJob jb = W.zc_jobs[j];
+      const ZcJob jb = W.zc_jobs[cfg.jbeg + j];
       const WorkItem it = S.items[jb.w];
       const int mtz = (S.nabf[it.a] * S.nao[it.a] + 127) / 128;
       const __nv_bfloat16 *Abase = S.cz + S.cz_base[it.a];
@@ -656,7 +671,7 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         const int j = zc_job_of(r, blockIdx.x, gridDim.x);
         if (r * (int)gridDim.x >= njobs || j >= njobs) break;
         if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
-        const ZcJob jb = W.zc_jobs[j];
+        const ZcJob jb = W.zc_jobs[cfg.jbeg + j];
         const WorkItem it = S.items[jb.w];
         const int wl = (int)(jb.w - W.w0);
         const int pA = S.nabf[it.a], na = S.nao[it.a], nb = S.nao[it.b];
@@ -715,7 +730,7 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
       for (int r = 0; !*abort_f; ++r) {
         const int j = zc_job_of(r, blockIdx.x, gridDim.x);
         if (r * (int)gridDim.x >= njobs || j >= njobs) break;
-        const ZcJob jb = W.zc_jobs[j];
+        const ZcJob jb = W.zc_jobs[cfg.jbeg + j];
         const WorkItem it = S.items[jb.w];
         const int mtz = (S.nabf[it.a] * S.nao[it.a] + 127) / 128;
         int R0 = 16;  // rows of a lone block (two blocks have 16 each)
@@ -766,7 +781,7 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
     for (int r = 0;; ++r) {
       const int j = zc_job_of(r, blockIdx.x, gridDim.x);
       if (r * (int)gridDim.x >= njobs || j >= njobs) break;
-      const ZcJob jb = W.zc_jobs[j];
+      const ZcJob jb = W.zc_jobs[cfg.jbeg + j];
       const WorkItem it = S.items[jb.w];
       const int wl = (int)(jb.w - W.w0);
       const int pA = S.nabf[it.a], na = S.nao[it.a], nb = S.nao[it.b];
@@ -1024,7 +1039,7 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
   if (threadIdx.x == 0) {
     unsigned long long t_end;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
-    W.cta_ns[blockIdx.x] = (long long)(t_end - ctl->t_start);
+    W.cta_ns[cfg.cta0 + blockIdx.x] = (long long)(t_end - ctl->t_start);
   }
 }
 
@@ -1033,9 +1048,9 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
 constexpr bool ZC_STAGE_Y = true;
 
 template <int KS>
-cudaError_t zc_run_t(const SplitShared &S, const SplitWave &W, const ZcPlanShape &P, int nsm,
-                     cudaStream_t st) {
-  const int blocks = (int)std::min<int64_t>(W.h_zc_jobs, nsm);
+cudaError_t zc_range_t(const SplitShared &S, const SplitWave &W, const ZcPlanShape &P, int nsm,
+                       int jbeg, int jend, int cta0, cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>(jend - jbeg, nsm);
   if (blocks <= 0) return cudaSuccess;
   constexpr size_t kMax = 227 * 1024;
   const int rs = P.nout_max <= 16 ? 16 : 32;
@@ -1048,7 +1063,7 @@ cudaError_t zc_run_t(const SplitShared &S, const SplitWave &W, const ZcPlanShape
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<blocks, threads, smem, st>>>(S, W, ZcCfg{ybytes, rs});
+    kern<<<blocks, threads, smem, st>>>(S, W, ZcCfg{ybytes, rs, jbeg, jend, cta0});
     return cudaGetLastError();
   };
   // 8 epilogue warps (2 column groups of 16).  16 warps (4 groups of 8) leave
@@ -1064,6 +1079,22 @@ cudaError_t zc_run_t(const SplitShared &S, const SplitWave &W, const ZcPlanShape
   if (ZC_STAGE_Y && smem_of(2, 32, P.ybytes, 2) <= kMax)
     return launch(k_zc<KS, 32, 2, 8, true>, T8, 2, 32, P.ybytes, 2);
   return launch(k_zc<KS, 32, 2, 8, false>, T8, 2, 32, 0, 2);
+}
+
+// The wave's small-class jobs [0, nsmall) with the shape of blocks of at most
+// 16 AOs, then the others with the system's shape.
+template <int KS>
+cudaError_t zc_run_t(const SplitShared &S, const SplitWave &W, const ZcPlanShape &P, int nsm,
+                     int nsmall, cudaStream_t st) {
+  const int njobs = (int)W.h_zc_jobs;
+  if (nsmall > 0) {
+    const ZcPlanShape Q{16, 16, P.ybytes_small, P.ybytes_small};
+    cudaError_t e = zc_range_t<KS>(S, W, Q, nsm, 0, nsmall, 0, st);
+    if (e != cudaSuccess) return e;
+  }
+  if (njobs > nsmall)
+    return zc_range_t<KS>(S, W, P, nsm, nsmall, njobs, nsm, st);
+  return cudaSuccess;
 }
 
 template <int KS>
@@ -1090,12 +1121,12 @@ cudaError_t split_zc_plan(const SplitShared &S, const SplitWave &W, int fill, cu
 }
 
 cudaError_t split_zc_run(const SplitShared &S, const SplitWave &W, int ks, const ZcPlanShape &P,
-                         int nsm, cudaStream_t st) {
+                         int nsm, int nsmall, cudaStream_t st) {
   switch (ks) {
-    case 2: return split::zc_run_t<2>(S, W, P, nsm, st);
-    case 4: return split::zc_run_t<4>(S, W, P, nsm, st);
-    case 5: return split::zc_run_t<5>(S, W, P, nsm, st);
-    case 6: return split::zc_run_t<6>(S, W, P, nsm, st);
+    case 2: return split::zc_run_t<2>(S, W, P, nsm, nsmall, st);
+    case 4: return split::zc_run_t<4>(S, W, P, nsm, nsmall, st);
+    case 5: return split::zc_run_t<5>(S, W, P, nsm, nsmall, st);
+    case 6: return split::zc_run_t<6>(S, W, P, nsm, nsmall, st);
     default: return cudaErrorInvalidValue;
   }
 }
