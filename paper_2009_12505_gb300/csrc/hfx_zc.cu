@@ -174,9 +174,9 @@ constexpr int ZC_NKEYS = 2 * ZC_NCOST;
 __device__ __forceinline__ int zc_cost_key(int mtz, int k) {
   return min(ZC_NCOST - 1, (mtz * (k / 16) + 3) / 4);
 }
-// Size class of a job: small when every block it touches has at most 16 AOs
-// (outputs, Z columns and F entries), so its Y rows fit the staging buffers
-// of the fastest kernel variant; small jobs take keys [0, 256), the others
+// Size class of a job: small when atom A and every block it touches have at
+// most 16 AOs (outputs, Z columns and F entries), so its Y rows fit the
+// staging buffers of the fastest kernel variant, which pairs its jobs; small jobs take keys [0, 256), the others
 // [256, 512), and the host places the small class first, so each class is a
 // contiguous, longest-first range launched with its own variant.
 __device__ __forceinline__ int zc_key(int mtz, int k, bool small) {
@@ -210,8 +210,9 @@ __device__ void zc_plan_group(const SplitShared &S, const SplitWave &W, const Wo
     ncv[q] = bp[q] == 1 ? S.nao[eg.other] : S.nao[it.b];
   }
   const unsigned long long rows = (unsigned long long)S.nabf[it.a] * S.nao[it.a];
-  // outputs and Z columns of both pieces are nao(B) and nao(G)
-  bool small = S.nao[it.b] <= 16;
+  // outputs and Z columns of both pieces are nao(B) and nao(G); the small
+  // class also bounds atom A (the outputs an epilogue thread owns)
+  bool small = S.nao[it.b] <= 16 && S.nao[it.a] <= 16;
   for (int q = 0; q < nblk; ++q) small = small && S.nao[(int)eg_n[q][0]] <= 16;
   // cursor over the union bits: word wd, remaining bits u
   int wd = 0;
@@ -388,14 +389,168 @@ __global__ void __launch_bounds__(128) k_zc_plan(SplitShared S, SplitWave W, int
 
 // ---------------------------------------------------------------- product
 
+// Epilogue data of one job, written to shared memory by a few lanes when its
+// pair starts and read by every epilogue thread on each of the job's tiles.
+struct ZcEpiJob {
+  int64_t czrow0;    // first row of atom A's C exponents
+  int64_t y2off;     // the work item's Y pairs in the wave scratch
+  int64_t sg[2][2];  // block q: Sigma offset of its outputs, of their mirror (-1: none)
+  int pA, na, nb, mtz, nblk, R0b;
+  int nout[2], ncv[2], pc[2], gcb[2];
+};
+
 struct ZcSmem {
   uint64_t full[8], empty[8], tfull[2], tempty[2], yfull[2], yempty[2], drain;
   unsigned long long t_start;  // globaltimer at the start of the roles
   uint32_t tslot;
   int abort_f;
   int stkb[8];  // K of the entry in each operand stage (16 or 32)
-  int ecol[ZC_COLS];  // column exponents of the job (column group q at q * CW)
+  int ecol[2][ZC_COLS];  // column exponents of the pair's jobs (column group q at q * CW)
+  ZcEpiJob ej[2][2];     // [pair parity][job of the pair]
 };
+
+// Number of jobs CTA b receives from zc_job_of over a list of njobs.
+__device__ __forceinline__ int zc_cta_jobs(int njobs, int b, int G) {
+  const int full = njobs / G, rem = njobs - full * G;
+  return full + (((full & 1) ? G - 1 - b : b) < rem ? 1 : 0);
+}
+
+// Tile order of a CTA.  Its jobs r = 0 .. n - 1 run heaviest first (operand
+// stages x row tiles).  With PAIR, pair p is job n - 1 - p (light) and job p
+// (heavy), and their row tiles alternate while both have some: the MMAs of a
+// long tile then run beside the epilogue of a short one, where one job after
+// the other leaves the epilogue idle through the long tiles and the tensor
+// pipe idle through the short ones.  Without PAIR, pair p is job p alone.
+// Every role walks the same order.
+template <bool PAIR>
+struct ZcPair {
+  int r0, r1, m0, m1, t0, t1, last;
+  bool two;
+  __device__ __forceinline__ void begin(int p, int n) {
+    r0 = PAIR ? n - 1 - p : p;
+    r1 = PAIR ? p : -1;
+    two = PAIR && r1 < r0;
+    m0 = m1 = t0 = t1 = 0;
+    last = 1;
+  }
+  // next tile: job x of the pair (0: r0, 1: r1) and its row tile mt
+  __device__ __forceinline__ bool next(int &x, int &mt) {
+    const bool a = t0 < m0, b = t1 < m1;
+    if (!a && !b) return false;
+    x = (a && (!b || last == 1)) ? 0 : 1;
+    last = x;
+    mt = x ? t1++ : t0++;
+    return true;
+  }
+};
+
+template <class T>
+__device__ __forceinline__ void zc_swap(T &a, T &b) {
+  const T t = a;
+  a = b;
+  b = t;
+}
+
+__device__ __forceinline__ ZcJob zc_job(const SplitWave &W, int jbeg, int r) {
+  return W.zc_jobs[jbeg + zc_job_of(r, blockIdx.x, gridDim.x)];
+}
+
+// rows of a job's lone column block (16 or 32); two blocks have 16 each
+__device__ __forceinline__ int zc_rows(const SplitShared &S, const ZcJob &jb, const WorkItem &it) {
+  if (jb.nblk != 1) return 16;
+  const int ncb = jb.piece[0] == 1 ? S.nao[S.nbr[it.gbase + jb.g[0]].other] : S.nao[it.b];
+  return ncb <= 16 ? 16 : 32;
+}
+
+// block and first column cq of column group q of width CW: two 16-column
+// blocks take half the groups each; one block takes the groups below its R
+template <int CW>
+__device__ __forceinline__ int zc_group_block(int nblk, int R0b, int q, int &cq) {
+  const int jc = q * CW;
+  if (nblk == 2) { cq = jc & 15; return jc >> 4; }
+  cq = jc;
+  return jc < R0b ? 0 : -1;
+}
+
+// Epilogue data of job r, by one whole warp: lanes 0 .. 3 look up the Sigma
+// offsets of block lane / 2 (odd lanes: the mirror), lane 4 the scalars.  A
+// missing Sigma key fails the build, and the block is not added.
+__device__ __forceinline__ void zc_epi_job(const SplitShared &S, const SplitWave &W, int jbeg,
+                                           int r, int lane, ZcEpiJob &e) {
+  const ZcJob jb = zc_job(W, jbeg, r);
+  const WorkItem it = S.items[jb.w];
+  const int q = (lane >> 1) & 1, m = lane & 1;
+  int64_t t = -1;
+  bool miss = false;
+  if (lane < 4 && q < jb.nblk) {
+    const int pcb = q ? jb.piece[1] : jb.piece[0];
+    const bool mir = S.sym && (pcb == 2 || it.role == 1);
+    if (m == 0 || mir) {
+      if (pcb == 1) {
+        t = m == 0 ? dh_find(S.shash, hk_pack(it.a, it.b, it.n[0], it.n[1], it.n[2]))
+                   : dh_find(S.shash, hk_pack(it.b, it.a, -it.n[0], -it.n[1], -it.n[2]));
+      } else {
+        const NbrEntry eg = S.nbr[it.gbase + (q ? jb.g[1] : jb.g[0])];
+        const int n0 = it.n[0] + eg.n[0], n1 = it.n[1] + eg.n[1], n2 = it.n[2] + eg.n[2];
+        t = m == 0 ? dh_find(S.shash, hk_pack(it.a, eg.other, n0, n1, n2))
+                   : dh_find(S.shash, hk_pack(eg.other, it.a, -n0, -n1, -n2));
+      }
+      miss = t < 0;
+      if (miss) atomicOr(S.err, HFX_DEV_ERR_MISSING);
+    }
+  }
+  const bool bad = __shfl_sync(0xffffffffu, (int)miss, lane & ~1) |
+                   __shfl_sync(0xffffffffu, (int)miss, lane | 1);
+  if (lane < 4) e.sg[q][m] = bad ? -1 : t;
+  if (lane == 4) {
+    const int pA = S.nabf[it.a], na = S.nao[it.a], nb = S.nao[it.b];
+    e.czrow0 = S.cz_rowpre[it.a];
+    e.y2off = W.y2_off[(int)(jb.w - W.w0)];
+    e.pA = pA;
+    e.na = na;
+    e.nb = nb;
+    e.mtz = (pA * na + 127) / 128;
+    e.nblk = jb.nblk;
+    e.R0b = 16;
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      e.nout[b] = e.ncv[b] = e.pc[b] = e.gcb[b] = 0;
+      if (b < jb.nblk) {
+        const int ng = S.nao[S.nbr[it.gbase + jb.g[b]].other];
+        e.pc[b] = jb.piece[b];
+        e.gcb[b] = S.kofs[it.gbase + jb.g[b]] / 16;
+        e.ncv[b] = jb.piece[b] == 1 ? ng : nb;
+        e.nout[b] = jb.piece[b] == 1 ? nb : ng;
+      }
+    }
+    if (jb.nblk > 0) e.R0b = e.ncv[0] <= 16 ? 16 : 32;
+  }
+}
+
+// Column exponents of job r's column group hf (CW columns), by lanes < CW.
+template <int CW>
+__device__ __forceinline__ void zc_epi_ecol(const SplitShared &S, const SplitWave &W, int jbeg,
+                                            int r, int hf, int lane, int *ecol) {
+  if (lane >= CW) return;
+  const ZcJob jb = zc_job(W, jbeg, r);
+  const WorkItem it = S.items[jb.w];
+  int ncv0 = 0, R0b = 16;
+  if (jb.nblk > 0) {
+    ncv0 = jb.piece[0] == 1 ? S.nao[S.nbr[it.gbase + jb.g[0]].other] : S.nao[it.b];
+    R0b = ncv0 <= 16 ? 16 : 32;
+  }
+  int c0 = 0;
+  const int hb = zc_group_block<CW>(jb.nblk, R0b, hf, c0);
+  int e = -1000;
+  if (hb >= 0) {
+    const int pc = hb ? jb.piece[1] : jb.piece[0], g = hb ? jb.g[1] : jb.g[0];
+    const int at = pc == 1 ? S.nbr[it.gbase + g].other : it.b;
+    const int ncvh = S.nao[at];  // piece 1: nao(G); piece 2: nao(B)
+    const int cc = c0 + lane;
+    if (cc < ncvh) e = row_exponent((long long)S.de[S.aoff[at] + cc]);
+  }
+  ecol[hf * CW + lane] = e;
+}
 
 // Launch shape of k_zc: ybytes = shared bytes per staged Y block (0: the
 // epilogue reads Y from global memory), rs = outputs per block held in the
@@ -534,11 +689,66 @@ __device__ __forceinline__ void zc_contract2(const uint64_t (&zh)[NP], const uin
   }
 }
 
-template <int KS, int KBM, int NST, int EPI, bool YST>
+// Loader-warp view of a job: operand bases, its entries (lane l holds entry
+// held + l) and the B rows per block.
+struct ZcLd {
+  const __nv_bfloat16 *A;
+  int64_t ktot, ent;
+  int nent, nblk, Rl, mtz, held;
+  ZcEnt mine;
+};
+
+__device__ __forceinline__ void zc_ld_job(const SplitShared &S, const SplitWave &W, int jbeg,
+                                          int r, ZcLd &L) {
+  const ZcJob jb = zc_job(W, jbeg, r);
+  const WorkItem it = S.items[jb.w];
+  L.A = S.cz + S.cz_base[it.a];
+  L.ktot = S.ktotZ[it.a];
+  L.ent = jb.ent;
+  L.nent = jb.nent;
+  L.nblk = jb.nblk;
+  L.Rl = zc_rows(S, jb, it);
+  L.mtz = (S.nabf[it.a] * S.nao[it.a] + 127) / 128;
+  L.held = -1;
+  L.mine = ZcEnt{0, 0, {-1, -1}};
+}
+
+// Y-loader view of a job: its Y pairs, sizes and the 16-column blocks of Y
+// columns of each column block.
+struct ZcYJob {
+  const float2 *Y2;
+  int pA, na, nb, mtz, nblk, ncb0, ncb1, cb0, cb1;
+};
+
+__device__ __forceinline__ void zc_y_job(const SplitShared &S, const SplitWave &W, int jbeg,
+                                         int r, ZcYJob &Y) {
+  const ZcJob jb = zc_job(W, jbeg, r);
+  const WorkItem it = S.items[jb.w];
+  Y.Y2 = reinterpret_cast<const float2 *>(W.scratch + W.y2_off[(int)(jb.w - W.w0)]);
+  Y.pA = S.nabf[it.a];
+  Y.na = S.nao[it.a];
+  Y.nb = S.nao[it.b];
+  Y.mtz = (Y.pA * Y.na + 127) / 128;
+  Y.nblk = jb.nblk;
+  Y.ncb0 = Y.ncb1 = Y.cb0 = Y.cb1 = 0;
+  if (jb.nblk > 0) {
+    Y.ncb0 = (S.nao[S.nbr[it.gbase + jb.g[0]].other] + 15) / 16;
+    Y.cb0 = S.kofs[it.gbase + jb.g[0]] / 16;
+  }
+  if (jb.nblk > 1) {
+    Y.ncb1 = (S.nao[S.nbr[it.gbase + jb.g[1]].other] + 15) / 16;
+    Y.cb1 = S.kofs[it.gbase + jb.g[1]] / 16;
+  }
+}
+
+template <int KS, int KBM, int NST, int EPI, bool YST, bool PAIR>
 __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
     k_zc(SplitShared S, SplitWave W, ZcCfg cfg) {
   constexpr int ZC_EPI = EPI, ZC_NQ = ZcGeo<EPI>::NQ, ZC_CW = ZcGeo<EPI>::CW,
-                ZC_ET = ZcGeo<EPI>::ET, ZC_OWN = ZcGeo<EPI>::OWN;
+                ZC_ET = ZcGeo<EPI>::ET;
+  // owned outputs per epilogue thread: paired jobs have blocks and atom A of
+  // at most 16 AOs, so at most 16 x 32 outputs per job
+  constexpr int ZC_OWN = PAIR ? (16 * 32 + ZC_ET - 1) / ZC_ET : ZcGeo<EPI>::OWN;
   constexpr int A_BYTES = KS * 128 * KBM * 2;
   constexpr int B_BYTES = KS * ZC_COLS * KBM * 2;
   constexpr int STG = A_BYTES + B_BYTES;
@@ -551,6 +761,9 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int njobs = cfg.jend - cfg.jbeg;
+  // this CTA's jobs and pairs
+  const int ncj = zc_cta_jobs(njobs, blockIdx.x, gridDim.x);
+  const int npair = PAIR ? (ncj + 1) / 2 : ncj;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -588,40 +801,38 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
     // the stage, then lane 0 copies the A tile and lanes 1 .. nblk one whole
     // B block each
     long long step = 0;
-    for (int r = 0;; ++r) {
-      const int j = zc_job_of(r, blockIdx.x, gridDim.x);
-      if (r * (int)gridDim.x >= njobs || j >= njobs) break;
+    bool ok = true;
+    for (int p = 0; p < npair && ok; ++p) {
       // one decision for the whole warp
       if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
-      const ZcJob jb = W.zc_jobs[cfg.jbeg + j];
-      const WorkItem it = S.items[jb.w];
-      const int mtz = (S.nabf[it.a] * S.nao[it.a] + 127) / 128;
-      const __nv_bfloat16 *Abase = S.cz + S.cz_base[it.a];
-      const int64_t ktot = S.ktotZ[it.a];
-      // B rows per block: 16 each for two blocks; 16 or 32 for one
-      int R0 = 16;
-      if (jb.nblk == 1) {
-        const int ncb = jb.piece[0] == 1 ? S.nao[S.nbr[it.gbase + jb.g[0]].other] : S.nao[it.b];
-        R0 = ncb <= 16 ? 16 : 32;
+      ZcPair<PAIR> pr;
+      pr.begin(p, ncj);
+      ZcLd L, Lo;  // L: the job of the current tile, Lo: the pair's other job
+      zc_ld_job(S, W, cfg.jbeg, pr.r0, L);
+      pr.m0 = L.mtz;
+      if (pr.two) {
+        zc_ld_job(S, W, cfg.jbeg, pr.r1, Lo);
+        pr.m1 = Lo.mtz;
       }
-      const int cb = lane - 1;
-      const bool has_b = lane >= 1 && lane <= jb.nblk;
-      const int Rl = jb.nblk == 1 ? R0 : 16;
-      ZcEnt mine = {0, 0, {-1, -1}};
-      int held = -1;  // q0 of the entries the lanes hold
-      bool ok = true;
-      for (int mt = 0; mt < mtz && ok; ++mt)
-        for (int q0 = 0; q0 < jb.nent && ok; q0 += 32) {
-          if (held != q0) {
-            if (q0 + lane < jb.nent) mine = W.zc_ents[jb.ent + q0 + lane];
-            held = q0;
+      int cur = 0, x, mt;
+      while (ok && pr.next(x, mt)) {
+        if (x != cur) {
+          zc_swap(L, Lo);
+          cur = x;
+        }
+        const int cb = lane - 1;
+        const bool has_b = lane >= 1 && lane <= L.nblk;
+        for (int q0 = 0; q0 < L.nent && ok; q0 += 32) {
+          if (L.held != q0) {
+            if (q0 + lane < L.nent) L.mine = W.zc_ents[L.ent + q0 + lane];
+            L.held = q0;
           }
-          const int nq = min(32, jb.nent - q0);
+          const int nq = min(32, L.nent - q0);
           for (int qq = 0; qq < nq; ++qq, ++step) {
-            const int kofs = __shfl_sync(0xffffffffu, mine.kofs, qq);
-            const int kb = __shfl_sync(0xffffffffu, mine.kb, qq);
-            const long long d0 = __shfl_sync(0xffffffffu, (long long)mine.dz[0], qq);
-            const long long d1 = __shfl_sync(0xffffffffu, (long long)mine.dz[1], qq);
+            const int kofs = __shfl_sync(0xffffffffu, L.mine.kofs, qq);
+            const int kb = __shfl_sync(0xffffffffu, L.mine.kb, qq);
+            const long long d0 = __shfl_sync(0xffffffffu, (long long)L.mine.dz[0], qq);
+            const long long d1 = __shfl_sync(0xffffffffu, (long long)L.mine.dz[1], qq);
             const int s = (int)(step % NST);
             bool w = true;
             if (lane == 0) {
@@ -638,24 +849,25 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
             }
             uint8_t *st = smem + s * STG;
             const uint32_t abytes = (uint32_t)(KS * 128 * kb * 2);
-            const uint32_t bbytes = (uint32_t)(KS * kb * 2) * (uint32_t)(jb.nblk * Rl);
+            const uint32_t bbytes = (uint32_t)(KS * kb * 2) * (uint32_t)(L.nblk * L.Rl);
             if (lane == 0) {
               ctl->stkb[s] = kb;  // read by the MMA issuer after the stage lands
               umma::mbar_arrive_expect_tx(&ctl->full[s], abytes + bbytes);
             }
             __syncwarp();
             if (lane == 0) {
-              umma::bulk_g2s(st, Abase + ((int64_t)mt * ktot + kofs) * KS * 128, abytes,
+              umma::bulk_g2s(st, L.A + ((int64_t)mt * L.ktot + kofs) * KS * 128, abytes,
                              &ctl->full[s]);
             } else if (has_b) {
               // B stage block-major: block b's KS digits of Rl rows x kb at b KS 16 kb
               const int64_t dz = cb == 0 ? d0 : d1;
               const __nv_bfloat16 *src = dz >= 0 ? S.dz + dz : S.dzero;
               umma::bulk_g2s(st + A_BYTES + cb * (KS * 16 * kb * 2), src,
-                             (uint32_t)(KS * Rl * kb * 2), &ctl->full[s]);
+                             (uint32_t)(KS * L.Rl * kb * 2), &ctl->full[s]);
             }
           }
         }
+      }
     }
     // drain: the last stages issued must have landed before the CTA exits
     if (lane == 0) {
@@ -667,24 +879,24 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
     // ------------------------------------------------------------ Y loader
     if constexpr (YST) {
       long long hand = 0;
-      for (int r = 0;; ++r) {
-        const int j = zc_job_of(r, blockIdx.x, gridDim.x);
-        if (r * (int)gridDim.x >= njobs || j >= njobs) break;
+      bool ok = true;
+      for (int p = 0; p < npair && ok; ++p) {
         if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
-        const ZcJob jb = W.zc_jobs[cfg.jbeg + j];
-        const WorkItem it = S.items[jb.w];
-        const int wl = (int)(jb.w - W.w0);
-        const int pA = S.nabf[it.a], na = S.nao[it.a], nb = S.nao[it.b];
-        const int mtz = (pA * na + 127) / 128;
-        const float2 *Y2 = reinterpret_cast<const float2 *>(W.scratch + W.y2_off[wl]);
-        int ncbg[2] = {0, 0}, cbs[2] = {0, 0};
-        for (int b = 0; b < jb.nblk; ++b) {
-          const NbrEntry eg = S.nbr[it.gbase + jb.g[b]];
-          ncbg[b] = (S.nao[eg.other] + 15) / 16;
-          cbs[b] = S.kofs[it.gbase + jb.g[b]] / 16;
+        ZcPair<PAIR> pr;
+        pr.begin(p, ncj);
+        ZcYJob Y, Yo;
+        zc_y_job(S, W, cfg.jbeg, pr.r0, Y);
+        pr.m0 = Y.mtz;
+        if (pr.two) {
+          zc_y_job(S, W, cfg.jbeg, pr.r1, Yo);
+          pr.m1 = Yo.mtz;
         }
-        bool ok = true;
-        for (int mt = 0; mt < mtz; ++mt, ++hand) {
+        int cur = 0, x, mt;
+        while (pr.next(x, mt)) {
+          if (x != cur) {
+            zc_swap(Y, Yo);
+            cur = x;
+          }
           const int tb = (int)(hand & 1);
           const long long use = hand >> 1;
           bool w = true;
@@ -698,21 +910,22 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
             ok = false;
             break;
           }
-          const int al0 = mt * 128 / na, al1 = min(pA - 1, (mt * 128 + 127) / na);
+          ++hand;
+          const int al0 = mt * 128 / Y.na, al1 = min(Y.pA - 1, (mt * 128 + 127) / Y.na);
           const int nal = al1 - al0 + 1;
-          const uint32_t run = (uint32_t)(nb * 16 * 8);  // one al's [b][16] pairs
-          const int n0 = ncbg[0] * nal, ncopy = n0 + (jb.nblk > 1 ? ncbg[1] * nal : 0);
+          const uint32_t run = (uint32_t)(Y.nb * 16 * 8);  // one al's [b][16] pairs
+          const int n0 = Y.ncb0 * nal, ncopy = n0 + (Y.nblk > 1 ? Y.ncb1 * nal : 0);
           if (lane == 0) umma::mbar_arrive_expect_tx(&ctl->yfull[tb], (uint32_t)ncopy * run);
           __syncwarp();
           for (int q = lane; q < ncopy; q += 32) {
             const int b = q < n0 ? 0 : 1;
             const int r = q - (b ? n0 : 0), k = r / nal, al = al0 + r - k * nal;
             uint8_t *dst = ybuf + (tb * 2 + b) * cfg.ybytes +
-                           ((int64_t)(k * nal + (al - al0)) * (nb * 16 + ZC_YPAD)) * 8;
-            umma::bulk_g2s(dst, zc_y_global(Y2, cbs[b] + k, pA, nb, al), run, &ctl->yfull[tb]);
+                           ((int64_t)(k * nal + (al - al0)) * (Y.nb * 16 + ZC_YPAD)) * 8;
+            umma::bulk_g2s(dst, zc_y_global(Y.Y2, (b ? Y.cb1 : Y.cb0) + k, Y.pA, Y.nb, al), run,
+                           &ctl->yfull[tb]);
           }
         }
-        if (!ok) break;
       }
     }
   } else if (warp == ZC_EPI + 1) {
@@ -727,30 +940,41 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         idesc32[i] = umma::idesc_bf16_f32(128, 32 * (KS - i));
       }
       const uint32_t sbase = umma::smem_u32(smem);
-      for (int r = 0; !*abort_f; ++r) {
-        const int j = zc_job_of(r, blockIdx.x, gridDim.x);
-        if (r * (int)gridDim.x >= njobs || j >= njobs) break;
-        const ZcJob jb = W.zc_jobs[cfg.jbeg + j];
-        const WorkItem it = S.items[jb.w];
-        const int mtz = (S.nabf[it.a] * S.nao[it.a] + 127) / 128;
-        int R0 = 16;  // rows of a lone block (two blocks have 16 each)
-        if (jb.nblk == 1) {
-          const int ncb = jb.piece[0] == 1 ? S.nao[S.nbr[it.gbase + jb.g[0]].other] : S.nao[it.b];
-          R0 = ncb <= 16 ? 16 : 32;
+      bool ok = true;
+      for (int p = 0; p < npair && ok && !*abort_f; ++p) {
+        ZcPair<PAIR> pr;
+        pr.begin(p, ncj);
+        // entries, blocks and rows per block of the pair's two jobs
+        int ne0, nk0, R0, ne1 = 0, nk1 = 0, R1 = 16;
+        {
+          const ZcJob jb = zc_job(W, cfg.jbeg, pr.r0);
+          const WorkItem it = S.items[jb.w];
+          ne0 = jb.nent;
+          nk0 = jb.nblk;
+          R0 = zc_rows(S, jb, it);
+          pr.m0 = (S.nabf[it.a] * S.nao[it.a] + 127) / 128;
         }
-        const int R = jb.nblk == 1 ? R0 : 16;
-        for (int mt = 0; mt < mtz && !*abort_f; ++mt, ++hand) {
+        if (pr.two) {
+          const ZcJob jb = zc_job(W, cfg.jbeg, pr.r1);
+          const WorkItem it = S.items[jb.w];
+          ne1 = jb.nent;
+          nk1 = jb.nblk;
+          R1 = zc_rows(S, jb, it);
+          pr.m1 = (S.nabf[it.a] * S.nao[it.a] + 127) / 128;
+        }
+        int x, mt;
+        while (ok && !*abort_f && pr.next(x, mt)) {
+          const int nent = x ? ne1 : ne0, nblk = x ? nk1 : nk0, R = x ? R1 : R0;
           const int tb = (int)(hand & 1);
           const long long use = hand >> 1;
           if (use >= 1 &&
               !umma::mbar_wait(&ctl->tempty[tb], (uint32_t)((use - 1) & 1), S.err, ZC_WAIT)) {
-            *abort_f = 1;
+            ok = false;
             break;
           }
           umma::fence_after_sync();
           const uint32_t dcol = tbase + (uint32_t)(tb * 256);
-          bool ok = true;
-          for (int q = 0; q < jb.nent; ++q, ++step) {
+          for (int q = 0; q < nent; ++q, ++step) {
             const int s = (int)(step % NST);
             if (!umma::mbar_wait(&ctl->full[s], (uint32_t)((step / NST) & 1), S.err, ZC_WAIT)) {
               ok = false;
@@ -759,15 +983,17 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
             umma::fence_after_sync();
             const uint32_t a0 = sbase + (uint32_t)(s * STG);
             if (KBM == 16 || ctl->stkb[s] == 16)
-              zc_stage_mmas<KS, 16>(a0, a0 + A_BYTES, dcol, jb.nblk, R, idesc16, idesc32, q == 0);
+              zc_stage_mmas<KS, 16>(a0, a0 + A_BYTES, dcol, nblk, R, idesc16, idesc32, q == 0);
             else
-              zc_stage_mmas<KS, 32>(a0, a0 + A_BYTES, dcol, jb.nblk, R, idesc16, idesc32, q == 0);
+              zc_stage_mmas<KS, 32>(a0, a0 + A_BYTES, dcol, nblk, R, idesc16, idesc32, q == 0);
             umma::mma_commit(&ctl->empty[s]);
           }
-          if (!ok) { *abort_f = 1; break; }
+          if (!ok) break;
           umma::mma_commit(&ctl->tfull[tb]);
+          ++hand;
         }
       }
+      if (!ok) *abort_f = 1;
       umma::mma_commit(&ctl->drain);
       umma::mbar_wait(&ctl->drain, 0, S.err, ZC_WAIT);
     }
@@ -778,78 +1004,55 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
     const int et = threadIdx.x;  // 0 .. ZC_ET - 1
     const int rs = cfg.rs;
     long long hand = 0;
-    for (int r = 0;; ++r) {
-      const int j = zc_job_of(r, blockIdx.x, gridDim.x);
-      if (r * (int)gridDim.x >= njobs || j >= njobs) break;
-      const ZcJob jb = W.zc_jobs[cfg.jbeg + j];
-      const WorkItem it = S.items[jb.w];
-      const int wl = (int)(jb.w - W.w0);
-      const int pA = S.nabf[it.a], na = S.nao[it.a], nb = S.nao[it.b];
-      const int mtz = (pA * na + 127) / 128;
-      const float2 *Y2 = reinterpret_cast<const float2 *>(W.scratch + W.y2_off[wl]);
-      // blocks 0 and 1: Z columns, outputs, TMEM rows per order, 16-column
-      // block of G's Y columns (scalars: no dynamically indexed arrays)
-      int ncv0 = 0, ncv1 = 0, nout0 = 0, nout1 = 0, R0b = 16, gcb0 = 0, gcb1 = 0;
-      const int pc0 = jb.piece[0], pc1 = jb.piece[1];
-      if (jb.nblk > 0) {
-        const int G = S.nbr[it.gbase + jb.g[0]].other, ng = S.nao[G];
-        gcb0 = S.kofs[it.gbase + jb.g[0]] / 16;
-        ncv0 = pc0 == 1 ? ng : nb;
-        nout0 = pc0 == 1 ? nb : ng;
-        R0b = ncv0 <= 16 ? 16 : 32;
+    bool aborted = false;
+    for (int p = 0; p < npair && !aborted; ++p) {
+      const int pp = p & 1;
+      ZcPair<PAIR> pr;
+      pr.begin(p, ncj);
+      // the pair's epilogue data: warps 0 and 1 the jobs' scalars and Sigma
+      // offsets, warps 2 + x + 4 hf the column exponents of job x's column
+      // group hf.  The previous pair's reads of the column exponents are
+      // behind its tile barriers, and its data sit in the other parity.
+      if (q4 < 2) {
+        if (hf == 0 && (q4 == 0 || pr.two))
+          zc_epi_job(S, W, cfg.jbeg, q4 ? pr.r1 : pr.r0, lane, ctl->ej[pp][q4]);
+      } else if (q4 == 2 || pr.two) {
+        zc_epi_ecol<ZC_CW>(S, W, cfg.jbeg, q4 == 3 ? pr.r1 : pr.r0, hf, lane, ctl->ecol[q4 - 2]);
       }
-      if (jb.nblk > 1) {
-        const int G = S.nbr[it.gbase + jb.g[1]].other, ng = S.nao[G];
-        gcb1 = S.kofs[it.gbase + jb.g[1]] / 16;
-        ncv1 = pc1 == 1 ? ng : nb;
-        nout1 = pc1 == 1 ? nb : ng;
-      }
-      // block and columns [c0, c0 + ZC_CW) of column group q (two 16-column
-      // blocks: the first half of the groups each; one block: all groups below R)
-      auto group_block = [&](int q, int &cq) -> int {
-        const int jc = q * ZC_CW;
-        if (jb.nblk == 2) { cq = jc & 15; return jc >> 4; }
-        cq = jc;
-        return jc < R0b ? 0 : -1;
-      };
-      int c0 = 0;
-      const int hb = group_block(hf, c0);
-      const bool h1 = hb == 1;
-      const int piece = hb >= 0 ? (h1 ? pc1 : pc0) : 0;
-      const int Rh = h1 ? 16 : R0b;
-      const int noh = h1 ? nout1 : nout0, ncvh = h1 ? ncv1 : ncv0, gcbh = h1 ? gcb1 : gcb0;
-      // column groups feeding block 0 and block 1 (bit q)
-      unsigned qm0 = 0, qm1 = 0;
+      asm volatile("bar.sync 1, %0;" ::"r"(ZC_ET) : "memory");
+      pr.m0 = ctl->ej[pp][0].mtz;
+      if (pr.two) pr.m1 = ctl->ej[pp][1].mtz;
+      // job sums of the owned outputs (f32 pairs): jh / jl of the current
+      // tile's job, oh / ol of the pair's other job
+      float jh[ZC_OWN], jl[ZC_OWN], oh[ZC_OWN], ol[ZC_OWN];
 #pragma unroll
-      for (int q = 0; q < ZC_NQ; ++q) {
-        int cq;
-        const int bq = group_block(q, cq);
-        qm0 |= (bq == 0 ? 1u : 0u) << q;
-        qm1 |= (bq == 1 ? 1u : 0u) << q;
-      }
-      // column exponents of this warp's columns (shared by the group's warps;
-      // the previous job's last reads are behind the tile barriers)
-      const int *ecol = ctl->ecol + hf * ZC_CW;
-      if (q4 == 0 && lane < ZC_CW) {
-        const int at = hb >= 0 ? (piece == 1 ? S.nbr[it.gbase + (h1 ? jb.g[1] : jb.g[0])].other
-                                             : it.b)
-                               : 0;
-        const int cc = c0 + lane;
-        ctl->ecol[hf * ZC_CW + lane] = (hb >= 0 && cc < ncvh)
-                                  ? row_exponent((long long)S.de[S.aoff[at] + cc]) : -1000;
-      }
-      float jh[ZC_OWN], jl[ZC_OWN];  // job sums of the owned outputs (f32 pairs)
+      for (int k = 0; k < ZC_OWN; ++k) jh[k] = jl[k] = oh[k] = ol[k] = 0.f;
+      int cur = 0, x, mt;
+      while (pr.next(x, mt)) {
+        if (x != cur) {
 #pragma unroll
-      for (int k = 0; k < ZC_OWN; ++k) { jh[k] = 0.f; jl[k] = 0.f; }
-      const int64_t czrow0 = S.cz_rowpre[it.a];
-      const int own0 = na * nout0;
-      const int nown = own0 + na * nout1;
-      bool aborted = false;
-      for (int mt = 0; mt < mtz; ++mt, ++hand) {
+          for (int k = 0; k < ZC_OWN; ++k) {
+            zc_swap(jh[k], oh[k]);
+            zc_swap(jl[k], ol[k]);
+          }
+          cur = x;
+        }
+        const ZcEpiJob &ej = ctl->ej[pp][x];
+        const int pA = ej.pA, na = ej.na, nb = ej.nb;
         const int tb = (int)(hand & 1);
         const uint32_t par = (uint32_t)((hand >> 1) & 1);
+        ++hand;
         // this row's exponent, read before the wait so its latency is hidden
-        const int eA = (mt * 128 + row < pA * na) ? S.cz_e[czrow0 + mt * 128 + row] : 0;
+        const int eA = (mt * 128 + row < pA * na) ? S.cz_e[ej.czrow0 + mt * 128 + row] : 0;
+        // this warp's column group: block hb, its first column c0
+        int c0 = 0;
+        const int hb = zc_group_block<ZC_CW>(ej.nblk, ej.R0b, hf, c0);
+        const int hq = hb > 0 ? 1 : 0;
+        const int piece = hb >= 0 ? ej.pc[hq] : 0;
+        const int Rh = hq ? 16 : ej.R0b;
+        const int noh = ej.nout[hq], ncvh = ej.ncv[hq], gcbh = ej.gcb[hq];
+        const int *ecol = ctl->ecol[x] + hf * ZC_CW;
+        const float2 *Y2 = reinterpret_cast<const float2 *>(W.scratch + ej.y2off);
         bool okw = umma::mbar_wait(&ctl->tfull[tb], par, S.err, ZC_WAIT);
         if constexpr (YST) {
           if (okw) okw = umma::mbar_wait(&ctl->yfull[tb], par, S.err, ZC_WAIT);
@@ -964,6 +1167,16 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         asm volatile("bar.sync 1, %0;" ::"r"(ZC_ET) : "memory");
         // owners: (block, a, o) summed over the tile's rows (al, a) and the
         // block's column groups, in a fixed order
+        const int nout0 = ej.nout[0];
+        const int own0 = na * nout0, nown = own0 + na * ej.nout[1];
+        unsigned qm0 = 0, qm1 = 0;  // column groups feeding block 0 and block 1 (bit q)
+#pragma unroll
+        for (int q = 0; q < ZC_NQ; ++q) {
+          int cq;
+          const int bq = zc_group_block<ZC_CW>(ej.nblk, ej.R0b, q, cq);
+          qm0 |= (bq == 0 ? 1u : 0u) << q;
+          qm1 |= (bq == 1 ? 1u : 0u) << q;
+        }
         const int r0 = mt * 128, rend = min(pA * na, r0 + 128);
         const int ph = r0 % na;
 #pragma unroll
@@ -994,42 +1207,28 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
           jl[k] = l;
         }
         asm volatile("bar.sync 1, %0;" ::"r"(ZC_ET) : "memory");
-      }
-      if (aborted) break;
-      // add the finished blocks to Sigma (and mirrors); a sum outside the
-      // fixed-point range is not added and fails the build
-      bool inrange = true;
+        if (mt + 1 < ej.mtz) continue;
+        // the job's last tile: add its finished blocks to Sigma (and mirrors);
+        // a sum outside the fixed-point range is not added and fails the build
+        bool inrange = true;
 #pragma unroll
-      for (int k = 0; k < ZC_OWN; ++k)
-        if (et + k * ZC_ET < nown) inrange = inrange && fx_df_in_range(jh[k]);
-      if (!inrange) atomicOr(S.err, HFX_DEV_ERR_BOUNDS);
+        for (int k = 0; k < ZC_OWN; ++k)
+          if (et + k * ZC_ET < nown) inrange = inrange && fx_df_in_range(jh[k]);
+        if (!inrange) atomicOr(S.err, HFX_DEV_ERR_BOUNDS);
 #pragma unroll
-      for (int k = 0; k < ZC_OWN && inrange; ++k) {
-        const int idx = et + k * ZC_ET;
-        if (idx >= nown) break;
-        const bool b1 = idx >= own0;
-        const int nob = b1 ? nout1 : nout0;
-        const int rem = idx - (b1 ? own0 : 0);
-        const int o = rem / na, a = rem - o * na;
-        const int pcb = b1 ? pc1 : pc0;
-        const NbrEntry eg = S.nbr[it.gbase + (b1 ? jb.g[1] : jb.g[0])];
-        const int nG0 = it.n[0] + eg.n[0], nG1 = it.n[1] + eg.n[1], nG2 = it.n[2] + eg.n[2];
-        int64_t t0, t1 = -1;
-        const bool mir = S.sym && (pcb == 2 || it.role == 1);
-        if (pcb == 1) {
-          t0 = dh_find(S.shash, hk_pack(it.a, it.b, it.n[0], it.n[1], it.n[2]));
-          if (mir) t1 = dh_find(S.shash, hk_pack(it.b, it.a, -it.n[0], -it.n[1], -it.n[2]));
-        } else {
-          t0 = dh_find(S.shash, hk_pack(it.a, eg.other, nG0, nG1, nG2));
-          if (mir) t1 = dh_find(S.shash, hk_pack(eg.other, it.a, -nG0, -nG1, -nG2));
+        for (int k = 0; k < ZC_OWN && inrange; ++k) {
+          const int idx = et + k * ZC_ET;
+          if (idx >= nown) break;
+          const int b1 = idx >= own0 ? 1 : 0;
+          const int nob = ej.nout[b1];
+          const int rem = idx - (b1 ? own0 : 0);
+          const int o = rem / na, a = rem - o * na;
+          const int64_t t0 = ej.sg[b1][0], t1 = ej.sg[b1][1];
+          if (t0 < 0) continue;  // missing key: recorded when the pair started
+          const float2 v = make_float2(jh[k], jl[k]);
+          fx_add_df(S.acc + 2 * (t0 + (int64_t)a * nob + o), v, true);
+          if (t1 >= 0) fx_add_df(S.acc + 2 * (t1 + (int64_t)o * na + a), v, true);
         }
-        if (t0 < 0 || (mir && t1 < 0)) {
-          atomicOr(S.err, HFX_DEV_ERR_MISSING);
-          continue;
-        }
-        const float2 v = make_float2(jh[k], jl[k]);
-        fx_add_df(S.acc + 2 * (t0 + (int64_t)a * nob + o), v, true);
-        if (t1 >= 0) fx_add_df(S.acc + 2 * (t1 + (int64_t)o * na + a), v, true);
       }
     }
   }
@@ -1049,7 +1248,7 @@ constexpr bool ZC_STAGE_Y = true;
 
 template <int KS>
 cudaError_t zc_range_t(const SplitShared &S, const SplitWave &W, const ZcPlanShape &P, int nsm,
-                       int jbeg, int jend, int cta0, cudaStream_t st) {
+                       int jbeg, int jend, int cta0, bool small, cudaStream_t st) {
   const int blocks = (int)std::min<int64_t>(jend - jbeg, nsm);
   if (blocks <= 0) return cudaSuccess;
   constexpr size_t kMax = 227 * 1024;
@@ -1069,16 +1268,20 @@ cudaError_t zc_range_t(const SplitShared &S, const SplitWave &W, const ZcPlanSha
   // 8 epilogue warps (2 column groups of 16).  16 warps (4 groups of 8) leave
   // room for only two operand stages next to the staged Y and were slower.
   constexpr int T8 = ZcGeo<8>::THREADS;
+  // The small class (every block and atom A of at most 16 AOs) pairs its jobs
+  // when its staged Y fits next to four operand stages.
   if (P.kbmax <= 16) {
-    if (ZC_STAGE_Y && smem_of(4, 16, P.ybytes, 2) <= kMax)
-      return launch(k_zc<KS, 16, 4, 8, true>, T8, 4, 16, P.ybytes, 2);
+    if (ZC_STAGE_Y && smem_of(4, 16, P.ybytes, 2) <= kMax) {
+      if (small) return launch(k_zc<KS, 16, 4, 8, true, true>, T8, 4, 16, P.ybytes, 2);
+      return launch(k_zc<KS, 16, 4, 8, true, false>, T8, 4, 16, P.ybytes, 2);
+    }
     if (ZC_STAGE_Y && smem_of(3, 16, P.ybytes, 2) <= kMax)
-      return launch(k_zc<KS, 16, 3, 8, true>, T8, 3, 16, P.ybytes, 2);
-    return launch(k_zc<KS, 16, 3, 8, false>, T8, 3, 16, 0, 2);
+      return launch(k_zc<KS, 16, 3, 8, true, false>, T8, 3, 16, P.ybytes, 2);
+    return launch(k_zc<KS, 16, 3, 8, false, false>, T8, 3, 16, 0, 2);
   }
   if (ZC_STAGE_Y && smem_of(2, 32, P.ybytes, 2) <= kMax)
-    return launch(k_zc<KS, 32, 2, 8, true>, T8, 2, 32, P.ybytes, 2);
-  return launch(k_zc<KS, 32, 2, 8, false>, T8, 2, 32, 0, 2);
+    return launch(k_zc<KS, 32, 2, 8, true, false>, T8, 2, 32, P.ybytes, 2);
+  return launch(k_zc<KS, 32, 2, 8, false, false>, T8, 2, 32, 0, 2);
 }
 
 // The wave's small-class jobs [0, nsmall) with the shape of blocks of at most
@@ -1089,11 +1292,11 @@ cudaError_t zc_run_t(const SplitShared &S, const SplitWave &W, const ZcPlanShape
   const int njobs = (int)W.h_zc_jobs;
   if (nsmall > 0) {
     const ZcPlanShape Q{16, 16, P.ybytes_small, P.ybytes_small};
-    cudaError_t e = zc_range_t<KS>(S, W, Q, nsm, 0, nsmall, 0, st);
+    cudaError_t e = zc_range_t<KS>(S, W, Q, nsm, 0, nsmall, 0, true, st);
     if (e != cudaSuccess) return e;
   }
   if (njobs > nsmall)
-    return zc_range_t<KS>(S, W, P, nsm, nsmall, njobs, nsm, st);
+    return zc_range_t<KS>(S, W, P, nsm, nsmall, njobs, nsm, false, st);
   return cudaSuccess;
 }
 
