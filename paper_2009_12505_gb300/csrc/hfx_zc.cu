@@ -1116,8 +1116,56 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
           else
             return zc_y_global(Y2, gcbh + k, pA, nb, al);
         };
-        // Z (f32 pairs) and the contraction with Y
-        if (hb >= 0 && rvalid) {
+        // a tile of at most 32 valid rows (the last of an atom of 13 AOs and 60
+        // ABFs holds 12): its rows are all in TMEM lane quarter 0, so that
+        // quarter's warps stage Z in rows 32 .. 63 of the reduction buffer
+        // (unused by such a tile) and all epilogue warps share the contraction
+        const int rv = min(128, pA * na - mt * 128);
+        if (PAIR && YST && rv <= 32) {
+          constexpr int NPT = ZC_CW / 2;
+          if (q4 == 0 && hb >= 0 && rvalid) {
+            float2 *zs = red + (int64_t)hf * rs * 128 + 32 + row;
+#pragma unroll
+            for (int j = 0; j < NPT; ++j) {
+              float2 z0, z1;
+              df_fin2(ds[j], dr[j], eA + ecol[2 * j] - SH, eA + ecol[2 * j + 1] - SH, z0, z1);
+              const int cend = min(ZC_CW, ncvh - c0);
+              zs[(2 * j) * 128] = 2 * j < cend ? z0 : make_float2(0.f, 0.f);
+              zs[(2 * j + 1) * 128] = 2 * j + 1 < cend ? z1 : make_float2(0.f, 0.f);
+            }
+          }
+          asm volatile("bar.sync 1, %0;" ::"r"(ZC_ET) : "memory");
+          // items (row r, column group q, output o), rows fastest; each output
+          // takes the same operations as in the row-per-thread form below
+          for (int idx = et; idx < ZC_NQ * 16 * 32; idx += ZC_ET) {
+            const int r = idx & 31, qo = idx >> 5, q = qo >> 4, o = qo & 15;
+            int cq = 0;
+            const int bq = zc_group_block<ZC_CW>(ej.nblk, ej.R0b, q, cq);
+            if (r >= rv || bq < 0) continue;
+            const int bqi = bq > 0 ? 1 : 0;
+            if (o >= ej.nout[bqi]) continue;
+            const int cend = min(ZC_CW, ej.ncv[bqi] - cq);
+            const float2 *zs = red + (int64_t)q * rs * 128 + 32 + r;
+            uint64_t zh[NPT], nzh[NPT], nzl[NPT];
+#pragma unroll
+            for (int j = 0; j < NPT; ++j) {
+              const float2 z0 = zs[(2 * j) * 128], z1 = zs[(2 * j + 1) * 128];
+              zh[j] = f2_pk(z0.x, z1.x);
+              nzh[j] = f2_pk(-z0.x, -z1.x);
+              nzl[j] = f2_pk(-z0.y, -z1.y);
+            }
+            const int alr = (mt * 128 + r) / na;
+            const float2 *yq = reinterpret_cast<const float2 *>(ybuf + (tb * 2 + bq) * cfg.ybytes);
+            float2 *outp = red + ((int64_t)q * rs + o) * 128 + r;
+            if (ej.pc[bqi] == 1) {
+              const float2 *yb = yq + ((int64_t)(cq >> 4) * nal + (alr - al0)) * (nb * 16 + ZC_YPAD);
+              zc_contract2<NPT, true>(zh, nzh, nzl, cend, yb + (cq & 15) + o * 16, 1, outp);
+            } else {
+              const float2 *yb = yq + ((int64_t)(o >> 4) * nal + (alr - al0)) * (nb * 16 + ZC_YPAD);
+              zc_contract2<NPT, false>(zh, nzh, nzl, cend, yb + cq * 16 + (o & 15), 1, outp);
+            }
+          }
+        } else if (hb >= 0 && rvalid) {
           const int cend = min(ZC_CW, ncvh - c0);
           float2 *rr = red + (int64_t)hf * rs * 128 + row;
           // Z = (order-group sum) 2^(eA + ecol - SH) as f32 pairs; zero from cend on
