@@ -579,27 +579,49 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         int lastgi = -1;
         int64_t off = -1, moff = -1;
         int ng = 0;
-        // unrolled, so the 32 chunk sums stay in registers
+        if (m.tbl) {
+          // unrolled and free of calls, so the 32 chunk sums stay in registers
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int c = c0 + i;
-          const int gi = m.gi[c];
-          if (i >= ilim || gi < 0) break;
-          if (gi != lastgi) {
-            lastgi = gi;
-            ng = m.ng[c];
-            if (m.tbl) {
+          for (int i = 0; i < 32; ++i) {
+            const int c = c0 + i;
+            const int gi = m.gi[c];
+            if (i >= ilim || gi < 0) break;
+            if (gi != lastgi) {
+              lastgi = gi;
+              ng = m.ng[c];
               off = m.off[F * m.ngb + gi];
               moff = m.moff[F * m.ngb + gi];
-            } else {
+            }
+            if (off < 0) continue;  // no surviving term in this block pair
+            const int g = m.g[c];
+            const int e = ea + m.eb[c] - SH;
+            fx_add_scaled(S.acc + 2 * (off + (int64_t)f * ng + g), -Wv[i], e, S.err);
+            if (moff >= 0)
+              fx_add_scaled(S.acc + 2 * (moff + (int64_t)g * nf + f), -Wv[i], e, S.err);
+          }
+        } else if (valid) {
+          // a tile over more block pairs than the table holds: the same adds
+          // in the same order, the sums copied to a local array first so the
+          // lookups' call does not hold them
+          long long Wl[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) Wl[i] = Wv[i];
+          for (int i = 0; i < 32; ++i) {
+            const int c = c0 + i;
+            const int gi = m.gi[c];
+            if (gi < 0) break;
+            if (gi != lastgi) {
+              lastgi = gi;
+              ng = m.ng[c];
               dab_lookup(S, jb, m.fb0 + F, m.gb0 + gi, m.mir != 0, off, moff);
             }
+            if (off < 0) continue;
+            const int g = m.g[c];
+            const int e = ea + m.eb[c] - SH;
+            fx_add_scaled(S.acc + 2 * (off + (int64_t)f * ng + g), -Wl[i], e, S.err);
+            if (moff >= 0)
+              fx_add_scaled(S.acc + 2 * (moff + (int64_t)g * nf + f), -Wl[i], e, S.err);
           }
-          if (off < 0) continue;  // no surviving term in this block pair
-          const int g = m.g[c];
-          const int e = ea + m.eb[c] - SH;
-          fx_add_scaled(S.acc + 2 * (off + (int64_t)f * ng + g), -Wv[i], e, S.err);
-          if (moff >= 0) fx_add_scaled(S.acc + 2 * (moff + (int64_t)g * nf + f), -Wv[i], e, S.err);
         }
       }
       if constexpr (JOB == 1) {

@@ -150,8 +150,8 @@ __global__ void k_slice_v(SplitShared S) {
 constexpr int PD_THREADS = 256;
 
 template <int KS>
-__global__ void __launch_bounds__(PD_THREADS) k_pdig(SplitShared S, SplitWave W) {
-  extern __shared__ float2 Ps[];  // [gc][K], then the staged Y [al][b][gc]
+__global__ void __launch_bounds__(PD_THREADS, 3) k_pdig(SplitShared S, SplitWave W) {
+  extern __shared__ __align__(16) float2 Ps[];  // [gc][K], then the staged Y
   __shared__ int es[32];
   __shared__ float2 Dp[32 * 32];  // D_AB as f32 pairs
   const int64_t t = blockIdx.x;
@@ -189,26 +189,62 @@ __global__ void __launch_bounds__(PD_THREADS) k_pdig(SplitShared S, SplitWave W)
     const int gn = min(gc, ng - g0);
     // stage Y[al][b][g0 .. g0 + gc) (Y2 layout [cb][al][b][16]; g0 is a multiple
     // of gc, so the gc pairs stay inside one 16-column block and one sector)
+    // staged as [al][b] rows of gc high words, then gc low words (gc > 1), so
+    // two columns' high (low) words are one register pair
     const float2 *yb = Y2 + ((int64_t)(cbG + (g0 >> 4)) * pA * nb) * 16 + (g0 & 15);
+    float *Yf = reinterpret_cast<float *>(Ys);
     for (int r = threadIdx.x; r < nrow; r += PD_THREADS) {
       const float2 *src = yb + (int64_t)r * 16;
       if (gc == 4) {
         const float4 u0 = reinterpret_cast<const float4 *>(src)[0];
         const float4 u1 = reinterpret_cast<const float4 *>(src)[1];
-        reinterpret_cast<float4 *>(Ys + r * 4)[0] = u0;
-        reinterpret_cast<float4 *>(Ys + r * 4)[1] = u1;
+        reinterpret_cast<float4 *>(Yf + r * 8)[0] = make_float4(u0.x, u0.z, u1.x, u1.z);
+        reinterpret_cast<float4 *>(Yf + r * 8)[1] = make_float4(u0.y, u0.w, u1.y, u1.w);
+      } else if (gc == 2) {
+        const float4 u0 = reinterpret_cast<const float4 *>(src)[0];
+        reinterpret_cast<float4 *>(Yf + r * 4)[0] = make_float4(u0.x, u0.z, u0.y, u0.w);
       } else {
-        for (int k = 0; k < gc; ++k) Ys[r * gc + k] = src[k];
+        Ys[r] = src[0];
       }
     }
     __syncthreads();
-    for (int idx = threadIdx.x; idx < gn * K; idx += PD_THREADS) {
-      const int gi = idx / K, kap = idx - gi * K, al = kap / na, a = kap - al * na;
-      const float2 *y = Ys + al * nb * gc + gi;
-      const float2 *d = Dp + a * nb;
-      float sh = 0.f, sl = 0.f;
-      for (int b = 0; b < nb; ++b) df_mac(sh, sl, d[b], y[b * gc]);
-      Ps[gi * K + kap] = make_float2(sh, sl);
+    if (gc == 1) {
+      for (int kap = threadIdx.x; kap < K; kap += PD_THREADS) {
+        const int al = kap / na, a = kap - al * na;
+        const float2 *y = Ys + al * nb;
+        const float2 *d = Dp + a * nb;
+        float sh = 0.f, sl = 0.f;
+        for (int b = 0; b < nb; ++b) df_mac(sh, sl, d[b], y[b]);
+        Ps[kap] = make_float2(sh, sl);
+      }
+    } else {
+      // all gn columns of one (al, a) per thread, two per packed (f32x2)
+      // operation; each lane takes exactly the scalar df_mac's operations
+      for (int kap = threadIdx.x; kap < K; kap += PD_THREADS) {
+        const int al = kap / na, a = kap - al * na;
+        const float *yr = Yf + (int64_t)al * nb * 2 * gc;
+        const float2 *d = Dp + a * nb;
+        uint64_t s0 = 0, r0 = 0, s1 = 0, r1 = 0;
+        for (int b = 0; b < nb; ++b) {
+          const float2 dv = d[b];
+          const uint64_t ah = f2_pk(dv.x, dv.x), nah = f2_pk(-dv.x, -dv.x),
+                         nal = f2_pk(-dv.y, -dv.y);
+          if (gc == 4) {
+            const float4 H = reinterpret_cast<const float4 *>(yr + b * 8)[0];
+            const float4 L = reinterpret_cast<const float4 *>(yr + b * 8)[1];
+            df_mac2(s0, r0, ah, nah, nal, f2_pk(H.x, H.y), f2_pk(L.x, L.y));
+            df_mac2(s1, r1, ah, nah, nal, f2_pk(H.z, H.w), f2_pk(L.z, L.w));
+          } else {
+            const float4 V = reinterpret_cast<const float4 *>(yr + b * 4)[0];
+            df_mac2(s0, r0, ah, nah, nal, f2_pk(V.x, V.y), f2_pk(V.z, V.w));
+          }
+        }
+        const float2 S0 = f2_un(s0), R0 = f2_un(r0), S1 = f2_un(s1), R1 = f2_un(r1);
+        Ps[kap] = make_float2(S0.x, R0.x);
+        if (gn > 1) Ps[K + kap] = make_float2(S0.y, R0.y);
+        if (gn > 2) Ps[2 * K + kap] = make_float2(S1.x, R1.x);
+        if (gn > 3) Ps[3 * K + kap] = make_float2(S1.y, R1.y);
+      }
     }
     __syncthreads();
     // one exponent per row (G, g0 + gi) over its K values
