@@ -14,18 +14,20 @@
 // covers up to four B digits j stacked along N at TMEM column 64 (i + j): 9
 // MMAs per K step of 16 instead of KS (KS + 1) / 2 = 21 for KS = 6.
 //
-// Roles (one CTA per SM, static round-robin over the wave's jobs): warp 8
-// copies each K tile's A and B digits (lanes 0 and 1, 1-D bulk copies) into a
-// ring of shared stages and then writes the job's epilogue data into one of
-// two shared slots, off the epilogue's path (Y jobs: row exponents and Y2
+// Roles (one CTA per SM, static round-robin over the wave's jobs; warp
+// numbers of Y jobs, those of D_AB jobs in parentheses): warp 16 (8) copies
+// each K tile's A and B digits (lanes 0 and 1, 1-D bulk copies) into a ring
+// of shared stages and then writes the job's epilogue data into one of two
+// shared slots, off the epilogue's path (Y jobs: row exponents and Y2
 // offsets, column exponents; D_AB jobs: the rows' (F, f) and columns' (G, g)
 // decoding with their exponents and the tile's Sigma_FG offsets per block
-// pair); warp 9 issues the MMAs into the TMEM accumulator;
-// warps 0-7 (TMEM lanes 32 (w % 4).., columns 32 (w / 4)..) drain the
+// pair); warp 17 (9) issues the MMAs into the TMEM accumulator; warps 0-15
+// (0-7), TMEM lanes 32 (w % 4).. and columns 16 (32) (w / 4).., drain the
 // accumulator into those sums, release it to the next job's MMAs, and then
 // write Y (f32 pairs, and FP64 where read) or add the surviving Sigma_FG
-// blocks to the fixed-point Sigma.  Every wait is bounded: on expiry the kernel records
-// HFX_DEV_ERR_TIMEOUT, drains its copies and MMAs, frees TMEM and returns.
+// blocks to the fixed-point Sigma.  Every wait is bounded: on expiry the
+// kernel records HFX_DEV_ERR_TIMEOUT, drains its copies and MMAs, frees TMEM
+// and returns.
 #include <cuda_bf16.h>
 
 #include "hfx_split.h"
@@ -33,8 +35,16 @@
 
 namespace split {
 
-constexpr int PG_EPI = 8;                      // epilogue warps
-constexpr int PG_THREADS = (PG_EPI + 2) * 32;  // + loader warp + MMA warp
+// Epilogue warps: 4 TMEM lane quarters x EPI / 4 groups of CW columns.  Y
+// jobs take 16 warps of 16 columns (96 registers, the budget of 20 warps, as
+// warps are placed four per scheduler): with 8 the epilogue had two warps per
+// scheduler to hide its latencies.  D_AB jobs keep 8 warps of 32 columns.
+template <int JOB>
+struct PgGeo {
+  static constexpr int EPI = JOB == 0 ? 16 : 8;
+  static constexpr int CW = NT / (EPI / 4);
+  static constexpr int THREADS = (EPI + 2) * 32;  // + loader warp + MMA warp
+};
 constexpr int PG_NST = 3;                      // operand stages
 constexpr long long PG_WAIT = 2000000000ll;    // cycles per bounded wait
 
@@ -273,7 +283,8 @@ __device__ __forceinline__ void pg_operands(const SplitShared &S, const SplitWav
 }
 
 template <int KS, int JOB>
-__global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWave W) {
+__global__ void __launch_bounds__(PgGeo<JOB>::THREADS, 1) k_pgemm(SplitShared S, SplitWave W) {
+  constexpr int PG_EPI = PgGeo<JOB>::EPI, PG_CW = PgGeo<JOB>::CW;
   constexpr int A_BYTES = KS * TM * TK * 2;
   constexpr int B_BYTES = KS * NT * TK * 2;
   constexpr int STAGE = A_BYTES + B_BYTES;
@@ -440,7 +451,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
     // ------------------------------------------------------------ epilogue
     const int q4 = warp & 3, hf = warp >> 2;
     const int row = q4 * 32 + lane;
-    const int c0 = hf * 32;  // this warp's 32 of the 64 columns
+    const int c0 = hf * PG_CW;  // this warp's PG_CW of the 64 columns
     long long hand = 0;
     long long mcount = 0;
     for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
@@ -448,7 +459,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
       if (jb.nk == 0) continue;  // no MMAs, no accumulator handoff
       int ea;
       // Y: the column exponents (pairs of int16)
-      uint32_t ebp[JOB == 0 ? 16 : 1];
+      uint32_t ebp[JOB == 0 ? PG_CW / 2 : 1];
       bool valid;
       // Y job: row (b, G, g) of Y, Y2 row, FP64 need, Y regions
       int64_t yrow = 0, y2row = -1, nrowY = 0, y2base = 0, y64base = 0;
@@ -469,7 +480,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         const PgMetaY &m = meta[ms];
         ea = m.ea[row];
 #pragma unroll
-        for (int p = 0; p < 16; ++p)
+        for (int p = 0; p < PG_CW / 2; ++p)
           ebp[p] = (uint32_t)(uint16_t)m.eb[c0 + 2 * p] |
                    ((uint32_t)(uint16_t)m.eb[c0 + 2 * p + 1] << 16);
         nbY = m.nbY;
@@ -507,12 +518,12 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
       // one accumulator handoff per K chunk.  D_AB: the chunks' exact sums add
       // in int64.  Y: the order groups (exact f32 integers times powers of two)
       // add in double-float, columns (2p, 2p + 1) in the two f32x2 lanes.
-      long long Wv[JOB == 1 ? 32 : 1];
-      uint64_t ds[JOB == 0 ? 16 : 1], dr[JOB == 0 ? 16 : 1];
+      long long Wv[JOB == 1 ? PG_CW : 1];
+      uint64_t ds[JOB == 0 ? PG_CW / 2 : 1], dr[JOB == 0 ? PG_CW / 2 : 1];
 #pragma unroll
-      for (int i = 0; i < (JOB == 1 ? 32 : 1); ++i) Wv[i] = 0;
+      for (int i = 0; i < (JOB == 1 ? PG_CW : 1); ++i) Wv[i] = 0;
 #pragma unroll
-      for (int p = 0; p < (JOB == 0 ? 16 : 1); ++p) ds[p] = dr[p] = 0;
+      for (int p = 0; p < (JOB == 0 ? PG_CW / 2 : 1); ++p) ds[p] = dr[p] = 0;
       bool aborted = false;
       for (int k0 = 0; k0 < jb.nk; k0 += KT_CHUNK) {
         const uint32_t par = (uint32_t)(hand & 1);
@@ -526,18 +537,20 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         umma::fence_after_sync();
 #pragma unroll
         for (int g = 0; g < KS; ++g) {
-          float v[32];
-          umma::tmem_ld32(tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(g * NT + c0), v);
+          float v[PG_CW];
+          const uint32_t ta = tbase + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(g * NT + c0);
+          if constexpr (PG_CW == 32) umma::tmem_ld32(ta, v);
+          else umma::tmem_ld16(ta, v);
           if constexpr (JOB == 0) {
             const float cg = __int_as_float((7 * (KS - 1 - g) + 127) << 23);
             const uint64_t c2 = f2_pk(cg, cg);
 #pragma unroll
-            for (int p = 0; p < 16; ++p)
+            for (int p = 0; p < PG_CW / 2; ++p)
               df_acc2(ds[p], dr[p], f2_mul(f2_pk(v[2 * p], v[2 * p + 1]), c2));
           } else {
             const long long sc = 1ll << (7 * (KS - 1 - g));
 #pragma unroll
-            for (int i = 0; i < 32; ++i) Wv[i] += (long long)__float2int_rn(v[i]) * sc;
+            for (int i = 0; i < PG_CW; ++i) Wv[i] += (long long)__float2int_rn(v[i]) * sc;
           }
         }
         // the accumulator is free for the next chunk's or job's MMAs
@@ -556,7 +569,7 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         double *Y = W.scratch + y64base;
         float2 *Y2 = reinterpret_cast<float2 *>(W.scratch + y2base);
 #pragma unroll
-        for (int p = 0; p < 16; ++p) {
+        for (int p = 0; p < PG_CW / 2; ++p) {
           const int al = jb.nt * NT + c0 + 2 * p;
           if (al >= pA) break;
           float2 o[2];
@@ -575,14 +588,14 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
         // offsets come from the slot's table, or (a tile over more block pairs
         // than the table holds) from the same lookups done here
         const PgMetaD &m = metaD[dms];
-        const int ilim = valid ? 32 : 0;
+        const int ilim = valid ? PG_CW : 0;
         int lastgi = -1;
         int64_t off = -1, moff = -1;
         int ng = 0;
         if (m.tbl) {
-          // unrolled and free of calls, so the 32 chunk sums stay in registers
+          // unrolled and free of calls, so the chunk sums stay in registers
 #pragma unroll
-          for (int i = 0; i < 32; ++i) {
+          for (int i = 0; i < PG_CW; ++i) {
             const int c = c0 + i;
             const int gi = m.gi[c];
             if (i >= ilim || gi < 0) break;
@@ -603,10 +616,10 @@ __global__ void __launch_bounds__(PG_THREADS, 1) k_pgemm(SplitShared S, SplitWav
           // a tile over more block pairs than the table holds: the same adds
           // in the same order, the sums copied to a local array first so the
           // lookups' call does not hold them
-          long long Wl[32];
+          long long Wl[PG_CW];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) Wl[i] = Wv[i];
-          for (int i = 0; i < 32; ++i) {
+          for (int i = 0; i < PG_CW; ++i) Wl[i] = Wv[i];
+          for (int i = 0; i < PG_CW; ++i) {
             const int c = c0 + i;
             const int gi = m.gi[c];
             if (gi < 0) break;
@@ -646,7 +659,7 @@ cudaError_t launch_pgemm_t(const SplitShared &S, const SplitWave &W, int64_t max
   cudaError_t e = cudaFuncSetAttribute(k_pgemm<KS, JOB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_pgemm<KS, JOB><<<blocks, PG_THREADS, smem, st>>>(S, W);
+  k_pgemm<KS, JOB><<<blocks, PgGeo<JOB>::THREADS, smem, st>>>(S, W);
   return cudaGetLastError();
 }
 
