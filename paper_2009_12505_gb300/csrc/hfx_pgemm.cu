@@ -17,17 +17,17 @@
 // Roles (one CTA per SM, static round-robin over the wave's jobs; warp
 // numbers of Y jobs, those of D_AB jobs in parentheses): warp 16 (8) copies
 // each K tile's A and B digits (lanes 0 and 1, 1-D bulk copies) into a ring
-// of shared stages and then writes the job's epilogue data into one of two
-// shared slots, off the epilogue's path (Y jobs: row exponents and Y2
-// offsets, column exponents; D_AB jobs: the rows' (F, f) and columns' (G, g)
-// decoding with their exponents and the tile's Sigma_FG offsets per block
-// pair); warp 17 (9) issues the MMAs into the TMEM accumulator; warps 0-15
-// (0-7), TMEM lanes 32 (w % 4).. and columns 16 (32) (w / 4).., drain the
-// accumulator into those sums, release it to the next job's MMAs, and then
-// write Y (f32 pairs, and FP64 where read) or add the surviving Sigma_FG
-// blocks to the fixed-point Sigma.  Every wait is bounded: on expiry the
-// kernel records HFX_DEV_ERR_TIMEOUT, drains its copies and MMAs, frees TMEM
-// and returns.
+// of shared stages; warp 18 (10) writes each job's epilogue data into one of
+// two shared slots, off the epilogue's and the loader's paths (Y jobs: row
+// exponents and Y2 offsets, column exponents; D_AB jobs: the rows' (F, f) and
+// columns' (G, g) decoding with their exponents and the tile's Sigma_FG
+// offsets per block pair); warp 17 (9) issues the MMAs into the TMEM
+// accumulator; warps 0-15 (0-7), TMEM lanes 32 (w % 4).. and columns 16 (32)
+// (w / 4).., drain the accumulator into those sums, release it to the next
+// job's MMAs, and then write Y (f32 pairs, and FP64 where read) or add the
+// surviving Sigma_FG blocks to the fixed-point Sigma.  Every wait is bounded:
+// on expiry the kernel records HFX_DEV_ERR_TIMEOUT, drains its copies and
+// MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 
 #include "hfx_split.h"
@@ -43,7 +43,7 @@ template <int JOB>
 struct PgGeo {
   static constexpr int EPI = JOB == 0 ? 16 : 8;
   static constexpr int CW = NT / (EPI / 4);
-  static constexpr int THREADS = (EPI + 2) * 32;  // + loader warp + MMA warp
+  static constexpr int THREADS = (EPI + 3) * 32;  // + loader, MMA and job-data warps
 };
 constexpr int PG_NST = 3;                      // operand stages
 constexpr long long PG_WAIT = 2000000000ll;    // cycles per bounded wait
@@ -57,7 +57,7 @@ struct PgSmem {
 
 constexpr int PG_CTL_BYTES = (int)((sizeof(PgSmem) + 15) / 16 * 16);
 
-// One Y job's epilogue data, written by the loader warp ahead of the job into
+// One Y job's epilogue data, written by the job-data warp ahead of the job into
 // one of two slots, so the epilogue reads shared memory instead of running a
 // chain of dependent global loads per job.
 struct PgMetaY {
@@ -70,7 +70,7 @@ struct PgMetaY {
   int16_t eb[NT];     // column exponents (0 beyond nabf(A))
 };
 
-// One D_AB job's epilogue data, written by the loader warp ahead of the job:
+// One D_AB job's epilogue data, written by the job-data warp ahead of the job:
 // the row (F, f) and column (G, g) decoding of the tile and, when the tile
 // spans at most PG_TBL (F block, G block) pairs, each pair's Sigma_FG offset
 // and that of its mirror (-1: no surviving term or no mirror).
@@ -87,7 +87,7 @@ struct PgMetaD {
   int64_t off[PG_TBL], moff[PG_TBL];  // [fi * ngb + gi]
 };
 
-// Fill m for D_AB job jb (the whole loader warp); loads issued level by level.
+// Fill m for D_AB job jb (the whole job-data warp); loads issued level by level.
 __device__ __forceinline__ void dab_meta_fill(const SplitShared &S, const SplitWave &W,
                                               const Job &jb, const WorkItem &it, PgMetaD &m,
                                               int lane) {
@@ -199,7 +199,7 @@ __device__ __noinline__ void dab_lookup(const SplitShared &S, const Job &jb, int
   }
 }
 
-// Fill m for Y job jb (the whole loader warp; lane l takes rows l, l + 32,
+// Fill m for Y job jb (the whole job-data warp; lane l takes rows l, l + 32,
 // l + 64, l + 96).  The loads are issued level by level for the four rows at
 // once, so the dependent chain is three loads deep, not twelve.
 __device__ __forceinline__ void y_meta_fill(const SplitShared &S, const SplitWave &W,
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(PgGeo<JOB>::THREADS, 1) k_pgemm(SplitShared S,
 
   if (warp == PG_EPI) {
     // ------------------------------------------------------------ loader
-    long long step = 0, mcount = 0;
+    long long step = 0;
     for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
       if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
       const Job jb = jobs[j];
@@ -332,34 +332,6 @@ __global__ void __launch_bounds__(PgGeo<JOB>::THREADS, 1) k_pgemm(SplitShared S,
       const __nv_bfloat16 *Ab, *Bb;
       const int16_t *ea_p, *eb_p;
       pg_operands<KS, JOB>(S, W, jb, it, Ab, Bb, ea_p, eb_p);
-      // The job's epilogue data go to slot mcount & 1, after the slot's last
-      // job is done with it.  A job of one accumulator chunk gets them after
-      // its copies (which then overlap the data's loads); a job of several
-      // chunks gets them first: its later copies wait for the MMAs of its
-      // second chunk, those for the epilogue's drain of its first, and that
-      // drain for these data.
-      auto put_meta = [&]() -> bool {
-        const int ms = (int)(mcount & 1);
-        const long long use = mcount >> 1;
-        bool w = true;
-        if (lane == 0) {
-          if (use >= 1)
-            w = umma::mbar_wait(&ctl->mempty[ms], (uint32_t)((use - 1) & 1), S.err, PG_WAIT);
-          w = w && !*abort_f;
-        }
-        if (!__shfl_sync(0xffffffffu, (int)w, 0)) {
-          if (lane == 0) *abort_f = 1;
-          return false;
-        }
-        if constexpr (JOB == 0) y_meta_fill(S, W, jb, it, meta[ms], lane);
-        else dab_meta_fill(S, W, jb, it, metaD[ms], lane);
-        __syncwarp();
-        if (lane == 0) umma::mbar_arrive(&ctl->mfull[ms]);
-        ++mcount;
-        return true;
-      };
-      const bool meta_first = jb.nk > KT_CHUNK;
-      if (meta_first && !put_meta()) break;
       bool ok = true;
       for (int kt = 0; kt < jb.nk; ++kt, ++step) {
         const int s = (int)(step % PG_NST);
@@ -385,13 +357,41 @@ __global__ void __launch_bounds__(PgGeo<JOB>::THREADS, 1) k_pgemm(SplitShared S,
           umma::bulk_g2s(st + A_BYTES, Bb + (int64_t)kt * KS * NT * TK, B_BYTES, &ctl->full[s]);
       }
       if (!ok) break;
-      if (jb.nk > 0 && !meta_first && !put_meta()) break;
     }
     // drain: the last stages issued must have landed before the CTA exits
     if (lane == 0) {
       const long long first = step > PG_NST ? step - PG_NST : 0;
       for (long long t = first; t < step; ++t)
         umma::mbar_wait(&ctl->full[t % PG_NST], (uint32_t)((t / PG_NST) & 1), S.err, PG_WAIT);
+    }
+  } else if (warp == PG_EPI + 2) {
+    // ------------------------------------------------------------ job data
+    // each job with K tiles gets its epilogue data in slot mcount & 1 once the
+    // slot's previous job is done with it; this warp waits on nothing but the
+    // epilogue, so the loader's copies never wait for these loads
+    long long mcount = 0;
+    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+      if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
+      const Job jb = jobs[j];
+      if (jb.nk == 0) continue;  // the epilogue skips it too
+      const WorkItem it = S.items[jb.w];
+      const int ms = (int)(mcount & 1);
+      const long long use = mcount >> 1;
+      bool w = true;
+      if (lane == 0) {
+        if (use >= 1)
+          w = umma::mbar_wait(&ctl->mempty[ms], (uint32_t)((use - 1) & 1), S.err, PG_WAIT);
+        w = w && !*abort_f;
+      }
+      if (!__shfl_sync(0xffffffffu, (int)w, 0)) {
+        if (lane == 0) *abort_f = 1;
+        break;
+      }
+      if constexpr (JOB == 0) y_meta_fill(S, W, jb, it, meta[ms], lane);
+      else dab_meta_fill(S, W, jb, it, metaD[ms], lane);
+      __syncwarp();
+      if (lane == 0) umma::mbar_arrive(&ctl->mfull[ms]);
+      ++mcount;
     }
   } else if (warp == PG_EPI + 1) {
     // ------------------------------------------------------------ MMA issuer
@@ -468,7 +468,7 @@ __global__ void __launch_bounds__(PgGeo<JOB>::THREADS, 1) k_pgemm(SplitShared S,
       // D_AB job: row (F - fb0, f) and the slot holding the job's data
       int F = 0, nf = 0, f = 0, dms = 0;
       if constexpr (JOB == 0) {
-        // the loader warp wrote this job's data into slot mcount & 1
+        // the job-data warp wrote this job's data into slot mcount & 1
         const int ms = (int)(mcount & 1);
         const bool okm = umma::mbar_wait(&ctl->mfull[ms], (uint32_t)((mcount >> 1) & 1), S.err,
                                          PG_WAIT);
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(PgGeo<JOB>::THREADS, 1) k_pgemm(SplitShared S,
         __syncwarp();
         if (lane == 0) umma::mbar_arrive(&ctl->mempty[ms]);
       } else {
-        // the loader warp wrote this job's data into slot mcount & 1; the slot
+        // the job-data warp wrote this job's data into slot mcount & 1; the slot
         // is held until the Sigma adds at the end of the job
         dms = (int)(mcount & 1);
         const bool okm = umma::mbar_wait(&ctl->mfull[dms], (uint32_t)((mcount >> 1) & 1),
