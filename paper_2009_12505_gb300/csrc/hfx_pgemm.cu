@@ -44,13 +44,15 @@ struct PgGeo {
   static constexpr int EPI = JOB == 0 ? 16 : 8;
   static constexpr int CW = NT / (EPI / 4);
   static constexpr int THREADS = (EPI + 3) * 32;  // + loader, MMA and job-data warps
+  // job-data slots: Y jobs are short, so their data run further ahead
+  static constexpr int NMS = JOB == 0 ? 4 : 2;
 };
 constexpr int PG_NST = 3;                      // operand stages
 constexpr long long PG_WAIT = 2000000000ll;    // cycles per bounded wait
 
 struct PgSmem {
   uint64_t full[PG_NST], empty[PG_NST], tfull, tempty, drain;
-  uint64_t mfull[2], mempty[2];  // Y jobs: the epilogue-data ring (PgMetaY)
+  uint64_t mfull[4], mempty[4];  // the epilogue-data ring (PgMetaY / PgMetaD slots)
   uint32_t tslot;
   int abort_f;
 };
@@ -284,7 +286,7 @@ __device__ __forceinline__ void pg_operands(const SplitShared &S, const SplitWav
 
 template <int KS, int JOB>
 __global__ void __launch_bounds__(PgGeo<JOB>::THREADS, 1) k_pgemm(SplitShared S, SplitWave W) {
-  constexpr int PG_EPI = PgGeo<JOB>::EPI, PG_CW = PgGeo<JOB>::CW;
+  constexpr int PG_EPI = PgGeo<JOB>::EPI, PG_CW = PgGeo<JOB>::CW, PG_NMS = PgGeo<JOB>::NMS;
   constexpr int A_BYTES = KS * TM * TK * 2;
   constexpr int B_BYTES = KS * NT * TK * 2;
   constexpr int STAGE = A_BYTES + B_BYTES;
@@ -306,7 +308,7 @@ __global__ void __launch_bounds__(PgGeo<JOB>::THREADS, 1) k_pgemm(SplitShared S,
     umma::mbar_init(&ctl->tfull, 1);
     umma::mbar_init(&ctl->tempty, PG_EPI);
     umma::mbar_init(&ctl->drain, 1);
-    for (int m = 0; m < 2; ++m) {
+    for (int m = 0; m < PG_NMS; ++m) {
       umma::mbar_init(&ctl->mfull[m], 1);
       umma::mbar_init(&ctl->mempty[m], PG_EPI);
     }
@@ -325,10 +327,20 @@ __global__ void __launch_bounds__(PgGeo<JOB>::THREADS, 1) k_pgemm(SplitShared S,
   if (warp == PG_EPI) {
     // ------------------------------------------------------------ loader
     long long step = 0;
-    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
+    // descriptors two jobs ahead and work items one job ahead, so a job's
+    // operand addresses wait on one level of loads (Y jobs have two K tiles)
+    const int G = (int)gridDim.x;
+    const int j0 = blockIdx.x;
+    Job jn1 = j0 < njobs ? jobs[j0] : Job{};
+    Job jn2 = j0 + G < njobs ? jobs[j0 + G] : Job{};
+    WorkItem itn1 = j0 < njobs ? S.items[jn1.w] : WorkItem{};
+    for (int j = j0; j < njobs; j += G) {
       if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
-      const Job jb = jobs[j];
-      const WorkItem it = S.items[jb.w];
+      const Job jb = jn1;
+      const WorkItem it = itn1;
+      jn1 = jn2;
+      if (j + G < njobs) itn1 = S.items[jn1.w];
+      if (j + 2 * G < njobs) jn2 = jobs[j + 2 * G];
       const __nv_bfloat16 *Ab, *Bb;
       const int16_t *ea_p, *eb_p;
       pg_operands<KS, JOB>(S, W, jb, it, Ab, Bb, ea_p, eb_p);
@@ -366,17 +378,19 @@ __global__ void __launch_bounds__(PgGeo<JOB>::THREADS, 1) k_pgemm(SplitShared S,
     }
   } else if (warp == PG_EPI + 2) {
     // ------------------------------------------------------------ job data
-    // each job with K tiles gets its epilogue data in slot mcount & 1 once the
+    // each job with K tiles gets its epilogue data in slot mcount % NMS once the
     // slot's previous job is done with it; this warp waits on nothing but the
     // epilogue, so the loader's copies never wait for these loads
     long long mcount = 0;
+    Job jnext = blockIdx.x < njobs ? jobs[blockIdx.x] : Job{};  // a job ahead
     for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
       if (__shfl_sync(0xffffffffu, lane == 0 ? *abort_f : 0, 0)) break;
-      const Job jb = jobs[j];
+      const Job jb = jnext;
+      if (j + (int)gridDim.x < njobs) jnext = jobs[j + gridDim.x];
       if (jb.nk == 0) continue;  // the epilogue skips it too
       const WorkItem it = S.items[jb.w];
-      const int ms = (int)(mcount & 1);
-      const long long use = mcount >> 1;
+      const int ms = (int)(mcount % PG_NMS);
+      const long long use = mcount / PG_NMS;
       bool w = true;
       if (lane == 0) {
         if (use >= 1)
@@ -401,8 +415,10 @@ __global__ void __launch_bounds__(PgGeo<JOB>::THREADS, 1) k_pgemm(SplitShared S,
       uint32_t idesc[4];
 #pragma unroll
       for (int n = 1; n <= 4; ++n) idesc[n - 1] = umma::idesc_bf16_f32(TM, NT * n);
+      Job jnext = blockIdx.x < njobs ? jobs[blockIdx.x] : Job{};  // a job ahead
       for (int j = blockIdx.x; j < njobs && !*abort_f; j += gridDim.x) {
-        const Job jb = jobs[j];
+        const Job jb = jnext;
+        if (j + (int)gridDim.x < njobs) jnext = jobs[j + gridDim.x];
         if (jb.nk == 0) continue;  // an empty job (a skipped candidate tile)
         bool ok = true;
         // K chunks of at most KT_CHUNK tiles, one accumulator handoff each
@@ -454,8 +470,11 @@ __global__ void __launch_bounds__(PgGeo<JOB>::THREADS, 1) k_pgemm(SplitShared S,
     const int c0 = hf * PG_CW;  // this warp's PG_CW of the 64 columns
     long long hand = 0;
     long long mcount = 0;
+    // the next job's descriptor is loaded a job ahead
+    Job jnext = blockIdx.x < njobs ? jobs[blockIdx.x] : Job{};
     for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
-      const Job jb = jobs[j];
+      const Job jb = jnext;
+      if (j + (int)gridDim.x < njobs) jnext = jobs[j + gridDim.x];
       if (jb.nk == 0) continue;  // no MMAs, no accumulator handoff
       int ea;
       // Y: the column exponents (pairs of int16)
@@ -468,9 +487,9 @@ __global__ void __launch_bounds__(PgGeo<JOB>::THREADS, 1) k_pgemm(SplitShared S,
       // D_AB job: row (F - fb0, f) and the slot holding the job's data
       int F = 0, nf = 0, f = 0, dms = 0;
       if constexpr (JOB == 0) {
-        // the job-data warp wrote this job's data into slot mcount & 1
-        const int ms = (int)(mcount & 1);
-        const bool okm = umma::mbar_wait(&ctl->mfull[ms], (uint32_t)((mcount >> 1) & 1), S.err,
+        // the job-data warp wrote this job's data into slot mcount % NMS
+        const int ms = (int)(mcount % PG_NMS);
+        const bool okm = umma::mbar_wait(&ctl->mfull[ms], (uint32_t)((mcount / PG_NMS) & 1), S.err,
                                          PG_WAIT);
         ++mcount;
         if (umma::bar_any(!okm || *abort_f, PG_EPI * 32)) {
@@ -497,10 +516,10 @@ __global__ void __launch_bounds__(PgGeo<JOB>::THREADS, 1) k_pgemm(SplitShared S,
         __syncwarp();
         if (lane == 0) umma::mbar_arrive(&ctl->mempty[ms]);
       } else {
-        // the job-data warp wrote this job's data into slot mcount & 1; the slot
+        // the job-data warp wrote this job's data into slot mcount % NMS; the slot
         // is held until the Sigma adds at the end of the job
-        dms = (int)(mcount & 1);
-        const bool okm = umma::mbar_wait(&ctl->mfull[dms], (uint32_t)((mcount >> 1) & 1),
+        dms = (int)(mcount % PG_NMS);
+        const bool okm = umma::mbar_wait(&ctl->mfull[dms], (uint32_t)((mcount / PG_NMS) & 1),
                                          S.err, PG_WAIT);
         ++mcount;
         if (umma::bar_any(!okm || *abort_f, PG_EPI * 32)) {
@@ -655,7 +674,7 @@ cudaError_t launch_pgemm_t(const SplitShared &S, const SplitWave &W, int64_t max
   const int blocks = (int)std::min<int64_t>(maxjobs, S.nsm > 0 ? S.nsm : 1);
   if (blocks <= 0) return cudaSuccess;
   const size_t smem = (size_t)PG_NST * KS * (TM + NT) * TK * 2 + PG_CTL_BYTES +
-                      2 * (JOB == 0 ? sizeof(PgMetaY) : sizeof(PgMetaD)) + 64;
+                      PgGeo<JOB>::NMS * (JOB == 0 ? sizeof(PgMetaY) : sizeof(PgMetaD)) + 64;
   cudaError_t e = cudaFuncSetAttribute(k_pgemm<KS, JOB>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
