@@ -746,9 +746,11 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
     k_zc(SplitShared S, SplitWave W, ZcCfg cfg) {
   constexpr int ZC_EPI = EPI, ZC_NQ = ZcGeo<EPI>::NQ, ZC_CW = ZcGeo<EPI>::CW,
                 ZC_ET = ZcGeo<EPI>::ET;
-  // owned outputs per epilogue thread: paired jobs have blocks and atom A of
-  // at most 16 AOs, so at most 16 x 32 outputs per job
-  constexpr int ZC_OWN = PAIR ? (16 * 32 + ZC_ET - 1) / ZC_ET : ZcGeo<EPI>::OWN;
+  // owned outputs per epilogue thread, for the job sums of both paired jobs:
+  // na x (outputs of the job's blocks), at most 16 x 32 in the small class
+  // (atom A and blocks of at most 16 AOs), else 32 x 64 (two blocks of 16
+  // columns of piece 1 have nao(B) outputs each)
+  constexpr int ZC_OWN = PAIR && KBM == 16 ? (16 * 32 + ZC_ET - 1) / ZC_ET : ZcGeo<EPI>::OWN;
   constexpr int A_BYTES = KS * 128 * KBM * 2;
   constexpr int B_BYTES = KS * ZC_COLS * KBM * 2;
   constexpr int STG = A_BYTES + B_BYTES;
@@ -1121,7 +1123,7 @@ __global__ void __launch_bounds__(ZcGeo<EPI>::THREADS, 1)
         // quarter's warps stage Z in rows 32 .. 63 of the reduction buffer
         // (unused by such a tile) and all epilogue warps share the contraction
         const int rv = min(128, pA * na - mt * 128);
-        if (PAIR && YST && rv <= 32) {
+        if (PAIR && YST && KBM == 16 && rv <= 32) {
           constexpr int NPT = ZC_CW / 2;
           if (q4 == 0 && hb >= 0 && rvalid) {
             float2 *zs = red + (int64_t)hf * rs * 128 + 32 + row;
@@ -1328,8 +1330,8 @@ cudaError_t zc_range_t(const SplitShared &S, const SplitWave &W, const ZcPlanSha
     return launch(k_zc<KS, 16, 3, 8, false, false>, T8, 3, 16, 0, 2);
   }
   if (ZC_STAGE_Y && smem_of(2, 32, P.ybytes, 2) <= kMax)
-    return launch(k_zc<KS, 32, 2, 8, true, false>, T8, 2, 32, P.ybytes, 2);
-  return launch(k_zc<KS, 32, 2, 8, false, false>, T8, 2, 32, 0, 2);
+    return launch(k_zc<KS, 32, 2, 8, true, true>, T8, 2, 32, P.ybytes, 2);
+  return launch(k_zc<KS, 32, 2, 8, false, true>, T8, 2, 32, 0, 2);
 }
 
 // The wave's small-class jobs [0, nsmall) with the shape of blocks of at most
