@@ -115,8 +115,8 @@ def workload_desc(wl) -> str:
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_zc launch on the 8-atom
 # cell over its issued bf16 tensor flops, captured from hfx_zc.cu with this
 # sha256 prefix (see the k_zc profile summary under profiles/)
-ZC_BYTES_PER_TENSOR_FLOP = (30.919904e9 + 0.473198e9) / 14.988985761792e12
-ZC_CAPTURED_SHA = "0a83cf7739c28ab5"
+ZC_BYTES_PER_TENSOR_FLOP = (30.483057e9 + 0.469812e9) / 14.988985761792e12
+ZC_CAPTURED_SHA = "4bbee58897ff9394"
 
 
 def zc_traffic(tensor_flops_per_launch):
