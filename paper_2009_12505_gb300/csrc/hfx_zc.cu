@@ -176,9 +176,10 @@ __device__ __forceinline__ int zc_cost_key(int mtz, int k) {
 }
 // Size class of a job: small when atom A and every block it touches have at
 // most 16 AOs (outputs, Z columns and F entries), so its Y rows fit the
-// staging buffers of the fastest kernel variant, which pairs its jobs; small jobs take keys [0, 256), the others
-// [256, 512), and the host places the small class first, so each class is a
-// contiguous, longest-first range launched with its own variant.
+// staging buffers of the fastest kernel variant and its job sums fit fewer
+// registers; small jobs take keys [0, 256), the others [256, 512), and the
+// host places the small class first, so each class is a contiguous,
+// longest-first range launched with its own variant.
 __device__ __forceinline__ int zc_key(int mtz, int k, bool small) {
   return zc_cost_key(mtz, k) + (small ? 0 : ZC_NCOST);
 }
@@ -1318,8 +1319,10 @@ cudaError_t zc_range_t(const SplitShared &S, const SplitWave &W, const ZcPlanSha
   // 8 epilogue warps (2 column groups of 16).  16 warps (4 groups of 8) leave
   // room for only two operand stages next to the staged Y and were slower.
   constexpr int T8 = ZcGeo<8>::THREADS;
-  // The small class (every block and atom A of at most 16 AOs) pairs its jobs
-  // when its staged Y fits next to four operand stages.
+  // Jobs are taken in heavy/light pairs by the small class's four-stage
+  // variant (every block and atom A of at most 16 AOs) and by both variants
+  // of the large-block class; the small class's fallbacks, for cells whose
+  // staged Y does not fit next to four stages, keep one job at a time.
   if (P.kbmax <= 16) {
     if (ZC_STAGE_Y && smem_of(4, 16, P.ybytes, 2) <= kMax) {
       if (small) return launch(k_zc<KS, 16, 4, 8, true, true>, T8, 4, 16, P.ybytes, 2);

@@ -8,14 +8,22 @@ import bench
 
 
 def test_traffic_follows_the_captured_source_only(monkeypatch):
-    import hashlib
     src = os.path.join(bench.ROOT, "paper_2009_12505_gb300", "csrc", "hfx_zc.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    monkeypatch.setattr(bench, "ZC_CAPTURED_SHA", sha)
+    monkeypatch.setattr(bench, "ZC_CAPTURED_SHA", bench.source_digest(src))
     t = bench.zc_traffic(1e12)
     assert t == bench.ZC_BYTES_PER_TENSOR_FLOP * 1e12
     monkeypatch.setattr(bench, "ZC_CAPTURED_SHA", "0000000000000000")
     assert bench.zc_traffic(1e12) is None
+
+
+def test_source_digest_ignores_comments_only(tmp_path):
+    base = "int f(int x) {\n  return x + 1;\n}\n"
+    a, b, c = tmp_path / "a.cu", tmp_path / "b.cu", tmp_path / "c.cu"
+    a.write_text(base)
+    b.write_text("// a comment\n" + base.replace("x + 1;", "x + 1;  /* note */") + "\n\n")
+    c.write_text(base.replace("x + 1", "x + 2"))
+    assert bench.source_digest(str(a)) == bench.source_digest(str(b))
+    assert bench.source_digest(str(a)) != bench.source_digest(str(c))
 
 
 def test_sample_atoms_and_term_total():
