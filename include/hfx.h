@@ -126,8 +126,13 @@ hfx_status hfx_set_D(hfx_ctx *ctx, int32_t k, int32_t l, const int32_t n[3], con
  *   offs  nblk + 1 int64 offsets in doubles, HOST memory; offs[e+1]-offs[e]
  *         must equal the block's shape
  *   on_device  0: data is host memory; 1: data is device memory on this GPU
- * Replaces any existing blocks with the same keys.
- * Errors: HFX_E_ARG, HFX_E_SHAPE, HFX_E_NOMEM, HFX_E_CUDA.
+ * Replaces any existing blocks with the same keys.  A call that sets every
+ * block of the kind again, in ascending key order (the packed order: keys
+ * compared as (i, j, n1, n2, n3)) with the same offsets as the kind's packed
+ * blocks after a build, copies the data into the device array in place; any
+ * other call copies it into a new device chunk that the next build packs.
+ * Errors: HFX_E_ARG, HFX_E_SHAPE, HFX_E_NOMEM, HFX_E_CUDA (after a failed
+ * in-place copy the kind's values are undefined until set again).
  */
 hfx_status hfx_set_many(hfx_ctx *ctx, char which, int64_t nblk, const int32_t *keys,
                         const double *data, const int64_t *offs, int on_device);

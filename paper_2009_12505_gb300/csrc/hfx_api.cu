@@ -972,6 +972,28 @@ hfx_status hfx_set_many(hfx_ctx *ctx, char which, int64_t nblk, const int32_t *k
   }
   Kind &K = ctx->K[k];
   const int64_t lo = offs[0], hi = offs[nblk];
+  // A full re-set of a packed kind in its packed key order with the same
+  // block sizes (C, V or D of the next SCF step): the values are copied into
+  // the packed array in place, with no new chunk to allocate and no old one
+  // to free, and the key map stays as it is.
+  if (!K.dirty && K.data_is_chunk && K.chunks.size() == 1 && K.data.p == K.chunks[0].dev &&
+      (int64_t)K.keys.size() == nblk && K.chunks[0].n == (size_t)(hi - lo)) {
+    bool same = true;
+    for (int64_t b = 0; same && b < nblk; ++b) {
+      const int32_t *kk = keys + 5 * b;
+      same = hk_pack(kk[0], kk[1], kk[2], kk[3], kk[4]) == K.keys[b] &&
+             offs[b] - lo == K.offs[b];
+    }
+    if (same) {
+      invalidate(ctx, k, false);
+      cudaError_t e = cudaMemcpyAsync(K.chunks[0].dev, data + lo, (size_t)(hi - lo) * sizeof(double),
+                                      on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                      ctx->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+      if (e != cudaSuccess) return fail_cuda(ctx, "cudaMemcpyAsync", e);
+      return HFX_OK;
+    }
+  }
   Chunk c;
   c.n = (size_t)(hi - lo);
   cudaError_t e = cudaMalloc((void **)&c.dev, (c.n > 0 ? c.n : 1) * sizeof(double));
